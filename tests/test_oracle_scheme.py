@@ -1,0 +1,213 @@
+"""Pins of the oracle's CKKS layer: parameters against the paper's printed
+sets and outside primality/residue routines, encoding against its O(N^2)
+definition and closed forms, encryption noise against its analytic bound,
+key switching against the key equation, and the homomorphic operations
+against their slot-wise meaning (Sec. 2.3, Algorithm 2, Algorithm 1)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import _lib as C
+from oracle import ckks, fasttext
+from oracle import params as P
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+rng = np.random.default_rng(7)
+
+
+def _z(n):
+    return rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+
+
+# ---- parameters ----------------------------------------------------------------------
+
+def test_primes_against_sympy():
+    sympy = pytest.importorskip("sympy")
+    for bits, logn in ((40, 12), (50, 16), (60, 16)):
+        ps = P.primes_of_bits(bits, logn, 6)
+        step = 2 << logn
+        assert ps == sorted(ps, reverse=True)
+        for p in ps:
+            assert sympy.isprime(p) and p % step == 1 and p.bit_length() == bits
+        # nothing skipped: every candidate above the last prime is composite
+        j = 1
+        while (1 << bits) - j * step + 1 > ps[-1]:
+            c = (1 << bits) - j * step + 1
+            assert sympy.isprime(c) == (c in ps)
+            j += 1
+    for n in range(2, 3000):
+        assert P.is_prime(n) == sympy.isprime(n)
+
+
+def test_root_is_smallest_nonresidue_power():
+    sympy = pytest.importorskip("sympy")
+    for logn in (12, 16):
+        for q in P.primes_of_bits(60, logn, 2) + P.primes_of_bits(40, logn, 2):
+            psi = P.root_2n(q, logn)
+            assert pow(psi, 1 << logn, q) == q - 1 and pow(psi, 2 << logn, q) == 1
+            x = 2
+            while sympy.is_quad_residue(x, q):
+                x += 1
+            assert psi == pow(x, (q - 1) >> (logn + 1), q)
+
+
+def test_security_table_agrees_with_paper_sets():
+    # the paper's sets at >= 128 bits fit under the bound; its 98-bit set does not
+    with open(os.path.join(HERE, "golden", "paper_parameter_sets.txt")) as f:
+        rows = [tuple(int(x) for x in ln.split()) for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 5
+    for logn, logq, lam in rows:
+        assert (logq <= P.SECURE_LOG_QP[logn]) == (lam >= 128), (logn, logq, lam)
+
+
+# ---- encoding (Sec. 2.3 ENCODE / DECODE) ------------------------------------------------
+
+def _encode_definition(orc, z, scale):
+    """m_k = (2/N) Re sum_j scale z_j omega^(-e_j k), written out."""
+    N = orc.N
+    e = orc.slot_exponents()
+    k = np.arange(N)
+    zz = np.zeros(N // 2, complex)
+    zz[: len(z)] = z
+    ph = np.exp(-1j * np.pi * np.outer(k, e) / N)
+    return (2.0 / N) * (ph @ (scale * zz)).real
+
+
+@pytest.mark.parametrize("logn", [4, 7, 10])
+def test_encode_matches_definition(logn):
+    orc = ckks.Oracle(logn=logn, n_limbs=2, n_special=1, alpha=1, mid_bits=50)
+    z = _z(orc.N // 2)
+    got = orc.encode_real(z, 2.0 ** 40)
+    want = _encode_definition(orc, z, 2.0 ** 40)
+    # FP64 rounding only: far below the 1/2 that could move a rounded coefficient
+    assert np.max(np.abs(got - want)) < 1e-14 * 2.0 ** 40 * orc.N
+
+
+def test_encode_closed_forms():
+    orc = ckks.Oracle(logn=10, n_limbs=2, n_special=1, alpha=1, mid_bits=50)
+    c = 0.3125
+    pt = orc.encode(np.full(orc.N // 2, c), 2.0 ** 40)
+    m = ckks.crt_centered(pt.m, orc.q[:2])
+    assert int(m[0]) == round(c * 2 ** 40) and all(int(v) == 0 for v in m[1:])
+    # a purely imaginary constant i*c lands on X^(N/2): omega^(e N/2) = i^e, and 5^j = 1 mod 4
+    pt = orc.encode(np.full(orc.N // 2, 1j * c), 2.0 ** 40)
+    m = ckks.crt_centered(pt.m, orc.q[:2])
+    assert int(m[orc.N // 2]) == round(c * 2 ** 40)
+    assert sum(abs(int(v)) for v in m) == round(c * 2 ** 40)
+
+
+def test_encode_rotation_is_automorphism():
+    orc = ckks.Oracle(logn=10, n_limbs=2, n_special=1, alpha=1, mid_bits=50)
+    z = _z(orc.N // 2)
+    for r in (1, 3, -1):
+        g = ckks.galois_element(r, orc.N)
+        a = ckks.crt_centered(C.automorph(orc.encode(z).m, orc.q[:2], g), orc.q[:2])
+        b = ckks.crt_centered(orc.encode(np.roll(z, -r)).m, orc.q[:2])
+        assert max(abs(int(x) - int(y)) for x, y in zip(a, b)) <= 1
+
+
+def test_decode_encode_precision():
+    orc = ckks.Oracle(logn=12, n_limbs=3, n_special=1, alpha=1)
+    z = _z(orc.N // 2)
+    assert np.max(np.abs(orc.decode(orc.encode(z)) - z)) < 2.0 ** -30
+
+
+# ---- encryption, keys, operations ------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small():
+    orc = ckks.Oracle(logn=10, n_limbs=3, n_special=2, alpha=2, first_bits=60, mid_bits=40, special_bits=60,
+                      seed=(11, 22, 33, 44))
+    orc.keygen(rot_steps=[1, 2, 4, 8, 16, 32, 64, 128, 256, -1, 3], relin=True)
+    return orc
+
+
+def _noise(orc, ct, pt):
+    d = C.vsub(orc.decrypt(ct).m, pt.m, orc.q[: ct.level])
+    return max(abs(int(v)) for v in ckks.crt_centered(d, orc.q[: ct.level]))
+
+
+def test_encrypt_noise_bounds(small):
+    orc = small
+    pt = orc.encode(_z(orc.N // 2))
+    assert _noise(orc, orc.encrypt_sk(pt, 5), pt) <= 19  # |e| <= 19 by the tail cut
+    bound_pk = 6 * 3.2 * math.sqrt(1 + 4 * orc.N / 3)
+    assert _noise(orc, orc.encrypt_pk(pt, 6), pt) <= bound_pk
+    for lvl in (1, 2):
+        ptl = orc.encode(_z(8), level=lvl)
+        assert _noise(orc, orc.encrypt_sk(ptl, 7), ptl) <= 19
+
+
+def _ks_bound(orc, l):
+    beta = -(-l // orc.alpha)
+    qj = [math.prod(orc.q[j * orc.alpha: min((j + 1) * orc.alpha, l)]) for j in range(beta)]
+    return orc.N * 19 * orc.alpha * sum(qj) / orc.Pprod + orc.N * orc.k + orc.k + 1
+
+
+@pytest.mark.parametrize("l", [1, 2, 3])
+def test_keyswitch_equation(small, l):
+    """u0 + u1 s = d s' + small, for the relinearisation key (s' = s^2) and a
+    rotation key (s' = s(X^g)); the error obeys the analytic bound."""
+    orc = small
+    q = orc.q[:l]
+    s = C.reduce_signed(orc.s, q)
+    d = np.stack([rng.integers(0, qi, orc.N, dtype=np.uint64) for qi in q])
+    for key_id, sp in ((0, C.polymul(s, s, q)), (5, C.automorph(s, q, 5))):
+        u0, u1 = orc.keyswitch(d, key_id)
+        err = C.vsub(C.vadd(u0, C.polymul(u1, s, q), q), C.polymul(d, sp, q), q)
+        e = max(abs(int(v)) for v in ckks.crt_centered(err, q))
+        assert e <= _ks_bound(orc, l), (key_id, e)
+
+
+def test_operations_slotwise(small):
+    orc = small
+    za, zb = _z(orc.N // 2), _z(orc.N // 2)
+    a, b = orc.encrypt_sk(orc.encode(za), 1), orc.encrypt_pk(orc.encode(zb), 2)
+    dec = lambda ct: orc.decode(orc.decrypt(ct))  # noqa: E731
+    assert np.max(np.abs(dec(orc.add(a, b)) - (za + zb))) < 2 ** -20
+    assert np.max(np.abs(dec(orc.sub(a, b)) - (za - zb))) < 2 ** -20
+    assert np.max(np.abs(dec(orc.add_plain(a, orc.encode(zb))) - (za + zb))) < 2 ** -20
+    assert np.max(np.abs(dec(orc.mul_plain(a, orc.encode(zb))) - za * zb)) < 2 ** -20
+    m = orc.mul_relin(a, b)
+    assert m.scale == 2.0 ** 80
+    assert np.max(np.abs(dec(m) - za * zb)) < 2 ** -20
+    r = orc.rescale(m)
+    assert r.level == 2 and r.scale == 2.0 ** 80 / orc.q[2]
+    assert np.max(np.abs(dec(r) - za * zb)) < 2 ** -20
+    for step in (1, 3, -1, 256):
+        assert np.max(np.abs(dec(orc.rotate(a, step)) - np.roll(za, -step))) < 2 ** -20
+
+
+def test_total_sum_closed_form(small):
+    orc = small
+    z = _z(orc.N // 2)
+    ct = orc.total_sum(orc.encrypt_sk(orc.encode(z), 9))
+    got = orc.decode(orc.decrypt(ct))
+    assert np.max(np.abs(got - z.sum())) < 2 ** -20 * orc.N
+
+
+def test_fasttext_single_token_and_encrypted_sequence(small):
+    orc = small
+    t = orc.N // 2
+    m, n, c = t, 4, 3
+    H = rng.normal(0, 0.1, (m, n))
+    O = rng.normal(0, 0.1, (n, c))
+    # single-token document: s = H_k O exactly
+    v = np.zeros(m)
+    v[17] = 1.0
+    assert np.allclose(fasttext.plain_scores(v, H, O), H[17] @ O, rtol=0, atol=1e-15)
+    # a normalised count vector through the encrypted sequence (SK-encrypted client data)
+    ids = rng.integers(0, m, 40)
+    v = np.bincount(ids, minlength=m) / 40.0
+    l = orc.L
+    v_ct = [orc.encrypt_sk(orc.encode(v, level=l), 21)]
+    Hp = fasttext.pack_H(H, t)
+    Op = fasttext.pack_O(O, t)
+    H_pts = [[orc.encode(Hp[j, 0], level=l)] for j in range(n)]
+    O_pts = [orc.encode(Op[j], level=l - 1) for j in range(n)]
+    S = fasttext.encrypted_scores(orc, v_ct, H_pts, O_pts)
+    assert S.level == l - 2
+    got = orc.decode(orc.decrypt(S))[:c].real
+    assert np.max(np.abs(got - fasttext.plain_scores(v, H, O))) < 2 ** -20
