@@ -1,0 +1,325 @@
+"""Benchmark of the GB300 RNS-CKKS hot path (PrivFT, arXiv 1908.06972).
+
+Workload (one step): a batch of 64 ciphertexts at N = 2^16 on a 30-prime chain
+(q_0: 60 bits, q_1..q_29: 50 bits; 4 special primes of 60 bits; digits of 4 primes),
+levels drawn uniformly from 5..30, each put through HMUL + relinearisation followed by
+a chain of 16 power-of-two rotations (steps 2^0 .. 2^14 and -1).  The batched path
+issues each stage once for the whole batch (keys read once per level group); the
+plain path issues every op for every ciphertext separately.
+
+Output: one JSON line (rank 0).  `value` is HE mult+relin per second of the batched
+path with inputs resident in HBM (each counted mult+relin carries its 16 rotations);
+`e2e` measures the same through the C ABI from host buffers (pft_ct_import H2D,
+the ops, pft_ct_export D2H of the 64 results) inside the timed region.
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+LOGN, L, K_SP, ALPHA = 16, 30, 4, 4
+FIRST, MID, SPECIAL = 60, 50, 60
+SCALE = 2.0 ** 50
+BATCH = 64
+STEPS_ROT = [1 << i for i in range(15)] + [-1]
+SEED = (0x5EED0001, 0x5EED0002, 0x5EED0003, 0x5EED0004)
+WORKLOAD = ("N=2^16, 30 limbs (60 + 29x50 bits) + 4 special (60 bits), digits of 4 primes; "
+            "batch 64 ciphertexts at levels U{5..30}; per ciphertext mul_relin then 16 chained "
+            "rotations (2^0..2^14, -1)")
+# ALU roofline (derivation in the design doc): 152 SMs x 64 32-bit IMAD per SM per clock x 2.07 GHz,
+# at 10 IMAD per 64-bit Shoup butterfly multiply.
+SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 10
+
+
+def levels():
+    rng = np.random.default_rng(20241203)
+    return [int(x) for x in rng.integers(5, 31, BATCH)]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- GPU arm ------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    import paper_1908_06972_gb300 as pft
+    from paper_1908_06972_gb300 import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pft.build()
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    pft.pft_keygen(ctx, STEPS_ROT, True)
+    lv = levels()
+    n = 1 << LOGN
+    A, B = [], []
+    for i, l in enumerate(lv):
+        pa = pft.pft_encode(ctx, synth.slots(1000 + i + 7919 * rank, 256), SCALE, l)
+        pb = pft.pft_encode(ctx, synth.slots(5000 + i + 7919 * rank, 256), SCALE, l)
+        A.append(pft.pft_encrypt(ctx, pa, pft.PFT_ENC_SK, 2 * i))
+        B.append(pft.pft_encrypt(ctx, pb, pft.PFT_ENC_SK, 2 * i + 1))
+        pft.pft_pt_destroy(pa)
+        pft.pft_pt_destroy(pb)
+    C = [pft.pft_ct_create(ctx) for _ in range(BATCH)]
+
+    def step_batched(a, b, c):
+        pft.pft_mul_relin_batch(ctx, a, b, c)
+        for s in STEPS_ROT:
+            pft.pft_rotate_batch(ctx, c, s, c)
+
+    def step_plain(a, b, c):
+        for i in range(BATCH):
+            pft.pft_mul_relin(ctx, a[i], b[i], c[i])
+            for s in STEPS_ROT:
+                pft.pft_rotate(ctx, c[i], s, c[i])
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step_batched(A, B, C)
+    # timed region: batched path, dominant kernel family timed with events on the library stream
+    pft.pft_prof_start(args.roofline_kernel)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: step_batched(A, B, C), args.steps)
+    k_ms, k_launches, all_launches, k_work = pft.pft_prof_stop()
+    ms_step = ms / args.steps
+    value = BATCH * world * args.steps / (ms / 1e3)
+
+    # plain one-op-per-launch path (same GPU, same inputs)
+    plain = None
+    if args.plain_steps > 0:
+        step_plain(A, B, C)
+        pm = timed(lambda: step_plain(A, B, C), args.plain_steps)
+        plain = BATCH * world * args.plain_steps / (pm / 1e3)
+
+    # end to end through the C ABI from pinned host buffers
+    host_in = []
+    for i in range(BATCH):
+        for h in (A[i], B[i]):
+            arr = torch.empty((2, lv[i], n), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+            pft.pft_ct_export(ctx, h, arr)
+            host_in.append((arr, pft.pft_ct_scale(h)))
+    host_out = [torch.empty((2, l - 0, n), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64) for l in lv]
+    h2d = sum(a.nbytes for a, _ in host_in)
+    d2h = sum(o.nbytes for o in host_out)
+
+    def step_e2e():
+        ins = [pft.pft_ct_import(ctx, arr, sc) for arr, sc in host_in]
+        a, b = ins[0::2], ins[1::2]
+        step_batched(a, b, C)
+        for i in range(BATCH):
+            pft.pft_ct_export(ctx, C[i], host_out[i])
+        for h in ins:
+            pft.pft_ct_destroy(h)
+
+    step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = BATCH * world * args.steps / e2e_s
+
+    # roofline of the timed kernel family
+    roof = None
+    if k_ms > 0 and args.roofline_kernel.startswith("ntt"):
+        achieved = k_work / (k_ms / 1e3) / 1e9  # Gbutterfly/s (one Shoup mulmod each)
+        peak = SMS * IMAD_PER_CLK * SM_MHZ_MAX * 1e6 / IMAD_PER_MULMOD / 1e9
+        roof = {"bound": "alu", "kernel": args.roofline_kernel, "achieved": round(achieved, 2),
+                "peak": round(peak, 2), "unit": "Gmulmod/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "launches": k_launches, "kernel_ms": round(k_ms, 3),
+                "kernel_share_of_step": round(k_ms / ms, 4),
+                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 10 IMAD per Shoup mulmod"}
+    elif k_ms > 0:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        achieved = k_work / (k_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": None, "launches": k_launches, "kernel_ms": round(k_ms, 3),
+                "kernel_share_of_step": round(k_ms / ms, 4)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_level)
+
+    out = {"metric": "HE mult+relin/s at N=2^16; enc. fastText inferences/s, batched vs plain",
+           "value": round(value, 3), "unit": "mult+relin/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "batch": BATCH, "levels_mean": round(float(np.mean(lv)), 2),
+                      "l2": "inputs larger than L2 (%.1f GB of ciphertexts)" % (h2d / 1e9),
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "plain_value": round(plain, 3) if plain else None,
+           "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h},
+           "gpu_launches": int(all_launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out))
+    for h in A + B + C:
+        pft.pft_ct_destroy(h)
+    pft.pft_ctx_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---- CPU oracle -------------------------------------------------------------------------------------
+def cpu_baseline(level):
+    """The oracle on a bounded sample: one ciphertext at `level` through mul_relin and one
+    rotation (keys generated for a chain truncated at `level`, which is the slice of the full
+    keys a level-`level` ciphertext touches); a unit = mul_relin + 16 rotations."""
+    from oracle import ckks
+    from paper_1908_06972_gb300 import synth
+
+    orc = ckks.Oracle(LOGN, level, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    orc.keygen([1], True)
+    a = orc.encrypt_sk(orc.encode(synth.slots(1, 256), level=level), 1)
+    b = orc.encrypt_sk(orc.encode(synth.slots(2, 256), level=level), 2)
+    t0 = time.perf_counter()
+    c = orc.mul_relin(a, b)
+    t1 = time.perf_counter()
+    orc.rotate(c, 1)
+    t2 = time.perf_counter()
+    unit_s = (t1 - t0) + 16 * (t2 - t1)
+    cores = len(os.sched_getaffinity(0))
+    return {"value": round(1.0 / unit_s, 6), "unit": "mult+relin/s", "cores": cores, "kind": "oracle",
+            "sample": "1 ciphertext at level %d (workload mean 17.5): mul_relin + 1 rotation timed, "
+                      "unit = mul_relin + 16 rotations (%.1f s measured)" % (level, t2 - t0)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    times = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.cpu_level)
+    for _ in range(args.steps):
+        r = cpu_baseline(args.cpu_level)
+        times.append(1.0 / r["value"])
+    value = len(times) / sum(times)
+    out = {"impl": "reference", "metric": "HE mult+relin/s at N=2^16; enc. fastText inferences/s, batched vs plain",
+           "value": round(value, 6), "unit": "mult+relin/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "batch": BATCH},
+           "cpu_baseline": {"value": round(value, 6), "unit": "mult+relin/s", "kind": "oracle",
+                            "cores": len(os.sched_getaffinity(0)), "sample": r["sample"]},
+           "e2e": {"value": round(value, 6), "unit": "mult+relin/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--roofline-kernel", default="ntt")
+    ap.add_argument("--cpu-level", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

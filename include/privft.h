@@ -1,0 +1,258 @@
+/*
+ * privft.h -- C ABI of the GB300 RNS-CKKS library behind encrypted fastText
+ * (PrivFT, arXiv 1908.06972).
+ *
+ * Scheme (Sec. 2.3 of the paper): R_q = Z_q[X]/(X^N+1), q = q_0 q_1 ... q_{l-1}
+ * a chain of word-sized NTT-friendly primes (here at most 60 bits each, so well
+ * below 2^62), CKKS encoding of N/2 complex slots, KEYGEN/ENC/DEC, HADD, HMUL
+ * (+ relinearisation), HADDPLAIN, HMULPLAIN, RESCALE (Eq. 1, Algorithm 3) and
+ * ROTATE (Sec. 2.3 and the rotation discussion of Sec. 5.3).  The inference
+ * entry point follows Sec. 3.1 (Fig. 3, Algorithm 2).
+ *
+ * Conventions shared by every call
+ *   - Every function returns an int status: PFT_OK (0) or a PFT_ERR_* code.
+ *     pft_last_error(ctx) gives a text for the last failure on that context.
+ *   - "level" l = number of RNS limbs a ciphertext/plaintext carries (1..L),
+ *     as in the paper's q_l = prod_{i<=l} p_i.
+ *   - Handles (pft_ctx, pft_ct, pft_pt, pft_ft_model) are created and destroyed
+ *     by the library.  Their device memory comes from the allocator given at
+ *     context creation (NULL -> cudaMallocAsync/cudaFreeAsync on the context's
+ *     stream).
+ *   - All device work is issued on the context stream (pft_set_stream; default
+ *     the legacy default stream) and is asynchronous; calls that return host
+ *     data (pft_decode, pft_ct_export, pft_pt_export) synchronise that stream.
+ *   - An output handle may alias an input handle.
+ *   - Device layout of a ciphertext: [2][l][N] uint64, limb-major, each limb in
+ *     the evaluation ("NTT") domain: entry i of limb r holds a(psi_r^(2 brv(i)+1))
+ *     mod q_r, brv the log2(N)-bit reversal, psi_r = x^((q_r-1)/2N) for the
+ *     smallest quadratic non-residue x of q_r.  Export/import use COEFFICIENT
+ *     form, canonical residues in [0, q_r).
+ *   - Primes, when not given, follow the rule: for a bit size b, the candidates
+ *     2^b - j*2N + 1, j = 1, 2, ..., that are prime, in that (descending) order;
+ *     q_0 takes the first of its size, q_1..q_{L-1} the next ones of theirs, the
+ *     special primes the next unused ones of theirs.
+ *   - Randomness: a ChaCha20 (RFC 8439) counter-mode stream keyed by the
+ *     256-bit seed, nonce (domain, object, sub); see the sampler notes at
+ *     pft_keygen.
+ */
+#ifndef PRIVFT_H
+#define PRIVFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    PFT_OK = 0,
+    PFT_ERR_ARG = 1,            /* bad argument (NULL, size, range) */
+    PFT_ERR_LEVEL_MISMATCH = 2, /* operands at different levels (Sec. 2.3: same level required) */
+    PFT_ERR_SCALE_MISMATCH = 3, /* add of operands whose scales differ */
+    PFT_ERR_NO_KEY = 4,         /* relinearisation / rotation key not generated */
+    PFT_ERR_OOM = 5,            /* the allocator returned NULL */
+    PFT_ERR_CUDA = 6,           /* a CUDA runtime call or launch failed */
+    PFT_ERR_TIMEOUT = 7,        /* a bounded device wait expired */
+    PFT_ERR_SECURITY = 8,       /* log2(QP) above the 128-bit bound without PFT_ALLOW_INSECURE */
+    PFT_ERR_NOT_IMPLEMENTED = 9
+};
+
+/* ---- opaque handles ------------------------------------------------------ */
+typedef struct pft_ctx pft_ctx;
+typedef struct pft_ct pft_ct;             /* ciphertext (c0, c1) */
+typedef struct pft_pt pft_pt;             /* plaintext mu */
+typedef struct pft_ft_model pft_ft_model; /* packed fastText weights (H, O) */
+
+/* Device allocator.  alloc(bytes, stream, user) returns device memory usable on
+ * `stream` (NULL on failure); free(ptr, stream, user) releases it once the work
+ * already queued on `stream` no longer needs it. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, void* stream, void* user);
+    void* user;
+} pft_allocator;
+
+#define PFT_ALLOW_INSECURE 1 /* pft_params.flags: accept log2(QP) above the 128-bit table */
+
+/* Encryption parameters (SETUP, Sec. 2.3 and Sec. 5.4).
+ *   log_n        log2 N, 4..16
+ *   n_limbs      L, number of ciphertext primes at the top level (1..60)
+ *   n_special    k, special primes for key switching (1..8)
+ *   alpha        primes per key-switching digit (1..8); beta = ceil(l/alpha) digits
+ *   first_bits   bit size of q_0 (20..60)
+ *   mid_bits     bit size of q_1..q_{L-1} (20..60)
+ *   special_bits bit size of the special primes (20..60)
+ *   primes       optional explicit chain [n_limbs + n_special] (q's then p's), or NULL
+ *   scale        default encoding scale Delta = 2^rho
+ *   seed         256-bit sampler key
+ *   sigma        Gaussian standard deviation (the paper uses 3.2); tail cut at floor(6 sigma)
+ *   flags        PFT_ALLOW_INSECURE
+ * Security table (max log2(QP), uniform ternary secret, 128-bit): N=2^10: 27,
+ * 2^11: 54, 2^12: 109, 2^13: 218, 2^14: 438, 2^15: 881, 2^16: 1772. */
+typedef struct {
+    int log_n;
+    int n_limbs;
+    int n_special;
+    int alpha;
+    int first_bits;
+    int mid_bits;
+    int special_bits;
+    const uint64_t* primes;
+    double scale;
+    uint64_t seed[4];
+    double sigma;
+    int flags;
+} pft_params;
+
+/* ---- context ------------------------------------------------------------- */
+/* Create a context: primes, transform tables, basis-conversion tables on the
+ * device.  `alloc` may be NULL.  Errors: ARG, SECURITY, OOM, CUDA. */
+int pft_ctx_create(const pft_params* params, const pft_allocator* alloc, pft_ctx** out);
+int pft_ctx_destroy(pft_ctx* ctx);
+/* Set the cudaStream_t (passed as void*) on which all later work is queued. */
+int pft_set_stream(pft_ctx* ctx, void* stream);
+const char* pft_last_error(pft_ctx* ctx);
+/* Chain info: N, L, k, alpha; primes_out (may be NULL) receives [L + k] primes. */
+int pft_ctx_info(pft_ctx* ctx, int* n, int* n_limbs, int* n_special, int* alpha, uint64_t* primes_out);
+
+/* ---- host-only utilities (no GPU needed) --------------------------------- */
+/* First `count` primes of `bits` bits congruent to 1 mod 2^(log_n+1), by the rule
+ * above, skipping the `n_exclude` values in `exclude`. */
+int pft_gen_primes(int log_n, int bits, int count, const uint64_t* exclude, int n_exclude, uint64_t* out);
+/* The 32-bit cumulative table of |X| used by the Gaussian sampler:
+ * out[j] = floor(2^32 P(|X| <= j)), j < tail, for P(X=x) ~ exp(-x^2/(2 sigma^2))
+ * on [-tail, tail], tail = floor(6 sigma).  Returns the number of entries via n_out. */
+int pft_gauss_cdt(double sigma, uint32_t* out, int cap, int* n_out);
+
+/* ---- launch accounting (diagnostics) --------------------------------------
+ * pft_prof_start(prefix): from now on count every kernel launch of the library
+ * and bracket each launch whose kernel name starts with `prefix` (e.g. "ntt",
+ * "ks_inner", "bconv"; "" times none) with CUDA events on its stream.
+ * pft_prof_stop: waits for the last timed launch, returns the summed device time
+ * (ms) of the timed launches, their number, the number of all launches since
+ * pft_prof_start, and the timed launches' summed algorithmic work (butterflies
+ * for "ntt*" kernels, bytes read + written for the memory-bound ones, 0 where
+ * not counted), then switches timing off.  Process-wide, not thread-safe.
+ * Any argument may be NULL. */
+int pft_prof_start(const char* prefix);
+int pft_prof_stop(double* ms, long long* timed_launches, long long* all_launches, double* work);
+
+/* ---- keys (KEYGEN, Sec. 2.3; key switching keys of the relinearisation and
+ * ROTATE footnote) ---------------------------------------------------------
+ * Sampler streams (64-bit word w = block w/8, 32-bit words 2(w%8) | 2(w%8)+1 << 32):
+ *   secret s        ternary, domain 1 (word c mod 3 - 1)
+ *   pk a / e        domain 2 (sub = limb) / domain 3
+ *   switching key   a_j: domain 4, object = key id, sub = 256 j + basis row;
+ *                   e_j: domain 5, object = key id, sub = j
+ *   key id          0 for relinearisation, the Galois element g for rotations
+ *   uniform mod q   words 2c, 2c+1 as a 128-bit value, reduced mod q
+ *   Gaussian        magnitude = number of table entries the top 32 bits of
+ *                   word c reach, sign = its lowest bit
+ * Keys: b_j = -a_j s + e_j + [limb in digit j] P s', with s' = s^2 (relin) or
+ * s(X^g) (rotation by step r, g = 5^r mod 2N), P = product of special primes.
+ * Generates s, pk, the relinearisation key (want_relin != 0) and one rotation key
+ * per entry of rot_steps (duplicates and identity steps are skipped). */
+int pft_keygen(pft_ctx* ctx, const int32_t* rot_steps, int n_steps, int want_relin);
+/* Add rotation keys after pft_keygen. */
+int pft_add_rotation_keys(pft_ctx* ctx, const int32_t* rot_steps, int n_steps);
+/* Export switching key `key_id` (0 = relin, else a Galois element) in coefficient
+ * form, [beta_max][2][L + k][N] uint64, into host memory `out` of `n` words. */
+int pft_key_export(pft_ctx* ctx, uint32_t key_id, uint64_t* out, size_t n);
+/* Export the secret s as int64[N] coefficients (-1, 0, 1). */
+int pft_secret_export(pft_ctx* ctx, int64_t* out, size_t n);
+
+/* ---- plaintexts / ciphertexts --------------------------------------------- */
+int pft_ct_create(pft_ctx* ctx, pft_ct** out); /* empty handle (level 0) */
+int pft_ct_destroy(pft_ct* ct);
+int pft_pt_destroy(pft_pt* pt);
+int pft_ct_level(const pft_ct* ct, int* level);
+int pft_ct_scale(const pft_ct* ct, double* scale);
+int pft_pt_level(const pft_pt* pt, int* level);
+/* Device pointer of the [2][l][N] buffer (evaluation domain), for zero-copy use. */
+int pft_ct_data(const pft_ct* ct, uint64_t** dev_ptr);
+
+/* ENCODE (Sec. 2.3): re_im = [2 * n_slots] doubles (re, im interleaved), n_slots <=
+ * N/2 (the rest zero); mu_k = round half away from zero of
+ * (2/N) Re sum_j scale z_j omega^(-(5^j mod 2N) k), omega = exp(i pi/N), computed
+ * on the host in FP64 with an FFT; |mu_k| >= 2^62 -> PFT_ERR_ARG. */
+int pft_encode(pft_ctx* ctx, const double* re_im, int n_slots, double scale, int level, pft_pt** out);
+/* DECODE: z_j = mu(omega^(5^j mod 2N)) / scale with mu's CRT-centered coefficients. */
+int pft_decode(pft_ctx* ctx, const pft_pt* pt, double* re_im_out, int n_slots);
+/* Plaintext from / to coefficient-form residues [level][N] (canonical < q_r). */
+int pft_pt_import(pft_ctx* ctx, const uint64_t* coeffs, int level, double scale, pft_pt** out);
+int pft_pt_export(pft_ctx* ctx, const pft_pt* pt, uint64_t* coeffs, size_t n);
+
+#define PFT_ENC_PK 0 /* c0 = v b + mu + e0, c1 = v a + e1 (v ternary, domain 8; e0, e1 domains 9, 10) */
+#define PFT_ENC_SK 1 /* c0 = -a s + mu + e, c1 = a (a domain 6, sub = limb; e domain 7) */
+/* ENC (Sec. 2.3, reading of the garbled formula as above); object id = nonce. */
+int pft_encrypt(pft_ctx* ctx, const pft_pt* pt, int mode, uint32_t nonce, pft_ct** out);
+/* DEC (Sec. 2.3): mu = c0 + c1 s. */
+int pft_decrypt(pft_ctx* ctx, const pft_ct* ct, pft_pt** out);
+/* Ciphertext from / to coefficient form [2][level][N] (canonical < q_r). */
+int pft_ct_import(pft_ctx* ctx, const uint64_t* coeffs, int level, double scale, pft_ct** out);
+int pft_ct_export(pft_ctx* ctx, const pft_ct* ct, uint64_t* coeffs, size_t n);
+
+/* ---- homomorphic operations (Sec. 2.3) ------------------------------------
+ * `out` must be a handle from pft_ct_create / an op; it is resized as needed. */
+int pft_add(pft_ctx* ctx, const pft_ct* a, const pft_ct* b, pft_ct* out);       /* HADD */
+int pft_sub(pft_ctx* ctx, const pft_ct* a, const pft_ct* b, pft_ct* out);
+int pft_add_plain(pft_ctx* ctx, const pft_ct* a, const pft_pt* p, pft_ct* out); /* HADDPLAIN */
+int pft_mul_plain(pft_ctx* ctx, const pft_ct* a, const pft_pt* p, pft_ct* out); /* HMULPLAIN, scale_a*scale_p */
+/* HMUL followed by relinearisation: tensor (c00c10, c00c11+c01c10, c01c11), then
+ * hybrid key switching of the third part (ModUp: fast basis conversion of each
+ * alpha-prime digit to the other primes; inner product with the key; ModDown:
+ * (x_Q - BConv_P->Q(x_P)) P^-1).  Same level required. */
+int pft_mul_relin(pft_ctx* ctx, const pft_ct* a, const pft_ct* b, pft_ct* out);
+/* RESCALE (Eq. 1 / Algorithm 3 with the rounding of Sec. 2.3): drop q_{l-1},
+ * c'_k = (c_k + h - r) q_{l-1}^-1 mod q_k, r = (c_{l-1} + h) mod q_{l-1},
+ * h = floor(q_{l-1}/2); scale /= q_{l-1}. */
+int pft_rescale(pft_ctx* ctx, const pft_ct* a, pft_ct* out);
+/* ROTATE: slot j of out = slot j+step of a (g = 5^step mod 2N), automorphism then
+ * key switching with the rotation key of g.  Steps with no key -> PFT_ERR_NO_KEY. */
+int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
+
+/* Batched forms: one launch per stage over all B ciphertexts (levels may differ
+ * between ciphertexts; pairs must match).  Keys are read once per level group. */
+int pft_add_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out);
+int pft_mul_plain_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_pt* const* p, int B, pft_ct* const* out);
+int pft_mul_relin_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out);
+int pft_rescale_batch(pft_ctx* ctx, const pft_ct* const* a, int B, pft_ct* const* out);
+int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out);
+
+/* ---- raw transforms on caller memory (kernel-level access) ----------------
+ * data: device buffer of n_polys polynomials [n_polys][n_limbs][N], limb r under
+ * prime r of the chain (r < L + k; rows >= L are the special primes).  inverse = 0:
+ * coefficient -> evaluation layout above; 1: back. In place. */
+int pft_ntt(pft_ctx* ctx, uint64_t* data, int n_polys, int n_limbs, int inverse);
+
+/* ---- encrypted fastText inference (Sec. 3.1, Fig. 3, Algorithm 2) ---------
+ * Model: H (m x n, row-major doubles) packed vertically -- plaintext (j, i) holds
+ * column j, vocabulary rows i*t .. i*t+t-1, t = N/2 -- at `level`, scale Delta;
+ * O (n x c) packed horizontally -- plaintext j holds row j in slots 0..c-1 -- at
+ * level-1, scale Delta. */
+int pft_ft_model_create(pft_ctx* ctx, const double* H, const double* O, int m, int n, int c, int level,
+                        pft_ft_model** out);
+/* The same from already encoded plaintexts: H_pts[j * n_chunks + i], O_pts[j]. */
+int pft_ft_model_import(pft_ctx* ctx, const pft_pt* const* H_pts, const pft_pt* const* O_pts, int m, int n,
+                        int c, pft_ft_model** out);
+int pft_ft_model_destroy(pft_ft_model* model);
+/* Scores of one document: v = ceil(m/t) ciphertexts at the model level (the
+ * client's count vector, already divided by w).  Sequence: h_j = TotalSum(sum_i
+ * v_i * H_{j,i}) with TotalSum rotating by 2^i, i = 0..log2(t)-1 (Algorithm 2),
+ * rescale; s = sum_j h_j * O_j; rescale.  Needs rotation keys for 2^i.
+ * `scores` receives s in slots 0..c-1 at level-2. */
+int pft_fasttext_infer(pft_ctx* ctx, const pft_ft_model* model, const pft_ct* const* v, int n_chunks,
+                       pft_ct* scores);
+/* B documents: v[b * n_chunks + i]; all columns of all documents share each
+ * rotation key read. */
+int pft_fasttext_infer_batch(pft_ctx* ctx, const pft_ft_model* model, const pft_ct* const* v, int n_chunks,
+                             int B, pft_ct* const* scores);
+/* Encrypted minibatch training step (Algorithm 5): not implemented yet. */
+int pft_fasttext_train_step(pft_ctx* ctx, pft_ft_model* model, const pft_ct* const* docs, int n_docs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRIVFT_H */

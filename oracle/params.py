@@ -83,8 +83,9 @@ def root_2n(q, logn):
     return psi
 
 
-def gauss_cdt(sigma="3.2", tail=19):
-    """32-bit cumulative table of |X| for the discrete Gaussian on [-tail, tail].
+def gauss_cdt(sigma="3.2"):
+    """32-bit cumulative table of |X| for the discrete Gaussian on [-tail, tail],
+    tail = floor(6 sigma) (19 for sigma = 3.2).
 
     P(X = x) is proportional to exp(-x^2 / (2 sigma^2)); T[j] = floor(2^32 *
     P(|X| <= j)) for j = 0 .. tail-1.  A sample's magnitude is the number of
@@ -92,6 +93,7 @@ def gauss_cdt(sigma="3.2", tail=19):
     """
     getcontext().prec = 60
     s = Decimal(sigma)
+    tail = int((6 * s).to_integral_value(rounding="ROUND_FLOOR"))
     rho = [(-(Decimal(k * k)) / (2 * s * s)).exp() for k in range(tail + 1)]
     z = rho[0] + 2 * sum(rho[1:])
     out, acc = [], rho[0]

@@ -1,0 +1,1457 @@
+// RNS-CKKS evaluator on one GPU: context and tables, keys, encryption, the
+// homomorphic operations of Sec. 2.3, hybrid key switching, rescale (Eq. 1 /
+// Algorithm 3 with rounding) and the encrypted fastText inference of Sec. 3.1.
+// Host code only orders kernel launches on the context stream; every step of the
+// arithmetic runs in the kernels of ntt.cu and poly.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+
+#include "pft_internal.h"
+
+using namespace pft;
+
+// ---- handles ---------------------------------------------------------------------------
+struct pft_ctx {
+    pft_params prm;
+    int logn = 0, n = 0, L = 0, k = 0, alpha = 0, beta_max = 0;
+    std::vector<u64> primes;  // q_0..q_{L-1}, p_0..p_{k-1}
+    pft_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    DevTables tabs{};
+    std::vector<void*> owned;  // table buffers
+    // basis-conversion tables: modup[(l-1) * beta_max + j], moddown[l-1] (device offsets)
+    std::vector<const u64*> modup_tab, moddown_tab;
+    const u64* moddown_consts = nullptr;           // [L][3] {0, P^-1, shoup}
+    std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {h mod q_k, p^-1, shoup}
+    std::vector<const u64*> pmodq_consts;          // digit j -> [alpha][3] {0, P mod q_m, shoup}
+    std::vector<u64> P_mod_q;
+    std::vector<u32> cdt;
+    // keys
+    bool have_sk = false;
+    u64* s_ntt = nullptr;  // [L+k][N]
+    std::vector<i64> s_coeff;
+    u64* pk = nullptr;  // [2][L][N]  (b, a)
+    std::map<u32, u64*> keys;
+};
+
+struct pft_ct {
+    pft_ctx* ctx = nullptr;
+    u64* data = nullptr;
+    size_t cap = 0;  // words
+    int level = 0;
+    double scale = 1.0;
+};
+struct pft_pt {
+    pft_ctx* ctx = nullptr;
+    u64* data = nullptr;
+    size_t cap = 0;
+    int level = 0;
+    double scale = 1.0;
+};
+struct pft_ft_model {
+    pft_ctx* ctx = nullptr;
+    int m = 0, n = 0, c = 0, chunks = 0, level = 0;
+    std::vector<pft_pt*> H, O;  // owned copies
+};
+
+namespace pft {
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+void check_cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) fail(PFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace pft
+
+// ---- memory --------------------------------------------------------------------------
+static void* dalloc(pft_ctx* c, size_t bytes) {
+    if (bytes == 0) return nullptr;
+    void* p = nullptr;
+    if (c->has_alloc) {
+        p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+        if (e != cudaSuccess) p = nullptr;
+    }
+    if (!p) fail(PFT_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    return p;
+}
+static void dfree(pft_ctx* c, void* p) {
+    if (!p) return;
+    if (c->has_alloc) c->alloc.free(p, (void*)c->stream, c->alloc.user);
+    else cudaFreeAsync(p, c->stream);
+}
+struct Scratch {
+    pft_ctx* c;
+    void* p;
+    Scratch(pft_ctx* c_, size_t bytes) : c(c_), p(dalloc(c_, bytes)) {}
+    ~Scratch() { dfree(c, p); }
+    u64* u() const { return (u64*)p; }
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+};
+template <class T>
+static T* upload(pft_ctx* c, Scratch& s, const std::vector<T>& v) {
+    PFT_CUDA(cudaMemcpyAsync(s.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return (T*)s.p;
+}
+static void ensure_ct(pft_ctx* c, pft_ct* ct, int level) {
+    const size_t need = (size_t)2 * level * c->n;
+    if (ct->cap < need) {
+        dfree(c, ct->data);
+        ct->data = nullptr;
+        ct->cap = 0;
+        ct->data = (u64*)dalloc(c, need * 8);
+        ct->cap = need;
+    }
+    ct->level = level;
+}
+static void ensure_pt(pft_ctx* c, pft_pt* pt, int level) {
+    const size_t need = (size_t)level * c->n;
+    if (pt->cap < need) {
+        dfree(c, pt->data);
+        pt->data = nullptr;
+        pt->cap = 0;
+        pt->data = (u64*)dalloc(c, need * 8);
+        pt->cap = need;
+    }
+    pt->level = level;
+}
+
+// ---- polynomial references ------------------------------------------------------------
+static PolyRef ref(u64* p, int nlimbs, int first = 0, int split = -1, int base2 = 0) {
+    PolyRef r;
+    r.ptr = p;
+    r.nlimbs = (uint16_t)nlimbs;
+    r.first = (uint16_t)first;
+    r.split = (uint16_t)(split < 0 ? nlimbs : split);
+    r.base2 = (uint16_t)base2;
+    return r;
+}
+static PolySet mkset(const std::vector<PolyRef>& v, size_t a, size_t b) {
+    PolySet s;
+    s.count = (int)(b - a);
+    s.max_limbs = 0;
+    for (size_t i = a; i < b; i++) {
+        s.p[i - a] = v[i];
+        s.max_limbs = std::max<int>(s.max_limbs, v[i].nlimbs);
+    }
+    return s;
+}
+template <class F>
+static void chunks(size_t n, F f) {
+    for (size_t i = 0; i < n; i += kMaxSet) f(i, std::min(n, i + (size_t)kMaxSet));
+}
+static void ntt_fwd(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
+    chunks(out.size(), [&](size_t a, size_t b) { ntt_forward(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
+}
+static void ntt_inv(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
+    chunks(out.size(), [&](size_t a, size_t b) { ntt_inverse(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
+}
+static void ew(pft_ctx* c, EwOp op, const std::vector<PolyRef>& a, const std::vector<PolyRef>& b,
+               const std::vector<PolyRef>& out) {
+    chunks(out.size(), [&](size_t x, size_t y) {
+        ew_binary(c->tabs, op, mkset(a, x, y), mkset(b.empty() ? a : b, x, y), mkset(out, x, y), c->stream);
+    });
+}
+static void subscale(pft_ctx* c, const std::vector<PolyRef>& x, const std::vector<PolyRef>* y,
+                     const std::vector<PolyRef>* acc, const std::vector<PolyRef>& out, const u64* consts) {
+    chunks(out.size(), [&](size_t a, size_t b) {
+        PolySet sx = mkset(x, a, b), so = mkset(out, a, b);
+        PolySet sy, sa;
+        if (y) sy = mkset(*y, a, b);
+        if (acc) sa = mkset(*acc, a, b);
+        sub_scale(c->tabs, sx, y ? &sy : nullptr, acc ? &sa : nullptr, so, consts, c->stream);
+    });
+}
+// the two polynomials of a ciphertext buffer [2][l][N]
+static PolyRef cpoly(u64* data, int l, int n, int pol) { return ref(data + (size_t)pol * l * n, l); }
+
+// ---- context construction ---------------------------------------------------------------
+static u64 shoup(u64 w, u64 q) { return (u64)(((unsigned __int128)w << 64) / q); }
+static int bitlen(u64 x) { return 64 - __builtin_clzll(x); }
+
+static const int kSecureLogQP[17] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 27, 54, 109, 218, 438, 881, 1772};
+
+static void* tab_alloc(pft_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    PFT_CUDA(cudaMalloc(&p, bytes));
+    c->owned.push_back(p);
+    return p;
+}
+template <class T>
+static T* tab_upload(pft_ctx* c, const std::vector<T>& v) {
+    T* p = (T*)tab_alloc(c, std::max<size_t>(1, v.size()) * sizeof(T));
+    PFT_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+static void build_tables(pft_ctx* c) {
+    const int P = (int)c->primes.size(), n = c->n, logn = c->logn, L = c->L, k = c->k;
+    // primes
+    std::vector<DPrime> dp(P);
+    for (int i = 0; i < P; i++) {
+        const u64 q = c->primes[i];
+        const int s = bitlen(q) - 1;
+        dp[i].q = q;
+        dp[i].mu = (u64)((((unsigned __int128)1) << (64 + s)) / q);
+        dp[i].r64 = (u64)((((unsigned __int128)1) << 64) % q);
+        dp[i].s = (u32)s;
+        dp[i].pad = 0;
+    }
+    c->tabs.logn = logn;
+    c->tabs.n = n;
+    c->tabs.primes = tab_upload(c, dp);
+    // twiddles
+    std::vector<ulonglong2> fwd((size_t)P * n), inv((size_t)P * n), ninv(P), inv1(P);
+    std::vector<u64> pw(n);
+    for (int i = 0; i < P; i++) {
+        const u64 q = c->primes[i];
+        const u64 psi = root_2n_host(q, logn);
+        const u64 psi_inv = invmod_host(psi, q);
+        pw[0] = 1;
+        for (int j = 1; j < n; j++) pw[j] = mulmod_host(pw[j - 1], psi, q);
+        for (int j = 0; j < n; j++) {
+            u32 b = 0;
+            for (int t = 0; t < logn; t++) b |= ((j >> t) & 1) << (logn - 1 - t);
+            const u64 w = pw[b];
+            const u64 wi = b == 0 ? 1 : q - mulmod_host(pw[n - b], 1, q);  // psi^-b = -psi^(N-b)
+            fwd[(size_t)i * n + j] = make_ulonglong2(w, shoup(w, q));
+            inv[(size_t)i * n + j] = make_ulonglong2(wi, shoup(wi, q));
+        }
+        (void)psi_inv;
+        const u64 ni = invmod_host((u64)n % q, q);
+        ninv[i] = make_ulonglong2(ni, shoup(ni, q));
+        const u64 v = mulmod_host(inv[(size_t)i * n + 1].x, ni, q);
+        inv1[i] = make_ulonglong2(v, shoup(v, q));
+    }
+    c->tabs.fwd = tab_upload(c, fwd);
+    c->tabs.inv = tab_upload(c, inv);
+    c->tabs.ninv = tab_upload(c, ninv);
+    c->tabs.inv1ninv = tab_upload(c, inv1);
+
+    // P mod q_m, P^-1 mod q_m
+    c->P_mod_q.assign(L, 0);
+    std::vector<u64> md(3 * (size_t)L);
+    for (int m = 0; m < L; m++) {
+        u64 pm = 1;
+        for (int j = 0; j < k; j++) pm = mulmod_host(pm, c->primes[L + j] % c->primes[m], c->primes[m]);
+        c->P_mod_q[m] = pm;
+        const u64 pi = invmod_host(pm, c->primes[m]);
+        md[3 * m] = 0;
+        md[3 * m + 1] = pi;
+        md[3 * m + 2] = shoup(pi, c->primes[m]);
+    }
+    c->moddown_consts = tab_upload(c, md);
+    // key generation: P mod q_m on the rows of digit j (consts indexed from the digit's first row)
+    for (int j = 0; j < c->beta_max; j++) {
+        std::vector<u64> v;
+        for (int m = j * c->alpha; m < std::min(L, (j + 1) * c->alpha); m++) {
+            v.push_back(0);
+            v.push_back(c->P_mod_q[m]);
+            v.push_back(shoup(c->P_mod_q[m], c->primes[m]));
+        }
+        c->pmodq_consts.push_back(tab_upload(c, v));
+    }
+    // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [ns][l + k] qhat mod target
+    c->modup_tab.assign((size_t)L * c->beta_max, nullptr);
+    for (int l = 1; l <= L; l++) {
+        const int beta = (l + c->alpha - 1) / c->alpha, E = l + k;
+        for (int j = 0; j < beta; j++) {
+            const int lo = j * c->alpha, hi = std::min(l, lo + c->alpha), ns = hi - lo;
+            std::vector<u64> tab(2 * ns + (size_t)ns * E);
+            for (int i = 0; i < ns; i++) {
+                const u64 qi = c->primes[lo + i];
+                u64 h = 1;
+                for (int i2 = 0; i2 < ns; i2++)
+                    if (i2 != i) h = mulmod_host(h, c->primes[lo + i2] % qi, qi);
+                const u64 hinv = invmod_host(h, qi);
+                tab[2 * i] = hinv;
+                tab[2 * i + 1] = shoup(hinv, qi);
+                for (int m = 0; m < E; m++) {
+                    const u64 t = m < l ? c->primes[m] : c->primes[L + m - l];
+                    u64 hm = 1;
+                    for (int i2 = 0; i2 < ns; i2++)
+                        if (i2 != i) hm = mulmod_host(hm, c->primes[lo + i2] % t, t);
+                    tab[2 * ns + (size_t)i * E + m] = hm;
+                }
+            }
+            c->modup_tab[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
+        }
+    }
+    // ModDown tables per level: [k]{phat_inv, shoup}, then [k][l] phat mod q_m
+    c->moddown_tab.assign(L, nullptr);
+    for (int l = 1; l <= L; l++) {
+        std::vector<u64> tab(2 * k + (size_t)k * l);
+        for (int i = 0; i < k; i++) {
+            const u64 pi = c->primes[L + i];
+            u64 h = 1;
+            for (int i2 = 0; i2 < k; i2++)
+                if (i2 != i) h = mulmod_host(h, c->primes[L + i2] % pi, pi);
+            const u64 hinv = invmod_host(h, pi);
+            tab[2 * i] = hinv;
+            tab[2 * i + 1] = shoup(hinv, pi);
+            for (int m = 0; m < l; m++) {
+                const u64 t = c->primes[m];
+                u64 hm = 1;
+                for (int i2 = 0; i2 < k; i2++)
+                    if (i2 != i) hm = mulmod_host(hm, c->primes[L + i2] % t, t);
+                tab[2 * k + (size_t)i * l + m] = hm;
+            }
+        }
+        c->moddown_tab[l - 1] = tab_upload(c, tab);
+    }
+    // rescale constants per level l >= 2: for k' < l-1: {floor(p/2) mod q_k', p^-1, shoup}, p = q_{l-1}
+    c->rescale_consts.assign(L, nullptr);
+    for (int l = 2; l <= L; l++) {
+        const u64 p = c->primes[l - 1];
+        std::vector<u64> v(3 * (size_t)(l - 1));
+        for (int kk = 0; kk < l - 1; kk++) {
+            const u64 q = c->primes[kk];
+            const u64 pinv = invmod_host(p % q, q);
+            v[3 * kk] = (p / 2) % q;
+            v[3 * kk + 1] = pinv;
+            v[3 * kk + 2] = shoup(pinv, q);
+        }
+        c->rescale_consts[l - 1] = tab_upload(c, v);
+    }
+}
+
+// ---- the C ABI guard ------------------------------------------------------------------
+template <class F>
+static int guard(pft_ctx* c, F f) {
+    try {
+        f();
+        return PFT_OK;
+    } catch (const Error& e) {
+        if (c) c->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host out of memory";
+        return PFT_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (c) c->err = e.what();
+        return PFT_ERR_ARG;
+    }
+}
+#define NEED(cond, code, msg) \
+    do {                      \
+        if (!(cond)) fail(code, msg); \
+    } while (0)
+
+static u32 galois_of(int n, int32_t step) {
+    const long long half = n / 2;
+    long long r = ((long long)step % half + half) % half;
+    u64 g = 1;
+    const u64 mask = (2ull * n) - 1;
+    for (long long i = 0; i < r; i++) g = (g * 5) & mask;
+    return (u32)g;
+}
+
+// ---- keygen ---------------------------------------------------------------------------------
+enum { DOM_SECRET = 1, DOM_PK_A, DOM_PK_E, DOM_KSK_A, DOM_KSK_E, DOM_ENC_A, DOM_ENC_E, DOM_ENC_V, DOM_ENC_E0, DOM_ENC_E1 };
+
+// signed polynomial from a sampler stream, reduced into `refs` and transformed
+static void sample_signed_ntt(pft_ctx* c, u32 dom, u32 obj, u32 sub, int kind, const std::vector<PolyRef>& refs) {
+    Scratch tmp(c, (size_t)c->n * 8);
+    sample_small(c->tabs, c->prm.seed, dom, obj, sub, kind, c->cdt.data(), (int)c->cdt.size(), (i64*)tmp.p,
+                 c->stream);
+    chunks(refs.size(), [&](size_t a, size_t b) { reduce_signed(c->tabs, (i64*)tmp.p, mkset(refs, a, b), c->stream); });
+    ntt_fwd(c, refs, refs);
+}
+
+// switching key from s' (evaluation form over the full basis, rows [L+k]) to s
+static u64* make_switch_key(pft_ctx* c, const u64* sp, u32 key_id) {
+    const int n = c->n, L = c->L, k = c->k, R = L + k;
+    u64* K = (u64*)dalloc(c, (size_t)c->beta_max * 2 * R * n * 8);
+    for (int j = 0; j < c->beta_max; j++) {
+        u64* b = K + (size_t)(2 * j) * R * n;
+        u64* a = K + (size_t)(2 * j + 1) * R * n;
+        std::vector<PolyRef> ra{ref(a, R, 0, L, L)}, rb{ref(b, R, 0, L, L)};
+        chunks(1, [&](size_t x, size_t y) {
+            sample_uniform(c->tabs, c->prm.seed, DOM_KSK_A, key_id, 256u * j, mkset(ra, x, y), c->stream);
+        });
+        ntt_fwd(c, ra, ra);
+        sample_signed_ntt(c, DOM_KSK_E, key_id, (u32)j, 1, rb);  // b = e
+        Scratch as(c, (size_t)R * n * 8);
+        std::vector<PolyRef> ras{ref(as.u(), R, 0, L, L)}, rs{ref((u64*)c->s_ntt, R, 0, L, L)};
+        ew(c, EwOp::Mul, ra, rs, ras);   // a s
+        ew(c, EwOp::Sub, rb, ras, rb);   // e - a s
+        // + P s' on the rows of digit j
+        const int lo = j * c->alpha, hi = std::min(L, lo + c->alpha);
+        Scratch ps(c, (size_t)(hi - lo) * n * 8);
+        std::vector<PolyRef> rsp{ref((u64*)sp + (size_t)lo * n, hi - lo, lo)};
+        std::vector<PolyRef> rps{ref(ps.u(), hi - lo, lo)};
+        std::vector<PolyRef> rbd{ref(b + (size_t)lo * n, hi - lo, lo)};
+        subscale(c, rsp, nullptr, nullptr, rps, c->pmodq_consts[j]);
+        ew(c, EwOp::Add, rbd, rps, rbd);
+    }
+    return K;
+}
+
+static void add_rot_keys(pft_ctx* c, const int32_t* steps, int n_steps) {
+    NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
+    const int n = c->n, R = c->L + c->k;
+    for (int i = 0; i < n_steps; i++) {
+        const u32 g = galois_of(n, steps[i]);
+        if (g == 1 || c->keys.count(g)) continue;
+        Scratch sg(c, (size_t)R * n * 8);
+        std::vector<PolyRef> in{ref(c->s_ntt, R, 0, c->L, c->L)}, out{ref(sg.u(), R, 0, c->L, c->L)};
+        chunks(1, [&](size_t a, size_t b) { automorph(c->tabs, mkset(in, a, b), mkset(out, a, b), g, c->stream); });
+        c->keys[g] = make_switch_key(c, sg.u(), g);
+    }
+}
+
+// ---- key switching ---------------------------------------------------------------------------
+struct KsIO {
+    const u64* d;     // [l][N] evaluation form
+    const u64* acc0;  // may be null
+    const u64* acc1;  // may be null
+    u64* out0;
+    u64* out1;
+};
+
+// For each input d (level l): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
+static void keyswitch_group(pft_ctx* c, int l, const u64* key, const std::vector<KsIO>& io) {
+    const int n = c->n, L = c->L, k = c->k, E = l + k, alpha = c->alpha;
+    const int beta = (l + alpha - 1) / alpha;
+    const size_t B = io.size();
+    if (B == 0) return;
+    const size_t limb = (size_t)n;
+    Scratch Dc(c, B * l * limb * 8), Ext(c, B * beta * E * limb * 8), U(c, B * 2 * E * limb * 8),
+        Cv(c, B * 2 * l * limb * 8);
+    auto dc = [&](size_t b) { return Dc.u() + b * l * limb; };
+    auto ext = [&](size_t b, int j) { return Ext.u() + (b * beta + j) * E * limb; };
+    auto uu = [&](size_t b, int pol) { return U.u() + (b * 2 + pol) * E * limb; };
+    auto cv = [&](size_t b, int pol) { return Cv.u() + (b * 2 + pol) * l * limb; };
+    // 1. coefficient form of d
+    {
+        std::vector<PolyRef> in, out;
+        for (size_t b = 0; b < B; b++) {
+            in.push_back(ref((u64*)io[b].d, l));
+            out.push_back(ref(dc(b), l));
+        }
+        ntt_inv(c, in, out);
+    }
+    // 2. ModUp: fast basis conversion of every digit to the other rows; digit rows copied
+    {
+        std::vector<BconvJob> jobs;
+        std::vector<PolyRef> cin, cout;
+        for (size_t b = 0; b < B; b++)
+            for (int j = 0; j < beta; j++) {
+                const int lo = j * alpha, hi = std::min(l, lo + alpha);
+                BconvJob J;
+                J.src = dc(b) + (size_t)lo * limb;
+                J.dst = ext(b, j);
+                J.table = c->modup_tab[(size_t)(l - 1) * c->beta_max + j];
+                J.ns = hi - lo;
+                J.src_p0 = lo;
+                J.nrows = E;
+                J.skip_lo = lo;
+                J.skip_hi = hi;
+                J.split = l;
+                J.base2 = L;
+                J.pad = 0;
+                jobs.push_back(J);
+                cin.push_back(ref((u64*)io[b].d + (size_t)lo * limb, hi - lo, lo));
+                cout.push_back(ref(ext(b, j) + (size_t)lo * limb, hi - lo, lo));
+            }
+        bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
+        ew(c, EwOp::Copy, cin, {}, cout);
+    }
+    // 3. evaluation form of the converted rows
+    {
+        std::vector<PolyRef> rows;
+        for (size_t b = 0; b < B; b++)
+            for (int j = 0; j < beta; j++) {
+                const int lo = j * alpha, hi = std::min(l, lo + alpha);
+                if (lo > 0) rows.push_back(ref(ext(b, j), lo, 0));
+                rows.push_back(ref(ext(b, j) + (size_t)hi * limb, E - hi, hi, l - hi, L));
+            }
+        ntt_fwd(c, rows, rows);
+    }
+    // 4. inner product with the key
+    ks_inner(c->tabs, Ext.u(), U.u(), key, (int)B, l, L, k, beta, c->stream);
+    // 5. ModDown: coefficient form of the special rows, conversion to q_0..q_{l-1}, evaluation form
+    {
+        std::vector<PolyRef> sp, cvr;
+        std::vector<BconvJob> jobs;
+        for (size_t b = 0; b < B; b++)
+            for (int pol = 0; pol < 2; pol++) {
+                sp.push_back(ref(uu(b, pol) + (size_t)l * limb, k, 0, 0, L));
+                cvr.push_back(ref(cv(b, pol), l));
+                BconvJob J;
+                J.src = uu(b, pol) + (size_t)l * limb;
+                J.dst = cv(b, pol);
+                J.table = c->moddown_tab[l - 1];
+                J.ns = k;
+                J.src_p0 = L;
+                J.nrows = l;
+                J.skip_lo = 0;
+                J.skip_hi = 0;
+                J.split = l;
+                J.base2 = L;
+                J.pad = 0;
+                jobs.push_back(J);
+            }
+        ntt_inv(c, sp, sp);
+        bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
+        ntt_fwd(c, cvr, cvr);
+    }
+    // 6. out = acc + (u_Q - conv) P^-1
+    {
+        std::vector<PolyRef> x, y, acc, out, x1, y1, out1, acc1;
+        bool all0 = true, all1 = true, none1 = true;
+        for (size_t b = 0; b < B; b++) {
+            all0 &= io[b].acc0 != nullptr;
+            all1 &= io[b].acc1 != nullptr;
+            none1 &= io[b].acc1 == nullptr;
+        }
+        NEED(all0 && (all1 || none1), PFT_ERR_ARG, "internal: mixed accumulators");
+        for (size_t b = 0; b < B; b++) {
+            x.push_back(ref(uu(b, 0), l));
+            y.push_back(ref(cv(b, 0), l));
+            acc.push_back(ref((u64*)io[b].acc0, l));
+            out.push_back(ref(io[b].out0, l));
+            x1.push_back(ref(uu(b, 1), l));
+            y1.push_back(ref(cv(b, 1), l));
+            if (io[b].acc1) acc1.push_back(ref((u64*)io[b].acc1, l));
+            out1.push_back(ref(io[b].out1, l));
+        }
+        subscale(c, x, &y, &acc, out, c->moddown_consts);
+        subscale(c, x1, &y1, all1 ? &acc1 : nullptr, out1, c->moddown_consts);
+    }
+}
+
+// ---- operations ---------------------------------------------------------------------------
+static void check_ct(const pft_ct* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty ciphertext"); }
+static void check_pt(const pft_pt* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty plaintext"); }
+
+static std::map<int, std::vector<int>> by_level(const pft_ct* const* a, int B) {
+    std::map<int, std::vector<int>> g;
+    for (int i = 0; i < B; i++) g[a[i]->level].push_back(i);
+    return g;
+}
+
+static void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out,
+                         EwOp op) {
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        check_ct(b[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+        NEED(a[i]->level == b[i]->level, PFT_ERR_LEVEL_MISMATCH, "HADD operands at different levels");
+        NEED(a[i]->scale == b[i]->scale, PFT_ERR_SCALE_MISMATCH, "HADD operands at different scales");
+    }
+    std::vector<PolyRef> ra, rb, ro;
+    for (int i = 0; i < B; i++) {
+        const int l = a[i]->level;
+        const double sc = a[i]->scale;
+        ensure_ct(c, out[i], l);
+        out[i]->scale = sc;
+        for (int pol = 0; pol < 2; pol++) {
+            ra.push_back(cpoly(a[i]->data, l, c->n, pol));
+            rb.push_back(cpoly(b[i]->data, l, c->n, pol));
+            ro.push_back(cpoly(out[i]->data, l, c->n, pol));
+        }
+    }
+    ew(c, op, ra, rb, ro);
+}
+
+static void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B,
+                               pft_ct* const* out) {
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        check_pt(p[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+        NEED(a[i]->level == p[i]->level, PFT_ERR_LEVEL_MISMATCH, "HMULPLAIN operands at different levels");
+    }
+    std::vector<PolyRef> ra, rb, ro;
+    for (int i = 0; i < B; i++) {
+        const int l = a[i]->level;
+        const double sc = a[i]->scale * p[i]->scale;
+        ensure_ct(c, out[i], l);
+        out[i]->scale = sc;
+        for (int pol = 0; pol < 2; pol++) {
+            ra.push_back(cpoly(a[i]->data, l, c->n, pol));
+            rb.push_back(ref(p[i]->data, l));
+            ro.push_back(cpoly(out[i]->data, l, c->n, pol));
+        }
+    }
+    ew(c, EwOp::Mul, ra, rb, ro);
+}
+
+static void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B,
+                               pft_ct* const* out) {
+    NEED(c->keys.count(0), PFT_ERR_NO_KEY, "no relinearisation key");
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        check_ct(b[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+        NEED(a[i]->level == b[i]->level, PFT_ERR_LEVEL_MISMATCH, "HMUL operands at different levels");
+    }
+    const size_t limb = c->n;
+    for (auto& kv : by_level(a, B)) {
+        const int l = kv.first;
+        const std::vector<int>& idx = kv.second;
+        Scratch D(c, idx.size() * 3 * l * limb * 8);
+        std::vector<PolyRef> ra, rb, rd;
+        for (size_t g = 0; g < idx.size(); g++) {
+            ra.push_back(ref(a[idx[g]]->data, l));
+            rb.push_back(ref(b[idx[g]]->data, l));
+            rd.push_back(ref(D.u() + g * 3 * l * limb, l));
+        }
+        chunks(rd.size(), [&](size_t x, size_t y) {
+            ew_tensor(c->tabs, mkset(ra, x, y), mkset(rb, x, y), mkset(rd, x, y), c->stream);
+        });
+        std::vector<KsIO> io;
+        for (size_t g = 0; g < idx.size(); g++) {
+            pft_ct* o = out[idx[g]];
+            const double sc = a[idx[g]]->scale * b[idx[g]]->scale;
+            ensure_ct(c, o, l);
+            o->scale = sc;
+            u64* d = D.u() + g * 3 * l * limb;
+            io.push_back(KsIO{d + 2 * l * limb, d, d + l * limb, o->data, o->data + l * limb});
+        }
+        keyswitch_group(c, l, c->keys[0], io);
+    }
+}
+
+static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out) {
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+    }
+    const u32 g = galois_of(c->n, step);
+    const size_t limb = c->n;
+    if (g == 1) {  // identity rotation
+        for (int i = 0; i < B; i++) {
+            if (out[i] == a[i]) continue;
+            const int l = a[i]->level;
+            const double sc = a[i]->scale;
+            ensure_ct(c, out[i], l);
+            out[i]->scale = sc;
+            PFT_CUDA(cudaMemcpyAsync(out[i]->data, a[i]->data, 2 * l * limb * 8, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        return;
+    }
+    NEED(c->keys.count(g), PFT_ERR_NO_KEY, "no rotation key for step " + std::to_string(step));
+    for (auto& kv : by_level(a, B)) {
+        const int l = kv.first;
+        const std::vector<int>& idx = kv.second;
+        Scratch R(c, idx.size() * 2 * l * limb * 8);
+        std::vector<PolyRef> rin, rout;
+        for (size_t i = 0; i < idx.size(); i++)
+            for (int pol = 0; pol < 2; pol++) {
+                rin.push_back(cpoly(a[idx[i]]->data, l, c->n, pol));
+                rout.push_back(cpoly(R.u() + i * 2 * l * limb, l, c->n, pol));
+            }
+        chunks(rout.size(), [&](size_t x, size_t y) {
+            automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
+        });
+        std::vector<KsIO> io;
+        for (size_t i = 0; i < idx.size(); i++) {
+            pft_ct* o = out[idx[i]];
+            const double sc = a[idx[i]]->scale;
+            ensure_ct(c, o, l);
+            o->scale = sc;
+            u64* r = R.u() + i * 2 * l * limb;
+            io.push_back(KsIO{r + l * limb, r, nullptr, o->data, o->data + l * limb});
+        }
+        keyswitch_group(c, l, c->keys[g], io);
+    }
+}
+
+static void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+        NEED(a[i]->level >= 2, PFT_ERR_LEVEL_MISMATCH, "rescale needs at least two primes");
+    }
+    const size_t limb = c->n;
+    for (auto& kv : by_level(a, B)) {
+        const int l = kv.first;
+        const std::vector<int>& idx = kv.second;
+        const size_t G = idx.size();
+        Scratch Last(c, G * 2 * limb * 8), Rb(c, G * 2 * (l - 1) * limb * 8);
+        std::vector<PolyRef> lin, lout, rr, x, y, out_refs;
+        // fresh output buffers (the output is smaller than the input and may alias it)
+        std::vector<u64*> nb(G);
+        for (size_t i = 0; i < G; i++) nb[i] = (u64*)dalloc(c, 2 * (l - 1) * limb * 8);
+        for (size_t i = 0; i < G; i++) {
+            u64* A = a[idx[i]]->data;
+            for (int pol = 0; pol < 2; pol++) {
+                lin.push_back(ref(A + ((size_t)pol * l + l - 1) * limb, 1, l - 1));
+                lout.push_back(ref(Last.u() + (i * 2 + pol) * limb, 1, l - 1));
+                rr.push_back(ref(Rb.u() + (i * 2 + pol) * (l - 1) * limb, l - 1));
+                x.push_back(ref(A + (size_t)pol * l * limb, l - 1));
+                out_refs.push_back(ref(nb[i] + (size_t)pol * (l - 1) * limb, l - 1));
+            }
+        }
+        ntt_inv(c, lin, lout);
+        chunks(rr.size(), [&](size_t p, size_t q) { rescale_bcast(c->tabs, mkset(lout, p, q), mkset(rr, p, q), c->stream); });
+        ntt_fwd(c, rr, rr);
+        subscale(c, x, &rr, nullptr, out_refs, c->rescale_consts[l - 1]);
+        for (size_t i = 0; i < G; i++) {
+            pft_ct* o = out[idx[i]];
+            const double sc = a[idx[i]]->scale / (double)c->primes[l - 1];
+            dfree(c, o->data);  // stream-ordered: queued work on the old buffer completes first
+            o->data = nb[i];
+            o->cap = 2 * (size_t)(l - 1) * limb;
+            o->level = l - 1;
+            o->scale = sc;
+        }
+        // inputs aliased by an output of the same group were released above; make sure no
+        // later entry of this group still points at them (each handle appears once per group)
+    }
+}
+
+// ---- encryption ----------------------------------------------------------------------------
+static void encrypt(pft_ctx* c, const pft_pt* pt, int mode, u32 nonce, pft_ct* out) {
+    NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
+    check_pt(pt);
+    const int l = pt->level, n = c->n;
+    const size_t limb = n;
+    ensure_ct(c, out, l);
+    out->scale = pt->scale;
+    u64* c0 = out->data;
+    u64* c1 = out->data + l * limb;
+    std::vector<PolyRef> r0{ref(c0, l)}, r1{ref(c1, l)}, rpt{ref(pt->data, l)}, rs{ref(c->s_ntt, l)};
+    if (mode == PFT_ENC_SK) {
+        sample_uniform(c->tabs, c->prm.seed, DOM_ENC_A, nonce, 0, mkset(r1, 0, 1), c->stream);
+        ntt_fwd(c, r1, r1);
+        sample_signed_ntt(c, DOM_ENC_E, nonce, 0, 1, r0);  // c0 = e
+        Scratch as(c, l * limb * 8);
+        std::vector<PolyRef> ras{ref(as.u(), l)};
+        ew(c, EwOp::Mul, r1, rs, ras);
+        ew(c, EwOp::Sub, r0, ras, r0);
+        ew(c, EwOp::Add, r0, rpt, r0);
+    } else {
+        Scratch v(c, l * limb * 8), e1(c, l * limb * 8), t(c, l * limb * 8);
+        std::vector<PolyRef> rv{ref(v.u(), l)}, re1{ref(e1.u(), l)}, rt{ref(t.u(), l)};
+        std::vector<PolyRef> rb{ref(c->pk, l)}, ra{ref(c->pk + (size_t)c->L * limb, l)};
+        sample_signed_ntt(c, DOM_ENC_V, nonce, 0, 0, rv);
+        sample_signed_ntt(c, DOM_ENC_E0, nonce, 0, 1, r0);
+        sample_signed_ntt(c, DOM_ENC_E1, nonce, 0, 1, re1);
+        ew(c, EwOp::Mul, rv, rb, rt);
+        ew(c, EwOp::Add, r0, rt, r0);
+        ew(c, EwOp::Add, r0, rpt, r0);
+        ew(c, EwOp::Mul, rv, ra, rt);
+        ew(c, EwOp::Add, re1, rt, r1);
+    }
+}
+
+// ---- fastText inference (Sec. 3.1) ----------------------------------------------------------
+static int ilog2(int x) {
+    int r = 0;
+    while ((1 << r) < x) r++;
+    return r;
+}
+
+static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int chunks_in, int B,
+                           pft_ct* const* scores) {
+    NEED(M && M->ctx == c, PFT_ERR_ARG, "model from another context");
+    NEED(chunks_in == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
+    const int l = M->level, n = c->n, cols = M->n;
+    const size_t limb = n;
+    NEED(l >= 3, PFT_ERR_LEVEL_MISMATCH, "inference needs three levels");
+    for (int i = 0; i < B * chunks_in; i++) {
+        check_ct(v[i]);
+        NEED(v[i]->level == l, PFT_ERR_LEVEL_MISMATCH, "input level differs from the model level");
+    }
+    const int steps = ilog2(n / 2);
+    for (int s = 0; s < steps; s++)
+        NEED(c->keys.count(galois_of(n, 1 << s)), PFT_ERR_NO_KEY, "missing rotation key for TotalSum");
+    const double sc_v = v[0]->scale, sc_h = M->H[0]->scale;
+    // 1. column products: T[b][j] = sum_i v[b][i] * H[j][i]   (Fig. 3 vertical packing)
+    const size_t nT = (size_t)B * cols;
+    std::vector<pft_ct> T(nT);
+    std::vector<pft_ct*> Tp(nT);
+    for (size_t i = 0; i < nT; i++) {
+        T[i].ctx = c;
+        ensure_ct(c, &T[i], l);
+        T[i].scale = sc_v * sc_h;
+        Tp[i] = &T[i];
+    }
+    struct Cleanup {
+        pft_ctx* c;
+        std::vector<pft_ct>* T;
+        ~Cleanup() {
+            for (auto& t : *T) dfree(c, t.data);
+        }
+    } cleanup{c, &T};
+    {
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int b = 0; b < B; b++)
+            for (int j = 0; j < cols; j++)
+                for (int pol = 0; pol < 2; pol++) {
+                    for (int i = 0; i < chunks_in; i++) {
+                        A.push_back(v[(size_t)b * chunks_in + i]->data + (size_t)pol * l * limb);
+                        Bv.push_back(M->H[(size_t)j * M->chunks + i]->data);
+                    }
+                    O.push_back(T[(size_t)b * cols + j].data + (size_t)pol * l * limb);
+                }
+        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
+        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), chunks_in, false, l,
+               c->stream);
+    }
+    // 2. TotalSum (Algorithm 2): T += rotate(T, 2^s), s = 0..log2(t)-1, all columns share each key
+    {
+        const int E = l + c->k, beta = (l + c->alpha - 1) / c->alpha;
+        const size_t per_ct = (size_t)(2 * l + l + beta * E + 2 * E + 2 * l + 3 * l) * limb * 8;
+        const size_t budget = (size_t)24 << 30;
+        const size_t tile = std::max<size_t>(1, std::min(nT, budget / per_ct));
+        for (int s = 0; s < steps; s++) {
+            const u32 g = galois_of(n, 1 << s);
+            for (size_t t0 = 0; t0 < nT; t0 += tile) {
+                const size_t t1 = std::min(nT, t0 + tile);
+                Scratch R(c, (t1 - t0) * 2 * l * limb * 8);
+                std::vector<PolyRef> rin, rout, tin0, rc0;
+                for (size_t i = t0; i < t1; i++)
+                    for (int pol = 0; pol < 2; pol++) {
+                        rin.push_back(cpoly(T[i].data, l, n, pol));
+                        rout.push_back(cpoly(R.u() + (i - t0) * 2 * l * limb, l, n, pol));
+                    }
+                chunks(rout.size(), [&](size_t x, size_t y) {
+                    automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
+                });
+                // c0' + T.c0 first, then key switch c1' with T.c0/T.c1 as accumulators (in place)
+                for (size_t i = t0; i < t1; i++) {
+                    tin0.push_back(cpoly(T[i].data, l, n, 0));
+                    rc0.push_back(cpoly(R.u() + (i - t0) * 2 * l * limb, l, n, 0));
+                }
+                ew(c, EwOp::Add, tin0, rc0, tin0);
+                std::vector<KsIO> io;
+                for (size_t i = t0; i < t1; i++) {
+                    u64* r = R.u() + (i - t0) * 2 * l * limb;
+                    io.push_back(KsIO{r + l * limb, T[i].data, T[i].data + l * limb, T[i].data, T[i].data + l * limb});
+                }
+                keyswitch_group(c, l, c->keys[g], io);
+            }
+        }
+    }
+    // 3. rescale every column
+    op_rescale_batch(c, Tp.data(), (int)nT, Tp.data());
+    // 4. s = sum_j h_j * O_j  (Fig. 3 horizontal packing), 5. rescale
+    {
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int j = 0; j < cols; j++) {
+            NEED(M->O[j]->level == l - 1, PFT_ERR_LEVEL_MISMATCH, "output-layer plaintexts must sit one level below");
+            Bv.push_back(M->O[j]->data);
+        }
+        for (int b = 0; b < B; b++) {
+            ensure_ct(c, scores[b], l - 1);
+            scores[b]->scale = T[(size_t)b * cols].scale * M->O[0]->scale;
+            for (int pol = 0; pol < 2; pol++) {
+                for (int j = 0; j < cols; j++) A.push_back(T[(size_t)b * cols + j].data + (size_t)pol * (l - 1) * limb);
+                O.push_back(scores[b]->data + (size_t)pol * (l - 1) * limb);
+            }
+        }
+        // B_k for output p = (b, pol) is O_k for every p: one shared table of `cols` entries
+        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
+        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l - 1,
+               c->stream);
+        op_rescale_batch(c, (const pft_ct* const*)scores, B, scores);
+    }
+}
+
+// ---- launch accounting ---------------------------------------------------------------------
+namespace {
+struct Prof {
+    bool on = false;
+    std::string prefix;
+    long long all = 0;
+    double work = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t used = 0;
+    bool open = false;
+};
+Prof g_prof;
+}  // namespace
+namespace pft {
+void prof_begin(const char* name, cudaStream_t st, double work) {
+    g_prof.all++;
+    if (!g_prof.on || strncmp(name, g_prof.prefix.c_str(), g_prof.prefix.size()) != 0) return;
+    g_prof.work += work;
+    if (g_prof.used == g_prof.ev.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+        g_prof.ev.push_back({a, b});
+    }
+    cudaEventRecord(g_prof.ev[g_prof.used].first, st);
+    g_prof.open = true;
+}
+void prof_end(const char* name, cudaStream_t st) {
+    if (!g_prof.open || strncmp(name, g_prof.prefix.c_str(), g_prof.prefix.size()) != 0) return;
+    cudaEventRecord(g_prof.ev[g_prof.used].second, st);
+    g_prof.used++;
+    g_prof.open = false;
+}
+}  // namespace pft
+
+// ===================================================================================================
+// C ABI
+// ===================================================================================================
+extern "C" {
+
+int pft_prof_start(const char* prefix) {
+    g_prof.on = prefix != nullptr && prefix[0] != 0;
+    g_prof.prefix = prefix ? prefix : "";
+    g_prof.all = 0;
+    g_prof.work = 0;
+    g_prof.used = 0;
+    g_prof.open = false;
+    return PFT_OK;
+}
+
+int pft_prof_stop(double* ms, long long* timed_launches, long long* all_launches, double* work) {
+    double tot = 0;
+    if (g_prof.used) {
+        if (cudaEventSynchronize(g_prof.ev[g_prof.used - 1].second) != cudaSuccess) return PFT_ERR_CUDA;
+        for (size_t i = 0; i < g_prof.used; i++) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, g_prof.ev[i].first, g_prof.ev[i].second) != cudaSuccess) return PFT_ERR_CUDA;
+            tot += t;
+        }
+    }
+    if (ms) *ms = tot;
+    if (timed_launches) *timed_launches = (long long)g_prof.used;
+    if (all_launches) *all_launches = g_prof.all;
+    if (work) *work = g_prof.work;
+    g_prof.on = false;
+    g_prof.used = 0;
+    return PFT_OK;
+}
+
+int pft_gen_primes(int log_n, int bits, int count, const uint64_t* exclude, int n_exclude, uint64_t* out) {
+    return guard(nullptr, [&] {
+        NEED(out && count >= 0, PFT_ERR_ARG, "bad arguments");
+        std::vector<u64> ex(exclude, exclude + (exclude ? n_exclude : 0));
+        std::vector<u64> p = gen_primes(log_n, bits, count, ex);
+        std::copy(p.begin(), p.end(), out);
+    });
+}
+
+int pft_gauss_cdt(double sigma, uint32_t* out, int cap, int* n_out) {
+    return guard(nullptr, [&] {
+        int tail = 0;
+        std::vector<u32> t = gauss_cdt(sigma, &tail);
+        NEED(out && cap >= tail, PFT_ERR_ARG, "output too small");
+        std::copy(t.begin(), t.end(), out);
+        if (n_out) *n_out = tail;
+    });
+}
+
+int pft_ctx_create(const pft_params* prm, const pft_allocator* alloc, pft_ctx** out) {
+    if (!prm || !out) return PFT_ERR_ARG;
+    *out = nullptr;
+    std::unique_ptr<pft_ctx> c(new pft_ctx());
+    int rc = guard(c.get(), [&] {
+        c->prm = *prm;
+        c->logn = prm->log_n;
+        NEED(prm->log_n >= 4 && prm->log_n <= 16, PFT_ERR_ARG, "log_n must be in 4..16");
+        NEED(prm->n_limbs >= 1 && prm->n_limbs <= kMaxLimbs, PFT_ERR_ARG, "n_limbs must be in 1..60");
+        NEED(prm->n_special >= 1 && prm->n_special <= kMaxSpecial, PFT_ERR_ARG, "n_special must be in 1..8");
+        NEED(prm->alpha >= 1 && prm->alpha <= kMaxAlpha, PFT_ERR_ARG, "alpha must be in 1..8");
+        c->n = 1 << c->logn;
+        c->L = prm->n_limbs;
+        c->k = prm->n_special;
+        c->alpha = prm->alpha;
+        c->beta_max = (c->L + c->alpha - 1) / c->alpha;
+        if (prm->primes) {
+            c->primes.assign(prm->primes, prm->primes + c->L + c->k);
+            for (u64 q : c->primes) {
+                NEED(q % (2ull * c->n) == 1 && bitlen(q) <= 60 && bitlen(q) >= 20, PFT_ERR_ARG,
+                     "explicit primes must be 20..60 bits and 1 mod 2N");
+            }
+        } else {
+            std::vector<u64> q0 = gen_primes(c->logn, prm->first_bits, 1, {});
+            std::vector<u64> mids = gen_primes(c->logn, prm->mid_bits, c->L - 1, q0);
+            std::vector<u64> used = q0;
+            used.insert(used.end(), mids.begin(), mids.end());
+            std::vector<u64> sp = gen_primes(c->logn, prm->special_bits, c->k, used);
+            c->primes = used;
+            c->primes.insert(c->primes.end(), sp.begin(), sp.end());
+        }
+        double logqp = 0;
+        for (u64 q : c->primes) logqp += std::log2((double)q);
+        if (!(prm->flags & PFT_ALLOW_INSECURE)) {
+            NEED(c->logn >= 10 && logqp <= kSecureLogQP[c->logn], PFT_ERR_SECURITY,
+                 "log2(QP) = " + std::to_string(logqp) + " is above the 128-bit bound for this N");
+        }
+        int tail = 0;
+        c->cdt = gauss_cdt(prm->sigma > 0 ? prm->sigma : 3.2, &tail);
+        if (alloc && alloc->alloc && alloc->free) {
+            c->alloc = *alloc;
+            c->has_alloc = true;
+        }
+        build_tables(c.get());
+    });
+    if (rc != PFT_OK) {
+        for (void* p : c->owned) cudaFree(p);
+        return rc;
+    }
+    *out = c.release();
+    return PFT_OK;
+}
+
+int pft_ctx_destroy(pft_ctx* c) {
+    if (!c) return PFT_OK;
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->keys) dfree(c, kv.second);
+    dfree(c, c->s_ntt);
+    dfree(c, c->pk);
+    cudaStreamSynchronize(c->stream);
+    for (void* p : c->owned) cudaFree(p);
+    delete c;
+    return PFT_OK;
+}
+
+int pft_set_stream(pft_ctx* c, void* stream) {
+    if (!c) return PFT_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return PFT_OK;
+}
+
+const char* pft_last_error(pft_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pft_ctx_info(pft_ctx* c, int* n, int* n_limbs, int* n_special, int* alpha, uint64_t* primes_out) {
+    if (!c) return PFT_ERR_ARG;
+    if (n) *n = c->n;
+    if (n_limbs) *n_limbs = c->L;
+    if (n_special) *n_special = c->k;
+    if (alpha) *alpha = c->alpha;
+    if (primes_out) std::copy(c->primes.begin(), c->primes.end(), primes_out);
+    return PFT_OK;
+}
+
+int pft_keygen(pft_ctx* c, const int32_t* rot_steps, int n_steps, int want_relin) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "null context");
+        const int n = c->n, L = c->L, R = L + c->k;
+        const size_t limb = n;
+        // s (ternary, the same integer polynomial in every prime of the full basis)
+        c->s_coeff.assign(n, 0);
+        if (!c->s_ntt) c->s_ntt = (u64*)dalloc(c, (size_t)R * limb * 8);
+        {
+            Scratch tmp(c, limb * 8);
+            sample_small(c->tabs, c->prm.seed, DOM_SECRET, 0, 0, 0, c->cdt.data(), (int)c->cdt.size(), (i64*)tmp.p,
+                         c->stream);
+            std::vector<PolyRef> rs{ref(c->s_ntt, R, 0, L, L)};
+            reduce_signed(c->tabs, (i64*)tmp.p, mkset(rs, 0, 1), c->stream);
+            PFT_CUDA(cudaMemcpyAsync(c->s_coeff.data(), tmp.p, limb * 8, cudaMemcpyDeviceToHost, c->stream));
+            PFT_CUDA(cudaStreamSynchronize(c->stream));
+            ntt_fwd(c, rs, rs);
+        }
+        // pk = (b, a): a uniform, b = -a s + e
+        if (!c->pk) c->pk = (u64*)dalloc(c, 2 * (size_t)L * limb * 8);
+        {
+            std::vector<PolyRef> rb{ref(c->pk, L)}, ra{ref(c->pk + (size_t)L * limb, L)}, rs{ref(c->s_ntt, L)};
+            sample_uniform(c->tabs, c->prm.seed, DOM_PK_A, 0, 0, mkset(ra, 0, 1), c->stream);
+            ntt_fwd(c, ra, ra);
+            sample_signed_ntt(c, DOM_PK_E, 0, 0, 1, rb);
+            Scratch as(c, (size_t)L * limb * 8);
+            std::vector<PolyRef> ras{ref(as.u(), L)};
+            ew(c, EwOp::Mul, ra, rs, ras);
+            ew(c, EwOp::Sub, rb, ras, rb);
+        }
+        c->have_sk = true;
+        for (auto& kv : c->keys) dfree(c, kv.second);
+        c->keys.clear();
+        if (want_relin) {
+            Scratch s2(c, (size_t)R * limb * 8);
+            std::vector<PolyRef> rs{ref(c->s_ntt, R, 0, L, L)}, r2{ref(s2.u(), R, 0, L, L)};
+            ew(c, EwOp::Mul, rs, rs, r2);
+            c->keys[0] = make_switch_key(c, s2.u(), 0);
+        }
+        if (n_steps > 0) {
+            NEED(rot_steps, PFT_ERR_ARG, "null rotation steps");
+            add_rot_keys(c, rot_steps, n_steps);
+        }
+    });
+}
+
+int pft_add_rotation_keys(pft_ctx* c, const int32_t* rot_steps, int n_steps) {
+    return guard(c, [&] {
+        NEED(c && (rot_steps || n_steps == 0), PFT_ERR_ARG, "bad arguments");
+        add_rot_keys(c, rot_steps, n_steps);
+    });
+}
+
+int pft_key_export(pft_ctx* c, uint32_t key_id, uint64_t* out, size_t nw) {
+    return guard(c, [&] {
+        NEED(c && out, PFT_ERR_ARG, "bad arguments");
+        NEED(c->keys.count(key_id), PFT_ERR_NO_KEY, "no such key");
+        const int R = c->L + c->k;
+        const size_t words = (size_t)c->beta_max * 2 * R * c->n;
+        NEED(nw >= words, PFT_ERR_ARG, "output too small");
+        Scratch t(c, words * 8);
+        std::vector<PolyRef> in, o;
+        for (int i = 0; i < 2 * c->beta_max; i++) {
+            in.push_back(ref(c->keys[key_id] + (size_t)i * R * c->n, R, 0, c->L, c->L));
+            o.push_back(ref(t.u() + (size_t)i * R * c->n, R, 0, c->L, c->L));
+        }
+        ntt_inv(c, in, o);
+        PFT_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, c->stream));
+        PFT_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+int pft_secret_export(pft_ctx* c, int64_t* out, size_t nw) {
+    return guard(c, [&] {
+        NEED(c && out && nw >= (size_t)c->n, PFT_ERR_ARG, "bad arguments");
+        NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
+        std::copy(c->s_coeff.begin(), c->s_coeff.end(), out);
+    });
+}
+
+int pft_ct_create(pft_ctx* c, pft_ct** out) {
+    if (!c || !out) return PFT_ERR_ARG;
+    *out = new pft_ct();
+    (*out)->ctx = c;
+    return PFT_OK;
+}
+int pft_ct_destroy(pft_ct* ct) {
+    if (!ct) return PFT_OK;
+    dfree(ct->ctx, ct->data);
+    delete ct;
+    return PFT_OK;
+}
+int pft_pt_destroy(pft_pt* pt) {
+    if (!pt) return PFT_OK;
+    dfree(pt->ctx, pt->data);
+    delete pt;
+    return PFT_OK;
+}
+int pft_ct_level(const pft_ct* ct, int* level) {
+    if (!ct || !level) return PFT_ERR_ARG;
+    *level = ct->level;
+    return PFT_OK;
+}
+int pft_ct_scale(const pft_ct* ct, double* scale) {
+    if (!ct || !scale) return PFT_ERR_ARG;
+    *scale = ct->scale;
+    return PFT_OK;
+}
+int pft_pt_level(const pft_pt* pt, int* level) {
+    if (!pt || !level) return PFT_ERR_ARG;
+    *level = pt->level;
+    return PFT_OK;
+}
+int pft_ct_data(const pft_ct* ct, uint64_t** p) {
+    if (!ct || !p) return PFT_ERR_ARG;
+    *p = ct->data;
+    return PFT_OK;
+}
+
+static pft_pt* new_pt(pft_ctx* c) {
+    pft_pt* p = new pft_pt();
+    p->ctx = c;
+    return p;
+}
+
+int pft_pt_import(pft_ctx* c, const uint64_t* coeffs, int level, double scale, pft_pt** out) {
+    return guard(c, [&] {
+        NEED(c && coeffs && out && level >= 1 && level <= c->L, PFT_ERR_ARG, "bad arguments");
+        std::unique_ptr<pft_pt> p(new_pt(c));
+        ensure_pt(c, p.get(), level);
+        p->scale = scale;
+        PFT_CUDA(cudaMemcpyAsync(p->data, coeffs, (size_t)level * c->n * 8, cudaMemcpyHostToDevice, c->stream));
+        std::vector<PolyRef> r{ref(p->data, level)};
+        ntt_fwd(c, r, r);
+        *out = p.release();
+    });
+}
+
+int pft_pt_export(pft_ctx* c, const pft_pt* pt, uint64_t* coeffs, size_t nw) {
+    return guard(c, [&] {
+        check_pt(pt);
+        NEED(c && coeffs && nw >= (size_t)pt->level * c->n, PFT_ERR_ARG, "bad arguments");
+        Scratch t(c, (size_t)pt->level * c->n * 8);
+        std::vector<PolyRef> in{ref(pt->data, pt->level)}, o{ref(t.u(), pt->level)};
+        ntt_inv(c, in, o);
+        PFT_CUDA(cudaMemcpyAsync(coeffs, t.p, (size_t)pt->level * c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+        PFT_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+int pft_ct_import(pft_ctx* c, const uint64_t* coeffs, int level, double scale, pft_ct** out) {
+    return guard(c, [&] {
+        NEED(c && coeffs && out && level >= 1 && level <= c->L, PFT_ERR_ARG, "bad arguments");
+        std::unique_ptr<pft_ct> ct(new pft_ct());
+        ct->ctx = c;
+        ensure_ct(c, ct.get(), level);
+        ct->scale = scale;
+        PFT_CUDA(cudaMemcpyAsync(ct->data, coeffs, (size_t)2 * level * c->n * 8, cudaMemcpyHostToDevice, c->stream));
+        std::vector<PolyRef> r{cpoly(ct->data, level, c->n, 0), cpoly(ct->data, level, c->n, 1)};
+        ntt_fwd(c, r, r);
+        *out = ct.release();
+    });
+}
+
+int pft_ct_export(pft_ctx* c, const pft_ct* ct, uint64_t* coeffs, size_t nw) {
+    return guard(c, [&] {
+        check_ct(ct);
+        const size_t words = (size_t)2 * ct->level * c->n;
+        NEED(c && coeffs && nw >= words, PFT_ERR_ARG, "bad arguments");
+        Scratch t(c, words * 8);
+        std::vector<PolyRef> in{cpoly(ct->data, ct->level, c->n, 0), cpoly(ct->data, ct->level, c->n, 1)};
+        std::vector<PolyRef> o{cpoly(t.u(), ct->level, c->n, 0), cpoly(t.u(), ct->level, c->n, 1)};
+        ntt_inv(c, in, o);
+        PFT_CUDA(cudaMemcpyAsync(coeffs, t.p, words * 8, cudaMemcpyDeviceToHost, c->stream));
+        PFT_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+int pft_encode(pft_ctx* c, const double* re_im, int n_slots, double scale, int level, pft_pt** out) {
+    return guard(c, [&] {
+        NEED(c && out && (re_im || n_slots == 0), PFT_ERR_ARG, "bad arguments");
+        NEED(n_slots >= 0 && n_slots <= c->n / 2, PFT_ERR_ARG, "too many slots");
+        NEED(level >= 1 && level <= c->L, PFT_ERR_ARG, "bad level");
+        std::vector<i64> coeffs;
+        NEED(encode_slots(c->logn, re_im, n_slots, scale, coeffs), PFT_ERR_ARG, "encoded coefficient exceeds 2^62");
+        std::unique_ptr<pft_pt> p(new_pt(c));
+        ensure_pt(c, p.get(), level);
+        p->scale = scale;
+        Scratch t(c, (size_t)c->n * 8);
+        PFT_CUDA(cudaMemcpyAsync(t.p, coeffs.data(), (size_t)c->n * 8, cudaMemcpyHostToDevice, c->stream));
+        std::vector<PolyRef> r{ref(p->data, level)};
+        reduce_signed(c->tabs, (i64*)t.p, mkset(r, 0, 1), c->stream);
+        ntt_fwd(c, r, r);
+        *out = p.release();
+    });
+}
+
+int pft_decode(pft_ctx* c, const pft_pt* pt, double* re_im, int n_slots) {
+    return guard(c, [&] {
+        check_pt(pt);
+        NEED(c && re_im && n_slots >= 0 && n_slots <= c->n / 2, PFT_ERR_ARG, "bad arguments");
+        const int l = pt->level;
+        std::vector<u64> rows((size_t)l * c->n);
+        Scratch t(c, rows.size() * 8);
+        std::vector<PolyRef> in{ref(pt->data, l)}, o{ref(t.u(), l)};
+        ntt_inv(c, in, o);
+        PFT_CUDA(cudaMemcpyAsync(rows.data(), t.p, rows.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        PFT_CUDA(cudaStreamSynchronize(c->stream));
+        std::vector<u64> ps(c->primes.begin(), c->primes.begin() + l);
+        std::vector<double> coeffs;
+        crt_to_double(ps, rows.data(), c->n, coeffs);
+        decode_coeffs(c->logn, coeffs, pt->scale, re_im, n_slots);
+    });
+}
+
+int pft_encrypt(pft_ctx* c, const pft_pt* pt, int mode, uint32_t nonce, pft_ct** out) {
+    return guard(c, [&] {
+        NEED(c && out && (mode == PFT_ENC_PK || mode == PFT_ENC_SK), PFT_ERR_ARG, "bad arguments");
+        std::unique_ptr<pft_ct> ct(new pft_ct());
+        ct->ctx = c;
+        encrypt(c, pt, mode, nonce, ct.get());
+        *out = ct.release();
+    });
+}
+
+int pft_decrypt(pft_ctx* c, const pft_ct* ct, pft_pt** out) {
+    return guard(c, [&] {
+        check_ct(ct);
+        NEED(c && out, PFT_ERR_ARG, "bad arguments");
+        NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
+        const int l = ct->level;
+        std::unique_ptr<pft_pt> p(new_pt(c));
+        ensure_pt(c, p.get(), l);
+        p->scale = ct->scale;
+        std::vector<PolyRef> r0{cpoly(ct->data, l, c->n, 0)}, r1{cpoly(ct->data, l, c->n, 1)}, rs{ref(c->s_ntt, l)},
+            rp{ref(p->data, l)};
+        ew(c, EwOp::Mul, r1, rs, rp);
+        ew(c, EwOp::Add, rp, r0, rp);
+        *out = p.release();
+    });
+}
+
+int pft_add(pft_ctx* c, const pft_ct* a, const pft_ct* b, pft_ct* out) {
+    return guard(c, [&] { op_add_batch(c, &a, &b, 1, &out, EwOp::Add); });
+}
+int pft_sub(pft_ctx* c, const pft_ct* a, const pft_ct* b, pft_ct* out) {
+    return guard(c, [&] { op_add_batch(c, &a, &b, 1, &out, EwOp::Sub); });
+}
+int pft_add_plain(pft_ctx* c, const pft_ct* a, const pft_pt* p, pft_ct* out) {
+    return guard(c, [&] {
+        check_ct(a);
+        check_pt(p);
+        NEED(out, PFT_ERR_ARG, "null output");
+        NEED(a->level == p->level, PFT_ERR_LEVEL_MISMATCH, "HADDPLAIN operands at different levels");
+        NEED(a->scale == p->scale, PFT_ERR_SCALE_MISMATCH, "HADDPLAIN operands at different scales");
+        const int l = a->level;
+        const double sc = a->scale;
+        const u64* src1 = a->data + (size_t)l * c->n;
+        ensure_ct(c, out, l);
+        out->scale = sc;
+        std::vector<PolyRef> r0{cpoly(a->data, l, c->n, 0)}, rp{ref(p->data, l)}, o0{cpoly(out->data, l, c->n, 0)};
+        ew(c, EwOp::Add, r0, rp, o0);
+        if (out != a) {
+            std::vector<PolyRef> r1{ref((u64*)src1, l)}, o1{cpoly(out->data, l, c->n, 1)};
+            ew(c, EwOp::Copy, r1, {}, o1);
+        }
+    });
+}
+int pft_mul_plain(pft_ctx* c, const pft_ct* a, const pft_pt* p, pft_ct* out) {
+    return guard(c, [&] { op_mul_plain_batch(c, &a, &p, 1, &out); });
+}
+int pft_mul_relin(pft_ctx* c, const pft_ct* a, const pft_ct* b, pft_ct* out) {
+    return guard(c, [&] { op_mul_relin_batch(c, &a, &b, 1, &out); });
+}
+int pft_rescale(pft_ctx* c, const pft_ct* a, pft_ct* out) {
+    return guard(c, [&] { op_rescale_batch(c, &a, 1, &out); });
+}
+int pft_rotate(pft_ctx* c, const pft_ct* a, int32_t step, pft_ct* out) {
+    return guard(c, [&] { op_rotate_batch(c, &a, 1, step, &out); });
+}
+int pft_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out) {
+    return guard(c, [&] {
+        NEED(c && a && b && out && B >= 0, PFT_ERR_ARG, "bad arguments");
+        op_add_batch(c, a, b, B, out, EwOp::Add);
+    });
+}
+int pft_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B, pft_ct* const* out) {
+    return guard(c, [&] {
+        NEED(c && a && p && out && B >= 0, PFT_ERR_ARG, "bad arguments");
+        op_mul_plain_batch(c, a, p, B, out);
+    });
+}
+int pft_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out) {
+    return guard(c, [&] {
+        NEED(c && a && b && out && B >= 0, PFT_ERR_ARG, "bad arguments");
+        op_mul_relin_batch(c, a, b, B, out);
+    });
+}
+int pft_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
+    return guard(c, [&] {
+        NEED(c && a && out && B >= 0, PFT_ERR_ARG, "bad arguments");
+        op_rescale_batch(c, a, B, out);
+    });
+}
+int pft_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out) {
+    return guard(c, [&] {
+        NEED(c && a && out && B >= 0, PFT_ERR_ARG, "bad arguments");
+        op_rotate_batch(c, a, B, step, out);
+    });
+}
+
+int pft_ntt(pft_ctx* c, uint64_t* data, int n_polys, int n_limbs, int inverse) {
+    return guard(c, [&] {
+        NEED(c && data && n_polys >= 0 && n_limbs >= 1 && n_limbs <= c->L + c->k, PFT_ERR_ARG, "bad arguments");
+        std::vector<PolyRef> r;
+        for (int i = 0; i < n_polys; i++) r.push_back(ref(data + (size_t)i * n_limbs * c->n, n_limbs));
+        if (inverse) ntt_inv(c, r, r);
+        else ntt_fwd(c, r, r);
+    });
+}
+
+int pft_ft_model_import(pft_ctx* c, const pft_pt* const* H_pts, const pft_pt* const* O_pts, int m, int n, int cl,
+                        pft_ft_model** out) {
+    return guard(c, [&] {
+        NEED(c && H_pts && O_pts && out && m >= 1 && n >= 1 && cl >= 1 && cl <= c->n / 2, PFT_ERR_ARG,
+             "bad arguments");
+        const int t = c->n / 2, chunks_n = (m + t - 1) / t;
+        std::unique_ptr<pft_ft_model> M(new pft_ft_model());
+        M->ctx = c;
+        M->m = m;
+        M->n = n;
+        M->c = cl;
+        M->chunks = chunks_n;
+        M->level = H_pts[0]->level;
+        auto copy_pt = [&](const pft_pt* p) {
+            check_pt(p);
+            pft_pt* q = new_pt(c);
+            ensure_pt(c, q, p->level);
+            q->scale = p->scale;
+            PFT_CUDA(cudaMemcpyAsync(q->data, p->data, (size_t)p->level * c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+            return q;
+        };
+        for (int i = 0; i < n * chunks_n; i++) {
+            NEED(H_pts[i]->level == M->level, PFT_ERR_LEVEL_MISMATCH, "embedding plaintexts at different levels");
+            M->H.push_back(copy_pt(H_pts[i]));
+        }
+        for (int j = 0; j < n; j++) M->O.push_back(copy_pt(O_pts[j]));
+        *out = M.release();
+    });
+}
+
+int pft_ft_model_create(pft_ctx* c, const double* H, const double* O, int m, int n, int cl, int level,
+                        pft_ft_model** out) {
+    return guard(c, [&] {
+        NEED(c && H && O && out && m >= 1 && n >= 1 && cl >= 1 && cl <= c->n / 2, PFT_ERR_ARG, "bad arguments");
+        NEED(level >= 3 && level <= c->L, PFT_ERR_ARG, "model level must be in 3..L");
+        const int t = c->n / 2, chunks_n = (m + t - 1) / t;
+        std::vector<pft_pt*> hp, op;
+        std::vector<double> slots(2 * (size_t)t);
+        auto cleanup = [&] {
+            for (auto p : hp) pft_pt_destroy(p);
+            for (auto p : op) pft_pt_destroy(p);
+        };
+        int rc = PFT_OK;
+        for (int j = 0; j < n && rc == PFT_OK; j++)
+            for (int i = 0; i < chunks_n && rc == PFT_OK; i++) {
+                std::fill(slots.begin(), slots.end(), 0.0);
+                for (int u = 0; u < t && i * t + u < m; u++) slots[2 * u] = H[(size_t)(i * t + u) * n + j];
+                pft_pt* p = nullptr;
+                rc = pft_encode(c, slots.data(), t, c->prm.scale, level, &p);
+                if (rc == PFT_OK) hp.push_back(p);
+            }
+        for (int j = 0; j < n && rc == PFT_OK; j++) {
+            std::fill(slots.begin(), slots.end(), 0.0);
+            for (int u = 0; u < cl; u++) slots[2 * u] = O[(size_t)j * cl + u];
+            pft_pt* p = nullptr;
+            rc = pft_encode(c, slots.data(), t, c->prm.scale, level - 1, &p);
+            if (rc == PFT_OK) op.push_back(p);
+        }
+        if (rc != PFT_OK) {
+            cleanup();
+            fail(rc, c->err);
+        }
+        std::unique_ptr<pft_ft_model> M(new pft_ft_model());
+        M->ctx = c;
+        M->m = m;
+        M->n = n;
+        M->c = cl;
+        M->chunks = chunks_n;
+        M->level = level;
+        M->H = hp;
+        M->O = op;
+        *out = M.release();
+    });
+}
+
+int pft_ft_model_destroy(pft_ft_model* M) {
+    if (!M) return PFT_OK;
+    for (auto p : M->H) pft_pt_destroy(p);
+    for (auto p : M->O) pft_pt_destroy(p);
+    delete M;
+    return PFT_OK;
+}
+
+int pft_fasttext_infer(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int n_chunks, pft_ct* scores) {
+    return guard(c, [&] {
+        NEED(c && v && scores, PFT_ERR_ARG, "bad arguments");
+        fasttext_batch(c, M, v, n_chunks, 1, &scores);
+    });
+}
+
+int pft_fasttext_infer_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int n_chunks, int B,
+                             pft_ct* const* scores) {
+    return guard(c, [&] {
+        NEED(c && v && scores && B >= 1, PFT_ERR_ARG, "bad arguments");
+        fasttext_batch(c, M, v, n_chunks, B, scores);
+    });
+}
+
+int pft_fasttext_train_step(pft_ctx* c, pft_ft_model*, const pft_ct* const*, int) {
+    if (c) c->err = "encrypted training (Algorithm 5) is not implemented";
+    return PFT_ERR_NOT_IMPLEMENTED;
+}
+
+}  // extern "C"

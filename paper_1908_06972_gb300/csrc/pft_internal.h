@@ -1,0 +1,152 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/privft.h"
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+typedef int64_t i64;
+
+namespace pft {
+
+constexpr int kMaxPrimes = 68;   // L + k
+constexpr int kMaxLimbs = 60;    // L
+constexpr int kMaxSpecial = 8;   // k
+constexpr int kMaxAlpha = 8;     // primes per digit
+constexpr int kMaxSet = 256;     // polynomials per launch descriptor
+constexpr int kMaxBconv = 96;    // basis-conversion jobs per launch (by-value parameters)
+
+// Per-prime constants on the device.
+//   Barrett (single 64-bit word): s = bitlen(q) - 1, mu = floor(2^(64+s) / q);
+//   valid for inputs x < 2^(64+s) = 2^(63+bitlen).
+struct DPrime {
+    u64 q;
+    u64 mu;
+    u64 r64;  // 2^64 mod q
+    u32 s;
+    u32 pad;
+};
+
+// A polynomial in a launch: `nlimbs` consecutive limbs of N words at `ptr`.
+// Limb r is reduced modulo prime index  (r < split ? first + r : base2 + r - split).
+struct PolyRef {
+    u64* ptr;
+    uint16_t nlimbs;
+    uint16_t first;
+    uint16_t split;
+    uint16_t base2;
+};
+struct PolySet {
+    int count;
+    int max_limbs;
+    PolyRef p[kMaxSet];
+};
+
+__host__ __device__ inline int prime_of(const PolyRef& r, int limb) {
+    return limb < r.split ? r.first + limb : r.base2 + (limb - r.split);
+}
+
+// Device tables of one context (all device pointers).
+struct DevTables {
+    int logn;
+    int n;
+    DPrime* primes;        // [P]
+    ulonglong2* fwd;       // [P][N] (psi^brv(i), shoup)
+    ulonglong2* inv;       // [P][N] (psi^-brv(i), shoup)
+    ulonglong2* ninv;      // [P] (N^-1, shoup)
+    ulonglong2* inv1ninv;  // [P] (psi^-brv(1) N^-1, shoup)
+};
+
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define PFT_CUDA(x) ::pft::check_cuda((x), #x)
+#define PFT_LAUNCH_CHECK(what) ::pft::check_cuda(cudaGetLastError(), what)
+
+// Launch accounting: every kernel launch is counted; launches whose name starts
+// with the prefix given to pft_prof_start are bracketed by CUDA events on their stream.
+// `work` is the launch's algorithmic work (butterflies for transforms, bytes for the
+// memory-bound kernels), summed over the timed launches.
+void prof_begin(const char* name, cudaStream_t st, double work);
+void prof_end(const char* name, cudaStream_t st);
+struct ProfScope {
+    const char* n;
+    cudaStream_t s;
+    ProfScope(const char* n_, cudaStream_t s_, double w) : n(n_), s(s_) { prof_begin(n, s, w); }
+    ~ProfScope() { prof_end(n, s); }
+};
+#define PFT_PROF(name, st, work) ::pft::ProfScope pft_prof_scope_(name, st, work)
+inline double set_limbs(const PolySet& s) {
+    double t = 0;
+    for (int i = 0; i < s.count; i++) t += s.p[i].nlimbs;
+    return t;
+}
+
+// ---- kernels (launchers) ------------------------------------------------------------
+// Negacyclic transform of every limb of every polynomial of `out` (input from `in`,
+// which may be the same set).
+void ntt_forward(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
+void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
+
+enum class EwOp { Add, Sub, Mul, Neg, Copy };
+// out[i] = a[i] (op) b[i] per limb (b ignored for Neg/Copy).
+void ew_binary(const DevTables& t, EwOp op, const PolySet& a, const PolySet& b, const PolySet& out, cudaStream_t st);
+// HMUL tensor: a, b refs point at ciphertexts [2][l][N]; d refs at [3][l][N] (nlimbs = l).
+void ew_tensor(const DevTables& t, const PolySet& a, const PolySet& b, const PolySet& d, cudaStream_t st);
+// O[p] = sum_{k<K} A[p K + k] * B[(shared ? 0 : p K) + k]; device pointer tables; l limbs each.
+void ew_dot(const DevTables& t, const u64* const* A, const u64* const* B, u64* const* O, int n_out, int K,
+            bool b_shared, int l, cudaStream_t st);
+// out = acc + ((x + c) - y) * s per limb, consts_dev[3 limb + {0,1,2}] = {c, s, s_shoup};
+// y may be null (taken as 0), acc may be null.
+void sub_scale(const DevTables& t, const PolySet& x, const PolySet* y, const PolySet* acc, const PolySet& out,
+               const u64* consts_dev, cudaStream_t st);
+// Galois automorphism X -> X^g in the evaluation layout.
+void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g, cudaStream_t st);
+
+// Fast basis conversion job: from ns source limbs (primes src_p0 ..) to rows
+// [0, nrows) \ [skip_lo, skip_hi) of dst; target prime of row m: m < split ? m : base2 + m - split.
+struct BconvJob {
+    const u64* src;
+    u64* dst;
+    const u64* table;  // [ns]{qhat_inv, shoup} then [ns][nrows] qhat mod target
+    int ns, src_p0, nrows, skip_lo, skip_hi, split, base2, pad;
+};
+void bconv(const DevTables& t, const BconvJob* jobs_host, int n_jobs, cudaStream_t st);  // jobs: host array
+
+// Key inner product for B inputs at level l sharing one key [beta_max][2][L+k][N]:
+//   u[b][pol][m] = sum_j ext[b][j][m] * key[j][pol][row(m)],  ext: [B][beta][l+k][N], u: [B][2][l+k][N].
+void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k, int beta,
+              cudaStream_t st);
+// r = (last + floor(p/2)) mod p for p = prime nlimbs(out), reduced into every limb of out.
+void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st);
+
+// Sampling (ChaCha20 streams, nonce (dom, obj, sub)).
+void sample_uniform(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 sub_base, const PolySet& out,
+                    cudaStream_t st);  // sub = sub_base + prime index of the limb
+void sample_small(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 sub, int kind, const u32* cdt,
+                  int nt, i64* out_dev, cudaStream_t st);  // kind 0 = ternary, 1 = Gaussian
+void reduce_signed(const DevTables& t, const i64* x_dev, const PolySet& out, cudaStream_t st);
+
+// ---- host math (encode.cpp) -----------------------------------------------------------
+std::vector<u64> gen_primes(int logn, int bits, int count, const std::vector<u64>& exclude);
+std::vector<u32> gauss_cdt(double sigma, int* tail);
+u64 mulmod_host(u64 a, u64 b, u64 q);
+u64 powmod_host(u64 a, u64 e, u64 q);
+u64 invmod_host(u64 a, u64 q);
+u64 root_2n_host(u64 q, int logn);
+// Encode slots (re, im interleaved, n_slots) -> rounded integer coefficients.
+bool encode_slots(int logn, const double* re_im, int n_slots, double scale, std::vector<i64>& coeffs);
+// Decode: CRT-centered coefficients as doubles -> slots.
+void decode_coeffs(int logn, const std::vector<double>& coeffs, double scale, double* re_im, int n_slots);
+// CRT of [l][N] residues to centered doubles.
+void crt_to_double(const std::vector<u64>& primes, const u64* rows, int n, std::vector<double>& out);
+
+}  // namespace pft

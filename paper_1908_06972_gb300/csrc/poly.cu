@@ -1,0 +1,501 @@
+// Limb-wise kernels of the RNS-CKKS evaluator (device side).
+//
+// Every kernel is a grid over (coefficient block, limb, polynomial) on the
+// limb-major [poly][limb][N] layout, moving two 64-bit words per thread with
+// 16-byte accesses.  Residues are canonical in [0, q) at every kernel boundary.
+#include "modarith.cuh"
+
+namespace pft {
+
+static constexpr int kEwThreads = 256;
+
+static dim3 ew_grid(int n, const PolySet& s) {
+    return dim3((unsigned)((n / 2 + kEwThreads - 1) / kEwThreads), (unsigned)s.max_limbs, (unsigned)s.count);
+}
+
+// ---- HADD / sub / pointwise product / negate / copy --------------------------------------
+template <int OP>
+__global__ void k_ew_binary(DevTables t, PolySet a, PolySet b, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
+    const DPrime P = load_prime(t.primes, prime_of(Ro, limb));
+    const size_t off = ((size_t)limb << t.logn) + 2 * (size_t)x2;
+    const ulonglong2 va = *reinterpret_cast<const ulonglong2*>(a.p[poly].ptr + off);
+    ulonglong2 vb = make_ulonglong2(0, 0);
+    if (OP <= 2) vb = *reinterpret_cast<const ulonglong2*>(b.p[poly].ptr + off);
+    ulonglong2 r;
+    if (OP == 0) {
+        r.x = addmod(va.x, vb.x, P.q);
+        r.y = addmod(va.y, vb.y, P.q);
+    } else if (OP == 1) {
+        r.x = submod(va.x, vb.x, P.q);
+        r.y = submod(va.y, vb.y, P.q);
+    } else if (OP == 2) {
+        r.x = mulmod(va.x, vb.x, P);
+        r.y = mulmod(va.y, vb.y, P);
+    } else if (OP == 3) {
+        r.x = va.x ? P.q - va.x : 0;
+        r.y = va.y ? P.q - va.y : 0;
+    } else {
+        r = va;
+    }
+    *reinterpret_cast<ulonglong2*>(Ro.ptr + off) = r;
+}
+
+void ew_binary(const DevTables& t, EwOp op, const PolySet& a, const PolySet& b, const PolySet& out,
+               cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 g = ew_grid(t.n, out);
+    PFT_PROF(op == EwOp::Mul ? "ew.mul" : (op == EwOp::Copy ? "ew.copy" : "ew.add"), st,
+             set_limbs(out) * t.n * 8.0 * (op == EwOp::Copy || op == EwOp::Neg ? 2 : 3));
+    switch (op) {
+        case EwOp::Add: k_ew_binary<0><<<g, kEwThreads, 0, st>>>(t, a, b, out); break;
+        case EwOp::Sub: k_ew_binary<1><<<g, kEwThreads, 0, st>>>(t, a, b, out); break;
+        case EwOp::Mul: k_ew_binary<2><<<g, kEwThreads, 0, st>>>(t, a, b, out); break;
+        case EwOp::Neg: k_ew_binary<3><<<g, kEwThreads, 0, st>>>(t, a, b, out); break;
+        case EwOp::Copy: k_ew_binary<4><<<g, kEwThreads, 0, st>>>(t, a, b, out); break;
+    }
+    PFT_LAUNCH_CHECK("ew_binary");
+}
+
+// ---- HMUL tensor: d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 (evaluation domain) -----------
+// set a / b / d hold one ref per ciphertext: ptr to [2][l][N] (a, b) or [3][l][N] (d).
+__global__ void k_tensor(DevTables t, PolySet a, PolySet b, PolySet d) {
+    const int c = blockIdx.z, limb = blockIdx.y;
+    const int l = d.p[c].nlimbs;
+    if (limb >= l) return;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
+    const DPrime P = load_prime(t.primes, limb);
+    const size_t off = ((size_t)limb << t.logn) + 2 * (size_t)x2;
+    const size_t ps = (size_t)l << t.logn;
+    const u64* A = a.p[c].ptr;
+    const u64* B = b.p[c].ptr;
+    u64* D = d.p[c].ptr;
+    const ulonglong2 a0 = *reinterpret_cast<const ulonglong2*>(A + off);
+    const ulonglong2 a1 = *reinterpret_cast<const ulonglong2*>(A + ps + off);
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(B + off);
+    const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(B + ps + off);
+    ulonglong2 r0, r1, r2;
+    r0.x = mulmod(a0.x, b0.x, P);
+    r0.y = mulmod(a0.y, b0.y, P);
+    r2.x = mulmod(a1.x, b1.x, P);
+    r2.y = mulmod(a1.y, b1.y, P);
+    U128 s = mul_wide(a0.x, b1.x);
+    mac_wide(s, a1.x, b0.x);
+    r1.x = barrett_reduce(s.hi, s.lo, P);
+    s = mul_wide(a0.y, b1.y);
+    mac_wide(s, a1.y, b0.y);
+    r1.y = barrett_reduce(s.hi, s.lo, P);
+    *reinterpret_cast<ulonglong2*>(D + off) = r0;
+    *reinterpret_cast<ulonglong2*>(D + ps + off) = r1;
+    *reinterpret_cast<ulonglong2*>(D + 2 * ps + off) = r2;
+}
+
+void ew_tensor(const DevTables& t, const PolySet& a, const PolySet& b, const PolySet& d, cudaStream_t st) {
+    if (d.count == 0) return;
+    PFT_PROF("tensor", st, set_limbs(d) * t.n * 8.0 * 7);
+    k_tensor<<<ew_grid(t.n, d), kEwThreads, 0, st>>>(t, a, b, d);
+    PFT_LAUNCH_CHECK("tensor");
+}
+
+// ---- dot products: out[p] = sum_k a[p*K + k] * b[(shared ? 0 : p*K) + k] --------------------
+// Pointer tables live in device memory (they can be long).  All polynomials carry
+// `l` limbs of the ciphertext chain.  128-bit accumulation, reduced every 8 terms.
+__global__ void k_dot(DevTables t, const u64* const* A, const u64* const* Bp, u64* const* O, int K, int b_shared,
+                      int l) {
+    const int p = blockIdx.z, limb = blockIdx.y;
+    if (limb >= l) return;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
+    const DPrime P = load_prime(t.primes, limb);
+    const size_t off = ((size_t)limb << t.logn) + 2 * (size_t)x2;
+    U128 sx = {0, 0}, sy = {0, 0};
+    for (int k = 0; k < K; k++) {
+        const ulonglong2 va = *reinterpret_cast<const ulonglong2*>(A[(size_t)p * K + k] + off);
+        const ulonglong2 vb = *reinterpret_cast<const ulonglong2*>(Bp[(b_shared ? 0 : (size_t)p * K) + k] + off);
+        mac_wide(sx, va.x, vb.x);
+        mac_wide(sy, va.y, vb.y);
+        if ((k & 7) == 7) {
+            sx.lo = barrett_reduce(sx.hi, sx.lo, P);
+            sx.hi = 0;
+            sy.lo = barrett_reduce(sy.hi, sy.lo, P);
+            sy.hi = 0;
+        }
+    }
+    ulonglong2 r;
+    r.x = barrett_reduce(sx.hi, sx.lo, P);
+    r.y = barrett_reduce(sy.hi, sy.lo, P);
+    *reinterpret_cast<ulonglong2*>(O[p] + off) = r;
+}
+
+void ew_dot(const DevTables& t, const u64* const* A, const u64* const* B, u64* const* O, int n_out, int K,
+            bool b_shared, int l, cudaStream_t st) {
+    if (n_out == 0) return;
+    dim3 g((unsigned)((t.n / 2 + kEwThreads - 1) / kEwThreads), (unsigned)l, (unsigned)n_out);
+    PFT_PROF("dot", st, (double)n_out * l * t.n * 8.0 * (2 * K + 1));
+    k_dot<<<g, kEwThreads, 0, st>>>(t, A, B, O, K, b_shared ? 1 : 0, l);
+    PFT_LAUNCH_CHECK("dot");
+}
+
+// ---- out = acc + (x - y) * s  (s per limb, Shoup pair) ---------------------------------
+// Used by ModDown (s = P^-1, acc = the other tensor part or the rotated c0) and by
+// rescale (x = c + h, y = NTT(r), s = p^-1): consts[limb] = {add_to_x, s, s_shoup}.
+__global__ void k_sub_scale(DevTables t, PolySet x, PolySet y, PolySet acc, PolySet out, const u64* consts,
+                            int has_y, int has_acc) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
+    const int pi = prime_of(Ro, limb);
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 c = __ldg(&consts[3 * limb]);
+    const u64 s = __ldg(&consts[3 * limb + 1]);
+    const u64 sp = __ldg(&consts[3 * limb + 2]);
+    const size_t off = ((size_t)limb << t.logn) + 2 * (size_t)x2;
+    const ulonglong2 vx = *reinterpret_cast<const ulonglong2*>(x.p[poly].ptr + off);
+    ulonglong2 vy = make_ulonglong2(0, 0);
+    if (has_y) vy = *reinterpret_cast<const ulonglong2*>(y.p[poly].ptr + off);
+    ulonglong2 r;
+    r.x = mul_shoup(submod(addmod(vx.x, c, q), vy.x, q), s, sp, q);
+    r.y = mul_shoup(submod(addmod(vx.y, c, q), vy.y, q), s, sp, q);
+    if (has_acc) {
+        const ulonglong2 va = *reinterpret_cast<const ulonglong2*>(acc.p[poly].ptr + off);
+        r.x = addmod(r.x, va.x, q);
+        r.y = addmod(r.y, va.y, q);
+    }
+    *reinterpret_cast<ulonglong2*>(Ro.ptr + off) = r;
+}
+
+void sub_scale(const DevTables& t, const PolySet& x, const PolySet* y, const PolySet* acc, const PolySet& out,
+               const u64* consts_dev, cudaStream_t st) {
+    if (out.count == 0) return;
+    PFT_PROF("sub_scale", st, set_limbs(out) * t.n * 8.0 * (2 + (y ? 1 : 0) + (acc ? 1 : 0)));
+    k_sub_scale<<<ew_grid(t.n, out), kEwThreads, 0, st>>>(t, x, y ? *y : out, acc ? *acc : out, out, consts_dev,
+                                                         y ? 1 : 0, acc ? 1 : 0);
+    PFT_LAUNCH_CHECK("sub_scale");
+}
+
+// ---- Galois automorphism X -> X^g in the evaluation layout ---------------------------------
+// Entry i holds a(psi^(2 brv(i) + 1)); a(X^g) there equals a(psi^((2 brv(i) + 1) g)),
+// i.e. entry brv(((2 brv(i) + 1) g mod 2N - 1) / 2) of the input.
+__global__ void k_automorph(DevTables t, PolySet in, PolySet out, u64 g) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= t.n) return;
+    const int logn = t.logn;
+    const u32 mask2n = (2u << logn) - 1;
+    const u32 bi = __brev((u32)i) >> (32 - logn);
+    const u32 e = (u32)(((u64)(2 * bi + 1) * g) & mask2n);
+    const u32 src = __brev((e - 1) >> 1) >> (32 - logn);
+    const size_t base = (size_t)limb << logn;
+    Ro.ptr[base + i] = __ldg(in.p[poly].ptr + base + src);
+}
+
+void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g, cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("automorph", st, set_limbs(out) * t.n * 16.0);
+    k_automorph<<<grid, 256, 0, st>>>(t, in, out, g);
+    PFT_LAUNCH_CHECK("automorph");
+}
+
+// ---- fast basis conversion (ModUp of one digit, or ModDown from the special primes) ------
+// For each coefficient: y_i = x_i * qhat_i^-1 mod s_i (Shoup), then for every target row m
+// (rows [0, nrows) except [skip_lo, skip_hi)):  out_m = sum_i y_i * (qhat_i mod t_m) mod t_m.
+// Target prime of row m: m < split ? m : base2 + m - split.  Table: [ns] {inv, inv_shoup},
+// then [ns][nrows] qhat_i mod t_m.
+struct BconvBatch {
+    BconvJob j[kMaxBconv];
+};
+__global__ void k_bconv(DevTables t, BconvBatch jobs) {
+    const BconvJob& J = jobs.j[blockIdx.y];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= t.n) return;
+    const int logn = t.logn;
+    u64 y[kMaxAlpha > kMaxSpecial ? kMaxAlpha : kMaxSpecial];
+#pragma unroll
+    for (int i = 0; i < kMaxAlpha; i++) {
+        if (i < J.ns) {
+            const u64 q = __ldg(&t.primes[J.src_p0 + i].q);
+            const u64 v = __ldg(J.src + ((size_t)i << logn) + x);
+            y[i] = mul_shoup(v, __ldg(&J.table[2 * i]), __ldg(&J.table[2 * i + 1]), q);
+        }
+    }
+    const u64* T = J.table + 2 * J.ns;
+    for (int m = 0; m < J.nrows; m++) {
+        if (m >= J.skip_lo && m < J.skip_hi) continue;
+        const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
+        U128 acc = {0, 0};
+#pragma unroll
+        for (int i = 0; i < kMaxAlpha; i++)
+            if (i < J.ns) mac_wide(acc, y[i], __ldg(&T[(size_t)i * J.nrows + m]));
+        J.dst[((size_t)m << logn) + x] = barrett_reduce(acc.hi, acc.lo, P);
+    }
+}
+
+void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st) {
+    for (int a = 0; a < n_jobs; a += kMaxBconv) {
+        const int cnt = n_jobs - a < kMaxBconv ? n_jobs - a : kMaxBconv;
+        BconvBatch b;
+        for (int i = 0; i < cnt; i++) b.j[i] = jobs[a + i];
+        dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)cnt);
+        PFT_PROF("bconv", st, 0.0);
+        k_bconv<<<grid, 256, 0, st>>>(t, b);
+        PFT_LAUNCH_CHECK("bconv");
+    }
+}
+
+// ---- key-switching inner product ---------------------------------------------------------
+//   u[b][pol][m] = sum_{j < beta} ext[b][j][m] * key[j][pol][row(m)],  m < l + k,
+//   row(m) = m (m < l) or L + m - l (special rows).  The key slice of coefficient x is
+// held in registers and reused for all B inputs, so each key word is read once per batch.
+template <int BMAX>
+__global__ void k_ks_inner(DevTables t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k,
+                           int beta) {
+    const int m = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= t.n) return;
+    const int logn = t.logn;
+    const int E = l + k;
+    const int row = m < l ? m : L + m - l;
+    const int rows_total = L + k;
+    const DPrime P = load_prime(t.primes, row);
+    u64 kb[BMAX], ka[BMAX];
+#pragma unroll
+    for (int j = 0; j < BMAX; j++) {
+        if (j < beta) {
+            kb[j] = __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x);
+            ka[j] = __ldg(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + x);
+        }
+    }
+    for (int b = 0; b < B; b++) {
+        const u64* eb = ext + ((size_t)b * beta * E << logn);
+        U128 s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+        for (int j = 0; j < BMAX; j++) {
+            if (j < beta) {
+                const u64 v = __ldg(eb + (((size_t)j * E + m) << logn) + x);
+                mac_wide(s0, v, kb[j]);
+                mac_wide(s1, v, ka[j]);
+                if ((j & 7) == 7) {
+                    s0.lo = barrett_reduce(s0.hi, s0.lo, P);
+                    s0.hi = 0;
+                    s1.lo = barrett_reduce(s1.hi, s1.lo, P);
+                    s1.hi = 0;
+                }
+            }
+        }
+        u64* ub = u + ((size_t)b * 2 * E << logn);
+        ub[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
+        ub[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
+    }
+}
+
+// Same sum for any number of digits, re-reading the key for every input.
+__global__ void k_ks_inner_generic(DevTables t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k,
+                                   int beta) {
+    const int m = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= t.n) return;
+    const int logn = t.logn;
+    const int E = l + k;
+    const int row = m < l ? m : L + m - l;
+    const int rows_total = L + k;
+    const DPrime P = load_prime(t.primes, row);
+    for (int b = 0; b < B; b++) {
+        const u64* eb = ext + ((size_t)b * beta * E << logn);
+        U128 s0 = {0, 0}, s1 = {0, 0};
+        for (int j = 0; j < beta; j++) {
+            const u64 v = __ldg(eb + (((size_t)j * E + m) << logn) + x);
+            mac_wide(s0, v, __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x));
+            mac_wide(s1, v, __ldg(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + x));
+            if ((j & 7) == 7) {
+                s0.lo = barrett_reduce(s0.hi, s0.lo, P);
+                s0.hi = 0;
+                s1.lo = barrett_reduce(s1.hi, s1.lo, P);
+                s1.hi = 0;
+            }
+        }
+        u64* ub = u + ((size_t)b * 2 * E << logn);
+        ub[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
+        ub[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
+    }
+}
+
+void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k, int beta,
+              cudaStream_t st) {
+    if (B == 0) return;
+    dim3 grid((unsigned)((t.n + 127) / 128), (unsigned)(l + k));
+    PFT_PROF("ks_inner", st, (double)t.n * 8.0 * (2.0 * beta * (l + k) + (double)B * beta * (l + k) + 2.0 * B * (l + k)));
+    if (beta <= 4) k_ks_inner<4><<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    else if (beta <= 8) k_ks_inner<8><<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    else if (beta <= 16) k_ks_inner<16><<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    else k_ks_inner_generic<<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    PFT_LAUNCH_CHECK("ks_inner");
+}
+
+// ---- rescale broadcast: r = (c_{l-1} + h) mod p, reduced into each lower prime ----------
+// last: coefficient-form last limb of each polynomial; out: [l-1][N] per polynomial.
+__global__ void k_rescale_bcast(DevTables t, PolySet last, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= t.n) return;
+    const int lp = Ro.nlimbs;  // index of the dropped prime
+    const u64 p = __ldg(&t.primes[lp].q);
+    u64 r = __ldg(last.p[poly].ptr + x) + (p >> 1);
+    if (r >= p) r -= p;
+    const DPrime P = load_prime(t.primes, limb);
+    Ro.ptr[((size_t)limb << t.logn) + x] = reduce64(r, P);
+}
+
+void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("rescale_bcast", st, set_limbs(out) * t.n * 8.0);
+    k_rescale_bcast<<<grid, 256, 0, st>>>(t, last, out);
+    PFT_LAUNCH_CHECK("rescale_bcast");
+}
+
+// ---- ChaCha20 sampler (RFC 8439 block function, counter mode) -----------------------------
+__device__ __forceinline__ u32 rotl(u32 x, int n) { return __funnelshift_l(x, x, n); }
+#define PFT_QR(a, b, c, d)                \
+    a += b; d ^= a; d = rotl(d, 16);      \
+    c += d; b ^= c; b = rotl(b, 12);      \
+    a += b; d ^= a; d = rotl(d, 8);       \
+    c += d; b ^= c; b = rotl(b, 7);
+
+__device__ void chacha_block(const u32 key[8], u32 ctr, u32 n0, u32 n1, u32 n2, u64 outw[8]) {
+    u32 s[16], x[16];
+    s[0] = 0x61707865u; s[1] = 0x3320646eu; s[2] = 0x79622d32u; s[3] = 0x6b206574u;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[4 + i] = key[i];
+    s[12] = ctr; s[13] = n0; s[14] = n1; s[15] = n2;
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = s[i];
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        PFT_QR(x[0], x[4], x[8], x[12]);
+        PFT_QR(x[1], x[5], x[9], x[13]);
+        PFT_QR(x[2], x[6], x[10], x[14]);
+        PFT_QR(x[3], x[7], x[11], x[15]);
+        PFT_QR(x[0], x[5], x[10], x[15]);
+        PFT_QR(x[1], x[6], x[11], x[12]);
+        PFT_QR(x[2], x[7], x[8], x[13]);
+        PFT_QR(x[3], x[4], x[9], x[14]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) outw[i] = (u64)(x[2 * i] + s[2 * i]) | ((u64)(x[2 * i + 1] + s[2 * i + 1]) << 32);
+}
+
+struct SeedKey {
+    u32 w[8];
+};
+static SeedKey seed_key(const u64 seed[4]) {
+    SeedKey k;
+    for (int i = 0; i < 4; i++) {
+        k.w[2 * i] = (u32)(seed[i] & 0xffffffffu);
+        k.w[2 * i + 1] = (u32)(seed[i] >> 32);
+    }
+    return k;
+}
+
+// uniform mod q: block b (counter b) gives coefficients 4b..4b+3 from word pairs.
+__global__ void k_sample_uniform(DevTables t, SeedKey key, u32 dom, u32 obj, u32 sub_base, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * b >= t.n) return;
+    const int pi = prime_of(Ro, limb);
+    const DPrime P = load_prime(t.primes, pi);
+    u64 w[8];
+    chacha_block(key.w, (u32)b, dom, obj, sub_base + (u32)pi, w);
+    u64* dst = Ro.ptr + ((size_t)limb << t.logn) + 4 * (size_t)b;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        // (hi 2^64 + lo) mod q = ((hi mod q) (2^64 mod q) + lo) mod q; the sum is below
+        // q^2 + 2^64 < 2^(63 + bitlen(q)), inside the Barrett bound.
+        const u64 hr = reduce64(w[2 * c + 1], P);
+        U128 acc = mul_wide(hr, P.r64);
+        acc.lo += w[2 * c];
+        acc.hi += (acc.lo < w[2 * c]) ? 1 : 0;
+        dst[c] = barrett_reduce(acc.hi, acc.lo, P);
+    }
+}
+
+void sample_uniform(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 sub_base, const PolySet& out,
+                    cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n / 4 + 127) / 128), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("sample", st, 0.0);
+    k_sample_uniform<<<grid, 128, 0, st>>>(t, seed_key(seed), dom, obj, sub_base, out);
+    PFT_LAUNCH_CHECK("sample_uniform");
+}
+
+struct Cdt {
+    u32 v[64];
+    int n;
+};
+// ternary (kind 0): word c mod 3 - 1;  Gaussian (kind 1): magnitude = #{j : top32(w) >= T_j}, sign = w & 1.
+__global__ void k_sample_small(DevTables t, SeedKey key, u32 dom, u32 obj, u32 sub, int kind, Cdt cdt, i64* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (8 * b >= t.n) return;
+    u64 w[8];
+    chacha_block(key.w, (u32)b, dom, obj, sub, w);
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        i64 v;
+        if (kind == 0) {
+            v = (i64)(w[c] % 3) - 1;
+        } else {
+            const u32 top = (u32)(w[c] >> 32);
+            i64 mag = 0;
+            for (int j = 0; j < cdt.n; j++) mag += (top >= cdt.v[j]) ? 1 : 0;
+            v = (w[c] & 1) ? -mag : mag;
+        }
+        out[8 * b + c] = v;
+    }
+}
+
+void sample_small(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 sub, int kind, const u32* cdt,
+                  int nt, i64* out_dev, cudaStream_t st) {
+    Cdt c;
+    c.n = nt;
+    for (int i = 0; i < nt && i < 64; i++) c.v[i] = cdt[i];
+    dim3 grid((unsigned)((t.n / 8 + 127) / 128));
+    PFT_PROF("sample", st, 0.0);
+    k_sample_small<<<grid, 128, 0, st>>>(t, seed_key(seed), dom, obj, sub, kind, c, out_dev);
+    PFT_LAUNCH_CHECK("sample_small");
+}
+
+// signed integer polynomial -> residues in every limb of every polynomial of `out`
+__global__ void k_reduce_signed(DevTables t, const i64* x, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= t.n) return;
+    const DPrime P = load_prime(t.primes, prime_of(Ro, limb));
+    const i64 v = x[c];
+    const u64 m = reduce64((u64)(v < 0 ? -v : v), P);
+    Ro.ptr[((size_t)limb << t.logn) + c] = (v < 0 && m) ? P.q - m : m;
+}
+
+void reduce_signed(const DevTables& t, const i64* x_dev, const PolySet& out, cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("reduce_signed", st, 0.0);
+    k_reduce_signed<<<grid, 256, 0, st>>>(t, x_dev, out);
+    PFT_LAUNCH_CHECK("reduce_signed");
+}
+
+}  // namespace pft

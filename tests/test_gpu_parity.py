@@ -1,0 +1,251 @@
+"""GPU (through the C ABI) against the oracle, element by element.
+
+Bar: bit-exact canonical residues in coefficient form for every integer result
+(keys, encryptions, HADD, HMULPLAIN, HMUL+relinearisation, ROTATE, RESCALE,
+TotalSum, the fastText sequence); encoding within one unit per coefficient (it is
+FP64 and the two sides use different FFTs); decrypted scores within 2^-20 of the
+FP64 plaintext computation.  Sizes: N = 2^12 (one-pass transform) and N = 2^16
+(two-pass transform, several tiles, digits with a ragged last one)."""
+import numpy as np
+import pytest
+
+from oracle import _lib as OC
+from oracle import ckks as OK
+from oracle import fasttext as OF
+from oracle import params as OP
+from paper_1908_06972_gb300 import synth
+
+from .pairs import Pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p1(gpu):
+    # toy smoke-test chain: N = 2^12, q0 60-bit, two 40-bit primes, one 60-bit special prime,
+    # one prime per digit (the paper's "one key holds l ciphertexts" structure)
+    p = Pair(gpu, 12, 3, 1, 1, rot_steps=[1, -1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 3])
+    yield p
+    p.close()
+
+
+@pytest.fixture(scope="module")
+def p16(gpu):
+    # N = 2^16, 6 primes (60 + 5 x 50), 2 special, digits of 4 primes (last digit ragged)
+    p = Pair(gpu, 16, 6, 2, 4, mid_bits=50, rot_steps=[1, 5, -1])
+    yield p
+    p.close()
+
+
+# ---- transform layout ---------------------------------------------------------------------
+@pytest.mark.parametrize("logn", [12, 16])
+def test_ntt_layout_matches_definition(gpu, logn):
+    import torch
+    p = Pair(gpu, logn, 2, 1, 1, gpu_keys=False, rot_steps=())
+    try:
+        info = gpu.pft_ctx_info(p.ctx)
+        primes = info["primes"]
+        n = 1 << logn
+        x = synth.residues(5, primes, n, polys=2)  # 2 polys x 3 rows (2 q's + 1 special)
+        x[0, 0, :4] = [0, 1, primes[0] - 1, 0]
+        t = torch.from_numpy(x.view(np.int64).copy()).cuda()
+        gpu.pft_ntt(p.ctx, t.data_ptr(), 2, 3, 0)
+        y = t.cpu().numpy().view(np.uint64)
+        idx = np.arange(n) if logn <= 12 else np.r_[0:64, n // 2 - 32:n // 2 + 32, n - 64:n]
+        for poly in range(2):
+            for r, q in enumerate(primes):
+                want = OC.eval_at(x[poly, r], OP.root_2n(q, logn), q, logn, idx)
+                assert np.array_equal(y[poly, r][idx], want), (poly, r)
+        gpu.pft_ntt(p.ctx, t.data_ptr(), 2, 3, 1)
+        assert np.array_equal(t.cpu().numpy().view(np.uint64), x)
+    finally:
+        p.close()
+
+
+# ---- keys and encryption ---------------------------------------------------------------------
+def test_keys_bit_exact(p1):
+    assert np.array_equal(p1.pft.pft_secret_export(p1.ctx), p1.orc.s)
+    assert np.array_equal(p1.pft.pft_key_export(p1.ctx, 0), p1.orc.keys[0])
+    g = OK.galois_element(1, p1.N)
+    assert np.array_equal(p1.pft.pft_key_export(p1.ctx, g), p1.orc.keys[g])
+
+
+def test_keys_bit_exact_n16(p16):
+    assert np.array_equal(p16.pft.pft_key_export(p16.ctx, 0), p16.orc.keys[0])
+    g = OK.galois_element(5, p16.N)
+    assert np.array_equal(p16.pft.pft_key_export(p16.ctx, g), p16.orc.keys[g])
+
+
+@pytest.mark.parametrize("level", [3, 2, 1])
+def test_encrypt_bit_exact(p1, level):
+    o = p1.orc
+    pt_o = o.encode(synth.slots(level, p1.N // 2), level=level)
+    pt_g = p1.pt(pt_o)
+    for mode, fn in ((p1.pft.PFT_ENC_SK, o.encrypt_sk), (p1.pft.PFT_ENC_PK, o.encrypt_pk)):
+        h = p1.pft.pft_encrypt(p1.ctx, pt_g, mode, 77 + level)
+        p1.handles.append(("ct", h))
+        p1.assert_equal(h, fn(pt_o, 77 + level), "encrypt mode %d" % mode)
+        dec = p1.pft.pft_decrypt(p1.ctx, h)
+        p1.handles.append(("pt", dec))
+        assert np.array_equal(p1.pft.pft_pt_export(p1.ctx, dec), o.decrypt(fn(pt_o, 77 + level)).m)
+
+
+def test_encode_within_one_unit(p1):
+    z = synth.slots(3, p1.N // 2)
+    h = p1.pft.pft_encode(p1.ctx, z, 2.0 ** 40, 3)
+    p1.handles.append(("pt", h))
+    got = OK.crt_centered(p1.pft.pft_pt_export(p1.ctx, h), p1.orc.q[:3])
+    want = OK.crt_centered(p1.orc.encode(z).m, p1.orc.q[:3])
+    diff = np.array([abs(int(a) - int(b)) for a, b in zip(got, want)])
+    assert diff.max() <= 1
+    assert (diff > 0).sum() <= p1.N // 100
+    zz = p1.pft.pft_decode(p1.ctx, h, p1.N // 2)
+    assert np.max(np.abs(zz - z)) < 2.0 ** -30
+
+
+# ---- operations -------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cts1(p1):
+    o = p1.orc
+    za, zb = synth.slots(101, p1.N // 2), synth.slots(102, p1.N // 2)
+    a, b = o.encrypt_sk(o.encode(za), 1), o.encrypt_pk(o.encode(zb), 2)
+    return za, zb, a, b
+
+
+def test_add_sub_plain_ops_bit_exact(p1, cts1):
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    za, zb, a, b = cts1
+    ga, gb = p1.ct(a), p1.ct(b)
+    out = p1.empty()
+    pf.pft_add(ctx, ga, gb, out)
+    p1.assert_equal(out, o.add(a, b), "add")
+    pf.pft_sub(ctx, ga, gb, out)
+    p1.assert_equal(out, o.sub(a, b), "sub")
+    ptb = o.encode(zb)
+    gp = p1.pt(ptb)
+    pf.pft_mul_plain(ctx, ga, gp, out)
+    p1.assert_equal(out, o.mul_plain(a, ptb), "mul_plain")
+    pf.pft_add_plain(ctx, ga, gp, out)
+    p1.assert_equal(out, o.add_plain(a, ptb), "add_plain")
+
+
+def test_mul_relin_rescale_rotate_bit_exact(p1, cts1):
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    za, zb, a, b = cts1
+    ga, gb = p1.ct(a), p1.ct(b)
+    m = p1.empty()
+    pf.pft_mul_relin(ctx, ga, gb, m)
+    mo = o.mul_relin(a, b)
+    p1.assert_equal(m, mo, "mul_relin")
+    r = p1.empty()
+    pf.pft_rescale(ctx, m, r)
+    ro = o.rescale(mo)
+    p1.assert_equal(r, ro, "rescale")
+    # rescale again (level 2 -> 1), in place (output aliases input)
+    pf.pft_rescale(ctx, r, r)
+    p1.assert_equal(r, o.rescale(ro), "rescale in place")
+    for step in (1, -1, 3):
+        rt = p1.empty()
+        pf.pft_rotate(ctx, ga, step, rt)
+        p1.assert_equal(rt, o.rotate(a, step), "rotate %d" % step)
+    # decrypted meaning (Sec. 2.3): z_a z_b after mul+rescale, left rotation
+    dec = pf.pft_decrypt(ctx, p1.ct(ro))
+    p1.handles.append(("pt", dec))
+    assert np.max(np.abs(pf.pft_decode(ctx, dec, p1.N // 2) - za * zb)) < 2.0 ** -20
+
+
+def test_in_place_ops(p1, cts1):
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    za, zb, a, b = cts1
+    ga, gb = p1.ct(a), p1.ct(b)
+    pf.pft_mul_relin(ctx, ga, gb, ga)
+    p1.assert_equal(ga, o.mul_relin(a, b), "mul_relin in place")
+    gb2 = p1.ct(b)
+    pf.pft_rotate(ctx, gb2, 1, gb2)
+    p1.assert_equal(gb2, o.rotate(b, 1), "rotate in place")
+
+
+def test_errors(p1, cts1):
+    pf, ctx = p1.pft, p1.ctx
+    za, zb, a, b = cts1
+    ga = p1.ct(a)
+    low = p1.ct(p1.orc.rescale(a))
+    out = p1.empty()
+    with pytest.raises(pf.PftError) as e:
+        pf.pft_add(ctx, ga, low, out)
+    assert e.value.code == pf.PFT_ERR_LEVEL_MISMATCH
+    with pytest.raises(pf.PftError) as e:
+        pf.pft_rotate(ctx, ga, 5, out)
+    assert e.value.code == pf.PFT_ERR_NO_KEY
+    with pytest.raises(pf.PftError) as e:
+        pf.pft_fasttext_train_step(ctx, None, [])
+    assert e.value.code == pf.PFT_ERR_NOT_IMPLEMENTED
+
+
+def test_batched_uneven_levels(p1):
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    A, B = [], []
+    for i, lvl in enumerate([3, 2, 3, 1, 2]):
+        A.append(o.encrypt_sk(o.encode(synth.slots(200 + i, 64), level=lvl), 300 + i))
+        B.append(o.encrypt_sk(o.encode(synth.slots(400 + i, 64), level=lvl), 500 + i))
+    gA, gB = [p1.ct(x) for x in A], [p1.ct(x) for x in B]
+    outs = [p1.empty() for _ in A]
+    pf.pft_mul_relin_batch(ctx, gA, gB, outs)
+    for i in range(len(A)):
+        p1.assert_equal(outs[i], o.mul_relin(A[i], B[i]), "batch mul_relin %d" % i)
+    rots = [p1.empty() for _ in A]
+    pf.pft_rotate_batch(ctx, gA, -1, rots)
+    for i in range(len(A)):
+        p1.assert_equal(rots[i], o.rotate(A[i], -1), "batch rotate %d" % i)
+    keep = [i for i in range(len(A)) if A[i].level >= 2]
+    res = [p1.empty() for _ in keep]
+    pf.pft_rescale_batch(ctx, [gA[i] for i in keep], res)
+    for j, i in enumerate(keep):
+        p1.assert_equal(res[j], o.rescale(A[i]), "batch rescale %d" % i)
+
+
+def test_total_sum_and_fasttext_n12(p1):
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    t = p1.N // 2
+    m, n, c = t, 4, 3
+    H, O = synth.fasttext_weights(9, m, n, c)
+    docs = synth.documents(10, m, 2, 20, 60)
+    Hp, Opk = OF.pack_H(H, t), OF.pack_O(O, t)
+    H_o = [[o.encode(Hp[j, 0], level=3)] for j in range(n)]
+    O_o = [o.encode(Opk[j], level=2) for j in range(n)]
+    model = pf.pft_ft_model_import(ctx, [p1.pt(H_o[j][0]) for j in range(n)], [p1.pt(x) for x in O_o], m, n, c)
+    try:
+        v_o = [o.encrypt_sk(o.encode(docs[d], level=3), 900 + d) for d in range(2)]
+        v_g = [p1.ct(x) for x in v_o]
+        scores = [p1.empty() for _ in range(2)]
+        pf.pft_fasttext_infer_batch(ctx, model, v_g, 1, scores)
+        one = p1.empty()
+        pf.pft_fasttext_infer(ctx, model, [v_g[1]], one)
+        for d in range(2):
+            want = OF.encrypted_scores(o, [v_o[d]], H_o, O_o)
+            p1.assert_equal(scores[d], want, "fasttext doc %d" % d)
+            dec = o.decode(o.decrypt(want))[:c].real
+            assert np.max(np.abs(dec - OF.plain_scores(docs[d], H, O))) < 2.0 ** -20
+        p1.assert_equal(one, OF.encrypted_scores(o, [v_o[1]], H_o, O_o), "fasttext single")
+    finally:
+        pf.pft_ft_model_destroy(model)
+
+
+# ---- N = 2^16 ---------------------------------------------------------------------------------
+def test_ops_bit_exact_n16(p16):
+    o, pf, ctx = p16.orc, p16.pft, p16.ctx
+    za, zb = synth.slots(1, 4096), synth.slots(2, 4096)
+    for lvl in (6, 5, 2):
+        a = o.encrypt_sk(o.encode(za, level=lvl), 10 + lvl)
+        b = o.encrypt_pk(o.encode(zb, level=lvl), 20 + lvl)
+        ga, gb = p16.ct(a), p16.ct(b)
+        m = p16.empty()
+        pf.pft_mul_relin(ctx, ga, gb, m)
+        mo = o.mul_relin(a, b)
+        p16.assert_equal(m, mo, "mul_relin n16 l=%d" % lvl)
+        r = p16.empty()
+        pf.pft_rescale(ctx, m, r)
+        p16.assert_equal(r, o.rescale(mo), "rescale n16 l=%d" % lvl)
+        rt = p16.empty()
+        pf.pft_rotate(ctx, ga, 5, rt)
+        p16.assert_equal(rt, o.rotate(a, 5), "rotate n16 l=%d" % lvl)
