@@ -232,6 +232,10 @@ def run_gpu(args):
                 "traffic": None, "launches": k_launches, "kernel_ms": round(k_ms, 3),
                 "kernel_share_of_step": round(k_ms / ms, 4)}
 
+    ft = None
+    if args.fasttext:
+        ft = fasttext_measure(pft, torch, max(1, args.steps // 2), 1)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_level)
@@ -246,7 +250,8 @@ def run_gpu(args):
            "plain_value": round(plain, 3) if plain else None,
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
-           "gpu_launches": int(all_launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}
+           "gpu_launches": int(all_launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+           "fasttext": ft}
     if rank == 0:
         print(json.dumps(out))
     for h in A + B + C:
@@ -255,6 +260,175 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---- encrypted fastText inference (Sec. 3.1, Fig. 3) ------------------------------------------------
+FT_M, FT_N, FT_C, FT_LEVEL, FT_BATCH = 32768, 64, 14, 3, 32
+FT_WORKLOAD = ("vocab 32768, dim 64, 14 classes, weights N(0, 0.1^2); Zipf(1.1) documents of 20-200 tokens; "
+               "N=2^16, chain 60 + 29x40 bits + 4 special (60 bits), digits of 4 primes, inputs at level 3")
+
+
+def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
+    from oracle import fasttext as OF  # FP64 Algorithm 1 for the reported accuracy check only
+    from paper_1908_06972_gb300 import synth
+
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, 60, 40, 60, 2.0 ** 40, SEED)
+    n = 1 << LOGN
+    t = n // 2
+    pft.pft_keygen(ctx, [1 << i for i in range(15)], False)
+    H, O = synth.fasttext_weights(77, FT_M, FT_N, FT_C)
+    docs = synth.documents(78, FT_M, FT_BATCH)
+    model = pft.pft_ft_model_create(ctx, H, O, FT_LEVEL)
+    vs = []
+    for d in range(FT_BATCH):
+        pt = pft.pft_encode(ctx, docs[d], 2.0 ** 40, FT_LEVEL)
+        vs.append(pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, 9000 + d))
+        pft.pft_pt_destroy(pt)
+    scores = [pft.pft_ct_create(ctx) for _ in range(FT_BATCH)]
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    batched = lambda: pft.pft_fasttext_infer_batch(ctx, model, vs, 1, scores)  # noqa: E731
+    single = lambda: [pft.pft_fasttext_infer(ctx, model, [vs[d]], scores[d]) for d in range(4)]  # noqa: E731
+    for _ in range(warmup):
+        batched()
+    tb = timed(batched, steps)
+    single()
+    ts = timed(single, 1)
+    # accuracy of one document against the FP64 Algorithm 1
+    dec = pft.pft_decrypt(ctx, scores[0])
+    got = pft.pft_decode(ctx, dec, FT_C)[:FT_C].real
+    pft.pft_pt_destroy(dec)
+    err = float(np.max(np.abs(got - OF.plain_scores(docs[0], H, O))))
+    # plain path: one library call per op per ciphertext
+    Hp = [pft.pft_encode(ctx, H[:, j], 2.0 ** 40, FT_LEVEL) for j in range(FT_N)]
+    Op = []
+    for j in range(FT_N):
+        row = np.zeros(FT_C)
+        row[:] = O[j]
+        Op.append(pft.pft_encode(ctx, row, 2.0 ** 40, FT_LEVEL - 1))
+    tmp, rot, acc = pft.pft_ct_create(ctx), pft.pft_ct_create(ctx), pft.pft_ct_create(ctx)
+    cols = [pft.pft_ct_create(ctx) for _ in range(FT_N)]
+
+    def plain(d):
+        for j in range(FT_N):
+            pft.pft_mul_plain(ctx, vs[d], Hp[j], cols[j])
+            for s in range(15):
+                pft.pft_rotate(ctx, cols[j], 1 << s, rot)
+                pft.pft_add(ctx, cols[j], rot, cols[j])
+            pft.pft_rescale(ctx, cols[j], cols[j])
+        pft.pft_mul_plain(ctx, cols[0], Op[0], acc)
+        for j in range(1, FT_N):
+            pft.pft_mul_plain(ctx, cols[j], Op[j], tmp)
+            pft.pft_add(ctx, acc, tmp, acc)
+        pft.pft_rescale(ctx, acc, acc)
+
+    plain(0)
+    tp = timed(lambda: [plain(d) for d in range(plain_docs)], 1)
+    for h in vs + scores + cols + [tmp, rot, acc]:
+        pft.pft_ct_destroy(h)
+    for h in Hp + Op:
+        pft.pft_pt_destroy(h)
+    pft.pft_ft_model_destroy(model)
+    pft.pft_ctx_destroy(ctx)
+    return {"workload": FT_WORKLOAD, "unit": "inferences/s",
+            "batched_value": round(FT_BATCH * steps / tb, 3), "batch": FT_BATCH,
+            "batch1_value": round(4 / ts, 3), "plain_value": round(plain_docs / tp, 3),
+            "max_abs_err_vs_fp64": err, "rotations_per_inference": FT_N * 15}
+
+
+# ---- isolated kernel case (for ncu captures and burst rooflines) --------------------------------
+def run_case_ntt(args):
+    """Forward + inverse transform of 16 polynomials x 30 limbs at N = 2^16 (252 MB > L2)."""
+    import torch
+
+    import paper_1908_06972_gb300 as pft
+
+    torch.cuda.set_device(0)
+    pft.build()
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    n, polys = 1 << LOGN, 16
+    primes = pft.pft_ctx_info(ctx)["primes"]
+    rng = np.random.default_rng(3)
+    host = np.stack([np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in primes[:L]]) for _ in range(polys)])
+    t = torch.from_numpy(host.view(np.int64)).cuda()
+    for _ in range(args.warmup):
+        pft.pft_ntt(ctx, t.data_ptr(), polys, L, 0)
+        pft.pft_ntt(ctx, t.data_ptr(), polys, L, 1)
+    torch.cuda.synchronize()
+    pft.pft_prof_start("ntt.fwd")
+    for _ in range(args.steps):
+        pft.pft_ntt(ctx, t.data_ptr(), polys, L, 0)
+        pft.pft_ntt(ctx, t.data_ptr(), polys, L, 1)
+    fwd_ms, fwd_n, _, fwd_work = pft.pft_prof_stop()
+    pft.pft_prof_start("ntt.inv")
+    for _ in range(args.steps):
+        pft.pft_ntt(ctx, t.data_ptr(), polys, L, 0)
+        pft.pft_ntt(ctx, t.data_ptr(), polys, L, 1)
+    inv_ms, inv_n, _, inv_work = pft.pft_prof_stop()
+    torch.cuda.synchronize()
+    ok = bool(np.array_equal(t.cpu().numpy().view(np.uint64), host))
+    peak = SMS * IMAD_PER_CLK * SM_MHZ_MAX * 1e6 / IMAD_PER_MULMOD
+    bytes_per_pass = polys * L * n * 8 * 2
+    res = {"case": "ntt", "polys": polys, "limbs": L, "N": n, "round_trip_exact": ok,
+           "fwd_us_per_pass": round(1e3 * fwd_ms / fwd_n, 2), "inv_us_per_pass": round(1e3 * inv_ms / inv_n, 2),
+           "fwd_gmulmod_s": round(fwd_work / (fwd_ms / 1e3) / 1e9, 1),
+           "inv_gmulmod_s": round(inv_work / (inv_ms / 1e3) / 1e9, 1),
+           "alu_peak_gmulmod_s": round(peak / 1e9, 1),
+           "fwd_gbs": round(bytes_per_pass * fwd_n / (fwd_ms / 1e3) / 1e9, 1),
+           "inv_gbs": round(bytes_per_pass * inv_n / (inv_ms / 1e3) / 1e9, 1)}
+    print(json.dumps(res))
+    pft.pft_ctx_destroy(ctx)
+
+
+def run_case_ks(args):
+    """Batched HMUL + relinearisation of 4 ciphertext pairs at level 30 (the benchmark's chain)."""
+    import torch
+
+    import paper_1908_06972_gb300 as pft
+    from paper_1908_06972_gb300 import synth
+
+    torch.cuda.set_device(0)
+    pft.build()
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    pft.pft_keygen(ctx, [], True)
+    A, B = [], []
+    for i in range(4):
+        p = pft.pft_encode(ctx, synth.slots(i, 64), SCALE, L)
+        A.append(pft.pft_encrypt(ctx, p, pft.PFT_ENC_SK, 2 * i))
+        B.append(pft.pft_encrypt(ctx, p, pft.PFT_ENC_SK, 2 * i + 1))
+        pft.pft_pt_destroy(p)
+    C = [pft.pft_ct_create(ctx) for _ in range(4)]
+    for _ in range(args.warmup):
+        pft.pft_mul_relin_batch(ctx, A, B, C)
+    torch.cuda.synchronize()
+    res = {"case": "ks", "level": L, "batch": 4}
+    for fam in ("bconv", "ks_inner", "ntt", "sub_scale"):
+        pft.pft_prof_start(fam)
+        for _ in range(args.steps):
+            pft.pft_mul_relin_batch(ctx, A, B, C)
+        ms, n, tot, work = pft.pft_prof_stop()
+        res[fam] = {"us_per_launch": round(1e3 * ms / max(1, n), 2), "launches_per_op": n // args.steps,
+                    "gbs": round(work / (ms / 1e3) / 1e9, 1) if work and fam != "ntt" else None}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pft.pft_mul_relin_batch(ctx, A, B, C)
+    e1.record()
+    torch.cuda.synchronize()
+    res["ms_per_batch"] = round(e0.elapsed_time(e1) / args.steps, 3)
+    print(json.dumps(res))
+    for h in A + B + C:
+        pft.pft_ct_destroy(h)
+    pft.pft_ctx_destroy(ctx)
 
 
 # ---- CPU oracle -------------------------------------------------------------------------------------
@@ -314,8 +488,14 @@ def main():
     ap.add_argument("--roofline-kernel", default="ntt")
     ap.add_argument("--cpu-level", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
+    ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case == "ntt":
+        run_case_ntt(args)
+    elif args.case == "ks":
+        run_case_ks(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -28,7 +28,7 @@ struct pft_ctx {
     // basis-conversion tables: modup[(l-1) * beta_max + j], moddown[l-1] (device offsets)
     std::vector<const u64*> modup_tab, moddown_tab;
     const u64* moddown_consts = nullptr;           // [L][3] {0, P^-1, shoup}
-    std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {h mod q_k, p^-1, shoup}
+    std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {0, p^-1, shoup}
     std::vector<const u64*> pmodq_consts;          // digit j -> [alpha][3] {0, P mod q_m, shoup}
     std::vector<u64> P_mod_q;
     std::vector<u32> cdt;
@@ -257,13 +257,15 @@ static void build_tables(pft_ctx* c) {
         }
         c->pmodq_consts.push_back(tab_upload(c, v));
     }
-    // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [ns][l + k] qhat mod target
+    // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [targets][ns] qhat mod target,
+    // targets = rows 0..l+k-1 outside the digit, in order
     c->modup_tab.assign((size_t)L * c->beta_max, nullptr);
     for (int l = 1; l <= L; l++) {
         const int beta = (l + c->alpha - 1) / c->alpha, E = l + k;
         for (int j = 0; j < beta; j++) {
             const int lo = j * c->alpha, hi = std::min(l, lo + c->alpha), ns = hi - lo;
-            std::vector<u64> tab(2 * ns + (size_t)ns * E);
+            const int nt = E - ns;
+            std::vector<u64> tab(2 * ns + (size_t)ns * nt);
             for (int i = 0; i < ns; i++) {
                 const u64 qi = c->primes[lo + i];
                 u64 h = 1;
@@ -272,18 +274,21 @@ static void build_tables(pft_ctx* c) {
                 const u64 hinv = invmod_host(h, qi);
                 tab[2 * i] = hinv;
                 tab[2 * i + 1] = shoup(hinv, qi);
+                int mi = 0;
                 for (int m = 0; m < E; m++) {
+                    if (m >= lo && m < hi) continue;
                     const u64 t = m < l ? c->primes[m] : c->primes[L + m - l];
                     u64 hm = 1;
                     for (int i2 = 0; i2 < ns; i2++)
                         if (i2 != i) hm = mulmod_host(hm, c->primes[lo + i2] % t, t);
-                    tab[2 * ns + (size_t)i * E + m] = hm;
+                    tab[2 * ns + (size_t)mi * ns + i] = hm;
+                    mi++;
                 }
             }
             c->modup_tab[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
         }
     }
-    // ModDown tables per level: [k]{phat_inv, shoup}, then [k][l] phat mod q_m
+    // ModDown tables per level: [k]{phat_inv, shoup}, then [l][k] phat mod q_m
     c->moddown_tab.assign(L, nullptr);
     for (int l = 1; l <= L; l++) {
         std::vector<u64> tab(2 * k + (size_t)k * l);
@@ -300,12 +305,12 @@ static void build_tables(pft_ctx* c) {
                 u64 hm = 1;
                 for (int i2 = 0; i2 < k; i2++)
                     if (i2 != i) hm = mulmod_host(hm, c->primes[L + i2] % t, t);
-                tab[2 * k + (size_t)i * l + m] = hm;
+                tab[2 * k + (size_t)m * k + i] = hm;
             }
         }
         c->moddown_tab[l - 1] = tab_upload(c, tab);
     }
-    // rescale constants per level l >= 2: for k' < l-1: {floor(p/2) mod q_k', p^-1, shoup}, p = q_{l-1}
+    // rescale constants per level l >= 2: for k' < l-1: {0, p^-1, shoup}, p = q_{l-1}
     c->rescale_consts.assign(L, nullptr);
     for (int l = 2; l <= L; l++) {
         const u64 p = c->primes[l - 1];
@@ -313,7 +318,7 @@ static void build_tables(pft_ctx* c) {
         for (int kk = 0; kk < l - 1; kk++) {
             const u64 q = c->primes[kk];
             const u64 pinv = invmod_host(p % q, q);
-            v[3 * kk] = (p / 2) % q;
+            v[3 * kk] = 0;
             v[3 * kk + 1] = pinv;
             v[3 * kk + 2] = shoup(pinv, q);
         }

@@ -15,9 +15,385 @@
 // (Harvey lazy butterflies: forward values in [0, 4q), inverse in [0, 2q)), and
 // rounds exchange through shared memory.  N <= 2^14: one pass, one CTA per limb.
 // N = 2^15, 2^16: two passes (8 + 7 or 8 + 8 stages).
+#include <cooperative_groups.h>
+
+#include <cstdlib>
+#include <cstring>
+
 #include "modarith.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace pft {
+
+// ---- butterflies ---------------------------------------------------------------------------
+// Cooley-Tukey (Harvey): X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q)
+__device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
+    if (X >= q2) X -= q2;
+    const u64 T = mul_shoup_lazy(Y, W.x, W.y, q);
+    Y = X - T + q2;
+    X = X + T;
+}
+// Gentleman-Sande: X, Y in [0, 2q) -> X + Y, (X - Y) W in [0, 2q)
+__device__ __forceinline__ void gs_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
+    u64 S = X + Y;
+    if (S >= q2) S -= q2;
+    const u64 D = X - Y + q2;
+    X = S;
+    Y = mul_shoup_lazy(D, W.x, W.y, q);
+}
+__device__ __forceinline__ u64 canon4(u64 v, u64 q, u64 q2) {
+    if (v >= q2) v -= q2;
+    if (v >= q) v -= q;
+    return v;
+}
+
+// ---- N = 2^16 in one launch: an 8-CTA cluster per limb ------------------------------------
+// The limb is viewed as a 256 x 256 array, element j = row * 256 + col.  Forward stages
+// 0..7 pair elements along a column (row bit 7 - s), stages 8..15 along a row (col bit
+// 15 - s); group index i = j / (2t) is row >> (8 - s) for s < 8 and
+// row 2^(s-8) + (col >> (16 - s)) for s >= 8.  CTA c of the cluster transforms columns
+// 32c..32c+31 (phase 1), then gathers rows 32c..32c+31 from all eight CTAs' shared memory
+// (distributed shared memory) and transforms them (phase 2); the inverse runs the same
+// two phases in the opposite order.  Lane = sub-transform, so every shared and remote
+// access is a stride-33 (odd) walk: conflict-free.  One HBM read and one write per limb.
+//
+// One round = four stages on 16 registers: register e holds element (e << W0) | wpart of
+// the current 256-point sub-transform; DIMHI = 0 for column stages (s = 7 - p), 8 for row
+// stages (s = 15 - p, r = the row being transformed).
+template <bool INV, int W0, int DIMHI>
+__device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, const ulonglong2* __restrict__ tw,
+                                            u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int lb = INV ? k : 3 - k;
+        const int p = W0 + lb;
+        const int s = DIMHI + 7 - p;
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            if (e & (1 << lb)) continue;
+            const int elem = (e << W0) | wpart;
+            const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
+            if (!INV) {
+                ct_bfly(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
+            } else if (s == 0) {  // last inverse stage: N^-1 folded into both outputs
+                u64 S = x[e] + x[e | (1 << lb)];
+                if (S >= q2) S -= q2;
+                const u64 D = x[e] - x[e | (1 << lb)] + q2;
+                x[e] = mul_shoup_lazy(S, NI.x, NI.y, q);
+                x[e | (1 << lb)] = mul_shoup_lazy(D, NI1.x, NI1.y, q);
+            } else {
+                gs_bfly(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
+            }
+        }
+    }
+}
+
+constexpr int kN16Stride = 33;  // shared layout [256][33]: element (a, lane) at a * 33 + lane
+
+template <bool INV, int MINB>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(512, MINB)
+    k_ntt16_cluster(DevTables t, PolySet in, PolySet out) {
+    extern __shared__ u64 sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int c = (int)cluster.block_rank();
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;  // uniform over the cluster (same limb)
+    const int pi = prime_of(Ro, limb);
+    const u64* src = in.p[poly].ptr + ((size_t)limb << 16);
+    u64* dst = Ro.ptr + ((size_t)limb << 16);
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 q2 = 2 * q;
+    const ulonglong2* tw = (INV ? t.inv : t.fwd) + ((size_t)pi << 16);
+    const ulonglong2 NI = INV ? __ldg(&t.ninv[pi]) : make_ulonglong2(0, 0);
+    const ulonglong2 NI1 = INV ? __ldg(&t.inv1ninv[pi]) : make_ulonglong2(0, 0);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int ST = kN16Stride;
+    u64 x[16];
+
+    if (!INV) {
+        // phase 1: columns 32c + lane
+        const int col = 32 * c + lane;
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = src[(size_t)((e << 4) | w) * 256 + col];
+        ntt16_round<false, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((e << 4) | w) * ST + lane] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((w << 4) | e) * ST + lane];
+        ntt16_round<false, 0, 0>(x, w << 4, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * ST + lane] = x[e];
+        cluster.sync();
+        // phase 2: rows 32c + lane, gathered from the CTA holding each column
+        const int r = 32 * c + lane;
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int cx = (e << 4) | w;
+            const u64* rem = cluster.map_shared_rank(sm, cx >> 5);
+            x[e] = rem[r * ST + (cx & 31)];
+        }
+        cluster.sync();
+        ntt16_round<false, 4, 8>(x, w, r, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((e << 4) | w) * ST + lane] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((w << 4) | e) * ST + lane];
+        ntt16_round<false, 0, 8>(x, w << 4, r, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * ST + lane] = canon4(x[e], q, q2);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int f = threadIdx.x + 512 * k;
+            const int rho = f >> 8, cx = f & 255;
+            dst[(size_t)(32 * c + rho) * 256 + cx] = sm[cx * ST + rho];
+        }
+    } else {
+        // phase 1: rows 32c + lane (coalesced load through shared memory, layout [col][row])
+        const int r = 32 * c + lane;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int f = threadIdx.x + 512 * k;
+            const int rho = f >> 8, cx = f & 255;
+            sm[cx * ST + rho] = src[(size_t)(32 * c + rho) * 256 + cx];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((w << 4) | e) * ST + lane];
+        ntt16_round<true, 0, 8>(x, w << 4, r, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * ST + lane] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((e << 4) | w) * ST + lane];
+        ntt16_round<true, 4, 8>(x, w, r, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((e << 4) | w) * ST + lane] = x[e];
+        cluster.sync();
+        // phase 2: columns 32c + lane, gathered from the CTA holding each row
+        const int col = 32 * c + lane;
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int row = (w << 4) | e;
+            const u64* rem = cluster.map_shared_rank(sm, row >> 5);
+            x[e] = rem[col * ST + (row & 31)];
+        }
+        cluster.sync();
+        ntt16_round<true, 0, 0>(x, w << 4, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * ST + lane] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((e << 4) | w) * ST + lane];
+        ntt16_round<true, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) dst[(size_t)((e << 4) | w) * 256 + col] = canon4(x[e], q, q2);
+    }
+}
+
+// ---- N = 2^16 in two passes of 8 stages, global memory touched from registers ----------------
+// Pass A (stages 0..7): 256-point column transforms at stride T = 2^LOGT; a CTA takes 16
+// adjacent columns, lane bits 0..3 = column, so every global access of a warp reads or
+// writes two 128-byte runs.  Pass B (stages 8..15): 16 contiguous 256-point rows per CTA,
+// lane bits 0..3 = point.  Each pass does 2 rounds of 4 stages with one shared-memory
+// exchange (odd strides 17 / 273: conflict-free); pass B stages its final store (forward)
+// or first load (inverse) through shared memory to keep the global side coalesced.
+constexpr int kRowStride = 273;  // 256 + 16 padding + 1
+
+template <bool INV, int LOGT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet in, PolySet out, int is_final) {
+    __shared__ u64 sm[256 * 17];
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int logn = t.logn;
+    const int pi = prime_of(Ro, limb);
+    const int cc = threadIdx.x & 15, w = threadIdx.x >> 4;
+    const int col = blockIdx.x * 16 + cc;
+    const u64* src = in.p[poly].ptr + ((size_t)limb << logn) + col;
+    u64* dst = Ro.ptr + ((size_t)limb << logn) + col;
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 q2 = 2 * q;
+    const ulonglong2* tw = (INV ? t.inv : t.fwd) + ((size_t)pi << logn);
+    const ulonglong2 NI = INV ? __ldg(&t.ninv[pi]) : make_ulonglong2(0, 0);
+    const ulonglong2 NI1 = INV ? __ldg(&t.inv1ninv[pi]) : make_ulonglong2(0, 0);
+    u64 x[16];
+    if (!INV) {
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = src[(size_t)((e << 4) | w) << LOGT];
+        ntt16_round<false, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((e << 4) | w) * 17 + cc] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((w << 4) | e) * 17 + cc];
+        ntt16_round<false, 0, 0>(x, w << 4, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) dst[(size_t)((w << 4) | e) << LOGT] = is_final ? canon4(x[e], q, q2) : x[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = src[(size_t)((w << 4) | e) << LOGT];
+        ntt16_round<true, 0, 0>(x, w << 4, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * 17 + cc] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[((e << 4) | w) * 17 + cc];
+        ntt16_round<true, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) dst[(size_t)((e << 4) | w) << LOGT] = is_final ? canon4(x[e], q, q2) : x[e];
+    }
+}
+
+template <bool INV, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet in, PolySet out, int is_final) {
+    __shared__ u64 sm[16 * kRowStride];
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int logn = t.logn;
+    const int pi = prime_of(Ro, limb);
+    const int w = threadIdx.x & 15, cc = threadIdx.x >> 4;
+    const int u = blockIdx.x * 16 + cc;
+    const u64* src = in.p[poly].ptr + ((size_t)limb << logn);
+    u64* dst = Ro.ptr + ((size_t)limb << logn);
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 q2 = 2 * q;
+    const ulonglong2* tw = (INV ? t.inv : t.fwd) + ((size_t)pi << logn);
+    const ulonglong2 NI = INV ? __ldg(&t.ninv[pi]) : make_ulonglong2(0, 0);
+    const ulonglong2 NI1 = INV ? __ldg(&t.inv1ninv[pi]) : make_ulonglong2(0, 0);
+    u64* my = sm + cc * kRowStride;
+    u64 x[16];
+    if (!INV) {
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = src[((size_t)u << 8) | (e << 4) | w];
+        ntt16_round<false, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) my[e * 17 + w] = x[e];  // point e*16 + w
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
+        ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) my[w * 17 + e] = is_final ? canon4(x[e], q, q2) : x[e];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int f = threadIdx.x + 256 * k;
+            const int c2 = f >> 8, m = f & 255;
+            dst[((size_t)(blockIdx.x * 16 + c2) << 8) | m] = sm[c2 * kRowStride + m + (m >> 4)];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int f = threadIdx.x + 256 * k;
+            const int c2 = f >> 8, m = f & 255;
+            sm[c2 * kRowStride + m + (m >> 4)] = src[((size_t)(blockIdx.x * 16 + c2) << 8) | m];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
+        ntt16_round<true, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) my[w * 17 + e] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = my[e * 17 + w];  // point e*16 + w
+        ntt16_round<true, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
+#pragma unroll
+        for (int e = 0; e < 16; e++) dst[((size_t)u << 8) | (e << 4) | w] = is_final ? canon4(x[e], q, q2) : x[e];
+    }
+}
+
+template <int MINB>
+static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
+                                   cudaStream_t st) {
+    dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);  // 256 sub-transforms / 16 per CTA
+    const double work = set_limbs(out) * (double)(t.n / 2) * 8;
+    if (!inverse) {
+        {
+            PFT_PROF("ntt.fwd.strided", st, work);
+            k_ntt8_strided<false, 8, MINB><<<grid, 256, 0, st>>>(t, in, out, 0);
+        }
+        PFT_LAUNCH_CHECK("ntt pass A");
+        {
+            PFT_PROF("ntt.fwd.contig", st, work);
+            k_ntt8_contig<false, MINB><<<grid, 256, 0, st>>>(t, out, out, 1);
+        }
+        PFT_LAUNCH_CHECK("ntt pass B");
+    } else {
+        {
+            PFT_PROF("ntt.inv.contig", st, work);
+            k_ntt8_contig<true, MINB><<<grid, 256, 0, st>>>(t, in, out, 0);
+        }
+        PFT_LAUNCH_CHECK("intt pass B");
+        {
+            PFT_PROF("ntt.inv.strided", st, work);
+            k_ntt8_strided<true, 8, MINB><<<grid, 256, 0, st>>>(t, out, out, 1);
+        }
+        PFT_LAUNCH_CHECK("intt pass A");
+    }
+}
+
+// Resident CTAs per SM the two-pass kernels are compiled for: 3 (80 registers, default)
+// or 4 (64 registers) with PFT_NTT_MINB=4.
+static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
+                                 cudaStream_t st) {
+    static int minb = 0;
+    if (!minb) {
+        const char* e = getenv("PFT_NTT_MINB");
+        minb = (e && e[0] == '4') ? 4 : 3;
+    }
+    if (minb == 4) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
+    else launch_ntt16_twopass_v<3>(t, in, out, inverse, st);
+}
+
+template <bool INV, int MINB>
+static void launch_ntt16_cluster_v(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
+    const size_t smem = (size_t)256 * kN16Stride * sizeof(u64);
+    static bool attr_set = false;
+    if (!attr_set) {
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt16_cluster<INV, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr_set = true;
+    }
+    dim3 grid(8, (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF(INV ? "ntt.inv.cluster" : "ntt.fwd.cluster", st, set_limbs(out) * (double)(t.n / 2) * 16);
+    k_ntt16_cluster<INV, MINB><<<grid, 512, smem, st>>>(t, in, out);
+    PFT_LAUNCH_CHECK("ntt16 cluster");
+}
+
+// Resident CTAs per SM the cluster kernel is compiled for: 2 (64 registers) by default,
+// 1 (no register cap) with PFT_NTT16_MINB=1.
+static int ntt16_minb() {
+    static int v = 0;
+    if (!v) {
+        const char* e = getenv("PFT_NTT16_MINB");
+        v = (e && e[0] == '1') ? 1 : 2;
+    }
+    return v;
+}
+
+template <bool INV>
+static void launch_ntt16_cluster(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
+    if (ntt16_minb() == 1) launch_ntt16_cluster_v<INV, 1>(t, in, out, st);
+    else launch_ntt16_cluster_v<INV, 2>(t, in, out, st);
+}
+
+// N = 2^16 path: the register-direct two-pass kernels (default); PFT_NTT16=cluster selects the
+// one-launch cluster kernel, PFT_NTT16=generic the generic shared-memory-staged passes.
+static int ntt16_path() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("PFT_NTT16");
+        v = (e && strcmp(e, "cluster") == 0) ? 1 : (e && strcmp(e, "generic") == 0) ? 2 : 0;
+    }
+    return v;
+}
 
 template <int S, int C, bool INV>
 __global__ void __launch_bounds__(C*(1 << (S - 4)))
@@ -211,7 +587,12 @@ static void run(const DevTables& t, const PolySet& in, const PolySet& out, bool 
         else run_single<false>(t, in, out, st);
         return;
     }
-    if (t.logn == 16) {
+    if (t.logn == 16 && ntt16_path() == 0) {
+        launch_ntt16_twopass(t, in, out, inverse, st);
+    } else if (t.logn == 16 && ntt16_path() == 1) {
+        if (!inverse) launch_ntt16_cluster<false>(t, in, out, st);
+        else launch_ntt16_cluster<true>(t, in, out, st);
+    } else if (t.logn == 16) {
         if (!inverse) {
             launch_pass<8, 16, false>(t, in, out, 0, 0, st);   // stages 0..7, stride 256
             launch_pass<8, 16, false>(t, out, out, 8, 1, st);  // stages 8..15, contiguous

@@ -116,7 +116,7 @@ void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g,
 struct BconvJob {
     const u64* src;
     u64* dst;
-    const u64* table;  // [ns]{qhat_inv, shoup} then [ns][nrows] qhat mod target
+    const u64* table;  // [ns]{qhat_inv, shoup} then [targets][ns] qhat mod target
     int ns, src_p0, nrows, skip_lo, skip_hi, split, base2, pad;
 };
 void bconv(const DevTables& t, const BconvJob* jobs_host, int n_jobs, cudaStream_t st);  // jobs: host array
@@ -125,7 +125,7 @@ void bconv(const DevTables& t, const BconvJob* jobs_host, int n_jobs, cudaStream
 //   u[b][pol][m] = sum_j ext[b][j][m] * key[j][pol][row(m)],  ext: [B][beta][l+k][N], u: [B][2][l+k][N].
 void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k, int beta,
               cudaStream_t st);
-// r = (last + floor(p/2)) mod p for p = prime nlimbs(out), reduced into every limb of out.
+// r = (last + h) mod p, h = floor(p/2), p = prime nlimbs(out); limb k of out = (r - h) mod q_k.
 void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st);
 
 // Sampling (ChaCha20 streams, nonce (dom, obj, sub)).

@@ -9,6 +9,10 @@ namespace pft {
 
 static constexpr int kEwThreads = 256;
 
+struct BconvBatch {
+    BconvJob j[kMaxBconv];
+};
+
 static dim3 ew_grid(int n, const PolySet& s) {
     return dim3((unsigned)((n / 2 + kEwThreads - 1) / kEwThreads), (unsigned)s.max_limbs, (unsigned)s.count);
 }
@@ -208,35 +212,50 @@ void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g,
 
 // ---- fast basis conversion (ModUp of one digit, or ModDown from the special primes) ------
 // For each coefficient: y_i = x_i * qhat_i^-1 mod s_i (Shoup), then for every target row m
-// (rows [0, nrows) except [skip_lo, skip_hi)):  out_m = sum_i y_i * (qhat_i mod t_m) mod t_m.
+// (rows [0, nrows) except [skip_lo, skip_hi), enumerated in order as targets 0..nt-1):
+//   out_m = sum_i y_i * (qhat_i mod t_m) mod t_m   (128-bit sum, one Barrett reduction).
 // Target prime of row m: m < split ? m : base2 + m - split.  Table: [ns] {inv, inv_shoup},
-// then [ns][nrows] qhat_i mod t_m.
-struct BconvBatch {
-    BconvJob j[kMaxBconv];
-};
-__global__ void k_bconv(DevTables t, BconvBatch jobs) {
+// then [nt][ns] qhat_i mod t_m (target-major).  Four targets per iteration give four
+// independent accumulation chains per thread.
+__global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
     const BconvJob& J = jobs.j[blockIdx.y];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= t.n) return;
     const int logn = t.logn;
-    u64 y[kMaxAlpha > kMaxSpecial ? kMaxAlpha : kMaxSpecial];
+    const int ns = J.ns;
+    u64 y[kMaxAlpha];
 #pragma unroll
     for (int i = 0; i < kMaxAlpha; i++) {
-        if (i < J.ns) {
+        y[i] = 0;
+        if (i < ns) {
             const u64 q = __ldg(&t.primes[J.src_p0 + i].q);
             const u64 v = __ldg(J.src + ((size_t)i << logn) + x);
             y[i] = mul_shoup(v, __ldg(&J.table[2 * i]), __ldg(&J.table[2 * i + 1]), q);
         }
     }
-    const u64* T = J.table + 2 * J.ns;
-    for (int m = 0; m < J.nrows; m++) {
-        if (m >= J.skip_lo && m < J.skip_hi) continue;
-        const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
-        U128 acc = {0, 0};
+    const u64* T = J.table + 2 * ns;
+    const int gap = J.skip_hi - J.skip_lo;
+    const int nt = J.nrows - gap;
+    for (int m0 = 0; m0 < nt; m0 += 4) {
+        U128 acc[4];
 #pragma unroll
-        for (int i = 0; i < kMaxAlpha; i++)
-            if (i < J.ns) mac_wide(acc, y[i], __ldg(&T[(size_t)i * J.nrows + m]));
-        J.dst[((size_t)m << logn) + x] = barrett_reduce(acc.hi, acc.lo, P);
+        for (int u = 0; u < 4; u++) {
+            acc[u].lo = 0;
+            acc[u].hi = 0;
+            const int mi = m0 + u < nt ? m0 + u : nt - 1;
+#pragma unroll
+            for (int i = 0; i < kMaxAlpha; i++)
+                if (i < ns) mac_wide(acc[u], y[i], __ldg(&T[(size_t)mi * ns + i]));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int mi = m0 + u;
+            if (mi < nt) {
+                const int m = mi < J.skip_lo ? mi : mi + gap;
+                const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
+                J.dst[((size_t)m << logn) + x] = barrett_reduce(acc[u].hi, acc[u].lo, P);
+            }
+        }
     }
 }
 
@@ -341,7 +360,9 @@ void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B,
     PFT_LAUNCH_CHECK("ks_inner");
 }
 
-// ---- rescale broadcast: r = (c_{l-1} + h) mod p, reduced into each lower prime ----------
+// ---- rescale broadcast: r = (c_{l-1} + h) mod p, h = floor(p/2), per coefficient; every
+// lower limb k receives (r - h) mod q_k (coefficient form), so that after the transform
+// c'_k = (c_k - out_k) p^-1 = (c_k + h - r) / p coefficient by coefficient.
 // last: coefficient-form last limb of each polynomial; out: [l-1][N] per polynomial.
 __global__ void k_rescale_bcast(DevTables t, PolySet last, PolySet out) {
     const int poly = blockIdx.z, limb = blockIdx.y;
@@ -354,7 +375,7 @@ __global__ void k_rescale_bcast(DevTables t, PolySet last, PolySet out) {
     u64 r = __ldg(last.p[poly].ptr + x) + (p >> 1);
     if (r >= p) r -= p;
     const DPrime P = load_prime(t.primes, limb);
-    Ro.ptr[((size_t)limb << t.logn) + x] = reduce64(r, P);
+    Ro.ptr[((size_t)limb << t.logn) + x] = submod(reduce64(r, P), reduce64(p >> 1, P), P.q);
 }
 
 void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st) {

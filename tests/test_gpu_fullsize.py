@@ -1,0 +1,109 @@
+"""Full-size GPU parity: the benchmark's chain (N = 2^16, 30 primes: 60 + 29 x 50 bits,
+4 special primes of 60 bits, digits of 4 primes) in the batched launch configuration the
+benchmark times, against the oracle bit for bit; and the encrypted fastText inference at
+N = 2^16 (32768 slots, 40-bit chain): a two-column model bit-exact against the oracle's
+full sequence, the 64 x 14 model through the batched path against the FP64 Algorithm 1
+within 2^-20."""
+import numpy as np
+import pytest
+
+from oracle import fasttext as OF
+from paper_1908_06972_gb300 import synth
+
+from .pairs import Pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p2(gpu):
+    p = Pair(gpu, 16, 30, 4, 4, first_bits=60, mid_bits=50, special_bits=60, scale=2.0 ** 50,
+             seed=(0x5EED0001, 0x5EED0002, 0x5EED0003, 0x5EED0004), rot_steps=[1, -1], insecure=False)
+    yield p
+    p.close()
+
+
+def test_p2_batched_mul_relin_rescale_rotate(p2):
+    o, pf, ctx = p2.orc, p2.pft, p2.ctx
+    lv = [30, 17, 5]
+    A = [o.encrypt_sk(o.encode(synth.slots(10 + i, 512), level=l), 100 + i) for i, l in enumerate(lv)]
+    B = [o.encrypt_pk(o.encode(synth.slots(20 + i, 512), level=l), 200 + i) for i, l in enumerate(lv)]
+    gA, gB = [p2.ct(x) for x in A], [p2.ct(x) for x in B]
+    C = [p2.empty() for _ in lv]
+    pf.pft_mul_relin_batch(ctx, gA, gB, C)
+    M = [o.mul_relin(a, b) for a, b in zip(A, B)]
+    for i in range(len(lv)):
+        p2.assert_equal(C[i], M[i], "p2 mul_relin l=%d" % lv[i])
+    pf.pft_rotate_batch(ctx, C, -1, C)
+    R = [o.rotate(m, -1) for m in M]
+    for i in range(len(lv)):
+        p2.assert_equal(C[i], R[i], "p2 rotate l=%d" % lv[i])
+    pf.pft_rescale_batch(ctx, C, C)
+    for i in range(len(lv)):
+        p2.assert_equal(C[i], o.rescale(R[i]), "p2 rescale l=%d" % lv[i])
+
+
+def test_p2_keys_match(p2):
+    assert np.array_equal(p2.pft.pft_key_export(p2.ctx, 0), p2.orc.keys[0])
+
+
+@pytest.fixture(scope="module")
+def p3(gpu):
+    steps = [1 << i for i in range(15)]
+    p = Pair(gpu, 16, 3, 4, 4, first_bits=60, mid_bits=40, special_bits=60, scale=2.0 ** 40,
+             seed=(0xF00D, 1, 2, 3), rot_steps=steps, insecure=False)
+    yield p
+    p.close()
+
+
+def test_fasttext_two_columns_bit_exact_n16(p3):
+    o, pf, ctx = p3.orc, p3.pft, p3.ctx
+    t = p3.N // 2
+    m, n, c = t, 2, 14
+    H, O = synth.fasttext_weights(31, m, n, c)
+    docs = synth.documents(32, m, 1)
+    Hp, Opk = OF.pack_H(H, t), OF.pack_O(O, t)
+    H_o = [[o.encode(Hp[j, 0], level=3)] for j in range(n)]
+    O_o = [o.encode(Opk[j], level=2) for j in range(n)]
+    model = pf.pft_ft_model_import(ctx, [p3.pt(H_o[j][0]) for j in range(n)], [p3.pt(x) for x in O_o], m, n, c)
+    try:
+        v = o.encrypt_sk(o.encode(docs[0], level=3), 4242)
+        s = p3.empty()
+        pf.pft_fasttext_infer(ctx, model, [p3.ct(v)], s)
+        want = OF.encrypted_scores(o, [v], H_o, O_o)
+        p3.assert_equal(s, want, "fasttext n16 two columns")
+        dec = o.decode(o.decrypt(want))[:c].real
+        assert np.max(np.abs(dec - OF.plain_scores(docs[0], H, O))) < 2.0 ** -20
+    finally:
+        pf.pft_ft_model_destroy(model)
+
+
+def test_fasttext_full_model_batched_tolerance(p3):
+    """Vocabulary 32768, embedding 64, 14 classes; 4 documents in one batched call."""
+    pf, ctx = p3.pft, p3.ctx
+    t = p3.N // 2
+    m, n, c = 32768, 64, 14
+    H, O = synth.fasttext_weights(41, m, n, c)
+    docs = synth.documents(42, m, 4)
+    model = pf.pft_ft_model_create(ctx, H, O, 3)
+    try:
+        vs = []
+        for d in range(4):
+            pt = pf.pft_encode(ctx, docs[d], 2.0 ** 40, 3)
+            vs.append(pf.pft_encrypt(ctx, pt, pf.PFT_ENC_SK, 7000 + d))
+            pf.pft_pt_destroy(pt)
+        scores = [p3.empty() for _ in range(4)]
+        pf.pft_fasttext_infer_batch(ctx, model, vs, 1, scores)
+        for d in range(4):
+            dec = pf.pft_decrypt(ctx, scores[d])
+            got = pf.pft_decode(ctx, dec, t)[:c].real
+            pf.pft_pt_destroy(dec)
+            want = OF.plain_scores(docs[d], H, O)
+            assert np.max(np.abs(got - want)) < 2.0 ** -20, np.max(np.abs(got - want))
+            srt = np.sort(want)
+            if srt[-1] - srt[-2] >= 2.0 ** -18:
+                assert int(np.argmax(got)) == int(np.argmax(want))
+        for h in vs:
+            pf.pft_ct_destroy(h)
+    finally:
+        pf.pft_ft_model_destroy(model)
