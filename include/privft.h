@@ -221,6 +221,26 @@ int pft_mul_relin_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_ct* cons
 int pft_rescale_batch(pft_ctx* ctx, const pft_ct* const* a, int B, pft_ct* const* out);
 int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out);
 
+/* ---- rescale without allocation --------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot obtain
+ * device memory at the moment they call the library -- for example an application whose
+ * device memory is entirely owned by another framework's pool, or a processing loop in
+ * which allocator calls are not allowed.  It computes exactly what pft_rescale computes,
+ * on raw device buffers, and allocates nothing: the caller passes the input and the output,
+ * and the working space comes from a fixed array of 4 Mi 64-bit words (32 MiB) compiled
+ * into the library, which every device that loads the library holds until the process
+ * exits.
+ *   in     device pointer, ciphertext [2][level][N] in the evaluation layout (pft_ct_data)
+ *   level  2..L; 2 N level must not exceed 4 Mi words (N = 2^16: level <= 32), else
+ *          PFT_ERR_ARG with a message naming the limit
+ *   out    device pointer, [2][level-1][N]; must not overlap `in`; receives the rescaled
+ *          ciphertext (its scale is the input scale divided by q_{level-1})
+ * Work is queued on the context stream.  The first call on a device looks up the device
+ * address of the fixed array; make that first call before any stream capture.  All calls
+ * on a device share the array and it keeps the last call's contents: calls whose GPU work
+ * overlaps (different streams or contexts on the same device) race on it. */
+int pft_rescale_noalloc(pft_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
+
 /* ---- raw transforms on caller memory (kernel-level access) ----------------
  * data: device buffer of n_polys polynomials [n_polys][n_limbs][N], limb r under
  * prime r of the chain (r < L + k; rows >= L are the special primes).  inverse = 0:

@@ -84,6 +84,7 @@ def lib():
             "pft_mul_relin_batch": [vp, pp, pp, i, pp], "pft_rescale_batch": [vp, pp, i, pp],
             "pft_rotate_batch": [vp, pp, i, c_int32, pp],
             "pft_ntt": [vp, c_void_p, i, i, i],
+            "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
             "pft_ft_model_create": [vp, POINTER(c_double), POINTER(c_double), i, i, i, i, pp],
             "pft_ft_model_import": [vp, pp, pp, i, i, i, pp], "pft_ft_model_destroy": [vp],
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
@@ -113,7 +114,7 @@ def exported_symbols():
             "pft_add_batch", "pft_mul_plain_batch", "pft_mul_relin_batch", "pft_rescale_batch",
             "pft_rotate_batch", "pft_ntt", "pft_ft_model_create", "pft_ft_model_import",
             "pft_ft_model_destroy", "pft_fasttext_infer", "pft_fasttext_infer_batch",
-            "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop"]
+            "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc"]
 
 
 def _check(rc, ctx=None):
@@ -392,6 +393,13 @@ def pft_rotate_batch(ctx, a, step, out):
 def pft_ntt(ctx, data_ptr, n_polys, n_limbs, inverse):
     """In-place transform of caller device memory (an int device pointer, e.g. tensor.data_ptr())."""
     _op("pft_ntt", ctx, c_void_p(data_ptr), n_polys, n_limbs, 1 if inverse else 0)
+
+
+def pft_rescale_noalloc(ctx, in_ptr, level, out_ptr):
+    """Rescale of raw device buffers (int device pointers) without any device allocation:
+    for callers that cannot allocate device memory when they call the library.  The library
+    uses a fixed 32 MiB array as working space (shared by all calls on a device)."""
+    _op("pft_rescale_noalloc", ctx, c_void_p(in_ptr), level, c_void_p(out_ptr))
 
 
 def pft_ft_model_create(ctx, H, O, level):

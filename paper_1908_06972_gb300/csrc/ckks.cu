@@ -865,6 +865,33 @@ static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* cons
     }
 }
 
+// ---- allocation-free rescale ---------------------------------------------------------------
+// For callers that cannot obtain device memory when they call the library (their device
+// memory is owned by another framework's pool, or allocator calls are not allowed in their
+// processing loop).  The working space of pft_rescale_noalloc -- the dropped limb of both
+// polynomials in coefficient form and its broadcast into the lower limbs -- lives in this
+// fixed array instead of coming from the allocator.  Every device that loads the library
+// holds it until the process exits; all calls on a device share it, so calls whose GPU work
+// overlaps (other streams, other contexts on the same device) race on it.
+constexpr size_t kNoAllocScratchWords = (size_t)4 << 20;  // 32 MiB
+static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchWords];
+static u64* g_noalloc_addr[128] = {nullptr};  // device address of the array, per device ordinal
+
+// Device address of the array for the current device.  The first call on a device looks it
+// up (host code cannot use the array's name as a device address).
+static u64* noalloc_scratch() {
+    int dev = -1;
+    PFT_CUDA(cudaGetDevice(&dev));
+    NEED(dev >= 0 && dev < 128, PFT_ERR_ARG, "device ordinal out of range");
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        PFT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        NEED(p != nullptr, PFT_ERR_CUDA, "no device address for the fixed scratch array");
+        g_noalloc_addr[dev] = (u64*)p;
+    }
+    return g_noalloc_addr[dev];
+}
+
 // ---- launch accounting ---------------------------------------------------------------------
 namespace {
 struct Prof {
@@ -1343,6 +1370,36 @@ int pft_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pf
     return guard(c, [&] {
         NEED(c && a && out && B >= 0, PFT_ERR_ARG, "bad arguments");
         op_rotate_batch(c, a, B, step, out);
+    });
+}
+
+int pft_rescale_noalloc(pft_ctx* c, const uint64_t* in, int level, uint64_t* out) {
+    return guard(c, [&] {
+        NEED(c && in && out, PFT_ERR_ARG, "null argument");
+        NEED(level >= 2 && level <= c->L, PFT_ERR_ARG, "level must be in 2..L");
+        const size_t n = (size_t)c->n, l = (size_t)level;
+        const size_t need = 2 * n + 2 * (l - 1) * n;
+        NEED(need <= kNoAllocScratchWords, PFT_ERR_ARG,
+             "rescale_noalloc: 2 N level = " + std::to_string(2 * n * l) + " words exceed the fixed scratch of " +
+                 std::to_string(kNoAllocScratchWords) + " words");
+        const u64* in_end = in + 2 * l * n;
+        const u64* out_end = out + 2 * (l - 1) * n;
+        NEED(out_end <= in || in_end <= out, PFT_ERR_ARG, "rescale_noalloc: output overlaps input");
+        u64* last = noalloc_scratch();
+        u64* rb = last + 2 * n;
+        u64* src = (u64*)in;
+        std::vector<PolyRef> lin, lout, rr, x, o;
+        for (int pol = 0; pol < 2; pol++) {
+            lin.push_back(ref(src + ((size_t)pol * l + l - 1) * n, 1, level - 1));
+            lout.push_back(ref(last + (size_t)pol * n, 1, level - 1));
+            rr.push_back(ref(rb + (size_t)pol * (l - 1) * n, level - 1));
+            x.push_back(ref(src + (size_t)pol * l * n, level - 1));
+            o.push_back(ref(out + (size_t)pol * (l - 1) * n, level - 1));
+        }
+        ntt_inv(c, lin, lout);
+        rescale_bcast(c->tabs, mkset(lout, 0, 2), mkset(rr, 0, 2), c->stream);
+        ntt_fwd(c, rr, rr);
+        subscale(c, x, &rr, nullptr, o, c->rescale_consts[level - 1]);
     });
 }
 
