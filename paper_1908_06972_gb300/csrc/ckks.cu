@@ -173,6 +173,8 @@ static PolyRef cpoly(u64* data, int l, int n, int pol) { return ref(data + (size
 
 // ---- context construction ---------------------------------------------------------------
 static u64 shoup(u64 w, u64 q) { return (u64)(((unsigned __int128)w << 64) / q); }
+// basis-conversion constants are stored as (c mod 2^30) | (c >> 30) << 32
+static u64 split30_host(u64 c) { return (c & 0x3fffffffull) | ((c >> 30) << 32); }
 static int bitlen(u64 x) { return 64 - __builtin_clzll(x); }
 
 static const int kSecureLogQP[17] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 27, 54, 109, 218, 438, 881, 1772};
@@ -257,8 +259,8 @@ static void build_tables(pft_ctx* c) {
         }
         c->pmodq_consts.push_back(tab_upload(c, v));
     }
-    // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [targets][ns] qhat mod target,
-    // targets = rows 0..l+k-1 outside the digit, in order
+    // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [targets][ns] qhat mod target
+    // (30-bit split), targets = rows 0..l+k-1 outside the digit, in order
     c->modup_tab.assign((size_t)L * c->beta_max, nullptr);
     for (int l = 1; l <= L; l++) {
         const int beta = (l + c->alpha - 1) / c->alpha, E = l + k;
@@ -281,14 +283,14 @@ static void build_tables(pft_ctx* c) {
                     u64 hm = 1;
                     for (int i2 = 0; i2 < ns; i2++)
                         if (i2 != i) hm = mulmod_host(hm, c->primes[lo + i2] % t, t);
-                    tab[2 * ns + (size_t)mi * ns + i] = hm;
+                    tab[2 * ns + (size_t)mi * ns + i] = split30_host(hm);
                     mi++;
                 }
             }
             c->modup_tab[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
         }
     }
-    // ModDown tables per level: [k]{phat_inv, shoup}, then [l][k] phat mod q_m
+    // ModDown tables per level: [k]{phat_inv, shoup}, then [l][k] phat mod q_m (30-bit split)
     c->moddown_tab.assign(L, nullptr);
     for (int l = 1; l <= L; l++) {
         std::vector<u64> tab(2 * k + (size_t)k * l);
@@ -305,7 +307,7 @@ static void build_tables(pft_ctx* c) {
                 u64 hm = 1;
                 for (int i2 = 0; i2 < k; i2++)
                     if (i2 != i) hm = mulmod_host(hm, c->primes[L + i2] % t, t);
-                tab[2 * k + (size_t)m * k + i] = hm;
+                tab[2 * k + (size_t)m * k + i] = split30_host(hm);
             }
         }
         c->moddown_tab[l - 1] = tab_upload(c, tab);

@@ -42,6 +42,38 @@ __device__ __forceinline__ void mac_wide(U128& acc, u64 a, u64 b) {
     acc.hi += hi + (acc.lo < lo ? 1 : 0);
 }
 
+// Sums of up to 8 products of values below 2^60 in three 64-bit partial sums: with
+// a = a1 2^30 + a0 and b = b1 2^30 + b0 (all halves below 2^30),
+//   sum a b = S00 + 2^30 S01 + 2^60 S11,  S00 = sum a0 b0 < 2^63,
+//   S01 = sum (a0 b1 + a1 b0) < 2^64,  S11 = sum a1 b1 < 2^63,
+// so every term is one 32x32+64 multiply-add and no carry is handled per term.
+struct Acc3 {
+    u64 s00, s01, s11;
+};
+__device__ __forceinline__ void split30(u64 a, u32& lo, u32& hi) {
+    lo = (u32)a & 0x3fffffffu;
+    hi = (u32)(a >> 30);
+}
+__device__ __forceinline__ void acc3_mac(Acc3& A, u32 a0, u32 a1, u32 b0, u32 b1) {
+    A.s00 += (u64)a0 * b0;
+    A.s01 += (u64)a0 * b1;
+    A.s01 += (u64)a1 * b0;
+    A.s11 += (u64)a1 * b1;
+}
+// the 128-bit value S00 + 2^30 S01 + 2^60 S11
+__device__ __forceinline__ U128 acc3_value(const Acc3& A) {
+    U128 r;
+    r.lo = A.s00;
+    r.hi = 0;
+    const u64 t1 = A.s01 << 30;
+    r.lo += t1;
+    r.hi += (A.s01 >> 34) + (r.lo < t1 ? 1 : 0);
+    const u64 t2 = A.s11 << 60;
+    r.lo += t2;
+    r.hi += (A.s11 >> 4) + (r.lo < t2 ? 1 : 0);
+    return r;
+}
+
 // x mod q for x = hi 2^64 + lo < 2^(64 + s)
 __device__ __forceinline__ u64 barrett_reduce(u64 hi, u64 lo, const DPrime& P) {
     u64 x1 = (hi << (64 - P.s)) | (lo >> P.s);

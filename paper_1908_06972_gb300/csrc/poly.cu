@@ -3,6 +3,9 @@
 // Every kernel is a grid over (coefficient block, limb, polynomial) on the
 // limb-major [poly][limb][N] layout, moving two 64-bit words per thread with
 // 16-byte accesses.  Residues are canonical in [0, q) at every kernel boundary.
+#include <algorithm>
+#include <vector>
+
 #include "modarith.cuh"
 
 namespace pft {
@@ -215,105 +218,144 @@ void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g,
 // (rows [0, nrows) except [skip_lo, skip_hi), enumerated in order as targets 0..nt-1):
 //   out_m = sum_i y_i * (qhat_i mod t_m) mod t_m   (128-bit sum, one Barrett reduction).
 // Target prime of row m: m < split ? m : base2 + m - split.  Table: [ns] {inv, inv_shoup},
-// then [nt][ns] qhat_i mod t_m (target-major).  Four targets per iteration give four
-// independent accumulation chains per thread.
+// then [nt][ns] qhat_i mod t_m (target-major, each split into 30-bit halves: low word =
+// c mod 2^30, high word = c >> 30).  NS (the number of source primes) is a
+// compile-time constant; each thread converts two adjacent coefficients for two targets at
+// a time (four independent accumulation chains).
+template <int NS>
 __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
-    const BconvJob& J = jobs.j[blockIdx.y];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= t.n) return;
+    const BconvJob J = jobs.j[blockIdx.y];
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
     const int logn = t.logn;
-    const int ns = J.ns;
-    u64 y[kMaxAlpha];
+    u64 ya[NS], yb[NS];
 #pragma unroll
-    for (int i = 0; i < kMaxAlpha; i++) {
-        y[i] = 0;
-        if (i < ns) {
-            const u64 q = __ldg(&t.primes[J.src_p0 + i].q);
-            const u64 v = __ldg(J.src + ((size_t)i << logn) + x);
-            y[i] = mul_shoup(v, __ldg(&J.table[2 * i]), __ldg(&J.table[2 * i + 1]), q);
-        }
+    for (int i = 0; i < NS; i++) {
+        const u64 q = __ldg(&t.primes[J.src_p0 + i].q);
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(J.src + ((size_t)i << logn) + 2 * (size_t)x2);
+        const u64 w = __ldg(&J.table[2 * i]), wp = __ldg(&J.table[2 * i + 1]);
+        ya[i] = mul_shoup(v.x, w, wp, q);
+        yb[i] = mul_shoup(v.y, w, wp, q);
     }
-    const u64* T = J.table + 2 * ns;
+    u32 ya0[NS], ya1[NS], yb0[NS], yb1[NS];
+#pragma unroll
+    for (int i = 0; i < NS; i++) {
+        split30(ya[i], ya0[i], ya1[i]);
+        split30(yb[i], yb0[i], yb1[i]);
+    }
+    // constants stored pre-split: low word = c mod 2^30, high word = c >> 30
+    const uint2* T = reinterpret_cast<const uint2*>(J.table + 2 * NS);
     const int gap = J.skip_hi - J.skip_lo;
     const int nt = J.nrows - gap;
-    for (int m0 = 0; m0 < nt; m0 += 4) {
-        U128 acc[4];
+    for (int m0 = 0; m0 < nt; m0 += 2) {
+        const int m1i = m0 + 1 < nt ? m0 + 1 : m0;
+        Acc3 a0 = {0, 0, 0}, b0 = {0, 0, 0}, a1 = {0, 0, 0}, b1 = {0, 0, 0};
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            acc[u].lo = 0;
-            acc[u].hi = 0;
-            const int mi = m0 + u < nt ? m0 + u : nt - 1;
-#pragma unroll
-            for (int i = 0; i < kMaxAlpha; i++)
-                if (i < ns) mac_wide(acc[u], y[i], __ldg(&T[(size_t)mi * ns + i]));
+        for (int i = 0; i < NS; i++) {
+            const uint2 c0 = __ldg(&T[(size_t)m0 * NS + i]);
+            const uint2 c1 = __ldg(&T[(size_t)m1i * NS + i]);
+            acc3_mac(a0, ya0[i], ya1[i], c0.x, c0.y);
+            acc3_mac(b0, yb0[i], yb1[i], c0.x, c0.y);
+            acc3_mac(a1, ya0[i], ya1[i], c1.x, c1.y);
+            acc3_mac(b1, yb0[i], yb1[i], c1.x, c1.y);
         }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int mi = m0 + u;
-            if (mi < nt) {
-                const int m = mi < J.skip_lo ? mi : mi + gap;
-                const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
-                J.dst[((size_t)m << logn) + x] = barrett_reduce(acc[u].hi, acc[u].lo, P);
-            }
+        {
+            const int m = m0 < J.skip_lo ? m0 : m0 + gap;
+            const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
+            const U128 va = acc3_value(a0), vb = acc3_value(b0);
+            ulonglong2 r;
+            r.x = barrett_reduce(va.hi, va.lo, P);
+            r.y = barrett_reduce(vb.hi, vb.lo, P);
+            *reinterpret_cast<ulonglong2*>(J.dst + ((size_t)m << logn) + 2 * (size_t)x2) = r;
+        }
+        if (m0 + 1 < nt) {
+            const int m = m1i < J.skip_lo ? m1i : m1i + gap;
+            const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
+            const U128 va = acc3_value(a1), vb = acc3_value(b1);
+            ulonglong2 r;
+            r.x = barrett_reduce(va.hi, va.lo, P);
+            r.y = barrett_reduce(vb.hi, vb.lo, P);
+            *reinterpret_cast<ulonglong2*>(J.dst + ((size_t)m << logn) + 2 * (size_t)x2) = r;
         }
     }
 }
 
 void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st) {
-    for (int a = 0; a < n_jobs; a += kMaxBconv) {
-        const int cnt = n_jobs - a < kMaxBconv ? n_jobs - a : kMaxBconv;
-        BconvBatch b;
-        for (int i = 0; i < cnt; i++) b.j[i] = jobs[a + i];
-        dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)cnt);
-        PFT_PROF("bconv", st, 0.0);
-        k_bconv<<<grid, 256, 0, st>>>(t, b);
-        PFT_LAUNCH_CHECK("bconv");
+    // one launch per source-prime count (the last ModUp digit can be shorter)
+    for (int ns = 1; ns <= kMaxAlpha; ns++) {
+        std::vector<BconvJob> sel;
+        for (int i = 0; i < n_jobs; i++)
+            if (jobs[i].ns == ns) sel.push_back(jobs[i]);
+        for (size_t a = 0; a < sel.size(); a += kMaxBconv) {
+            const int cnt = (int)std::min(sel.size() - a, (size_t)kMaxBconv);
+            BconvBatch b;
+            for (int i = 0; i < cnt; i++) b.j[i] = sel[a + i];
+            dim3 grid((unsigned)((t.n / 2 + 255) / 256), (unsigned)cnt);
+            PFT_PROF("bconv", st, 0.0);
+            switch (ns) {
+                case 1: k_bconv<1><<<grid, 256, 0, st>>>(t, b); break;
+                case 2: k_bconv<2><<<grid, 256, 0, st>>>(t, b); break;
+                case 3: k_bconv<3><<<grid, 256, 0, st>>>(t, b); break;
+                case 4: k_bconv<4><<<grid, 256, 0, st>>>(t, b); break;
+                case 5: k_bconv<5><<<grid, 256, 0, st>>>(t, b); break;
+                case 6: k_bconv<6><<<grid, 256, 0, st>>>(t, b); break;
+                case 7: k_bconv<7><<<grid, 256, 0, st>>>(t, b); break;
+                default: k_bconv<8><<<grid, 256, 0, st>>>(t, b); break;
+            }
+            PFT_LAUNCH_CHECK("bconv");
+        }
     }
 }
 
 // ---- key-switching inner product ---------------------------------------------------------
 //   u[b][pol][m] = sum_{j < beta} ext[b][j][m] * key[j][pol][row(m)],  m < l + k,
-//   row(m) = m (m < l) or L + m - l (special rows).  The key slice of coefficient x is
-// held in registers and reused for all B inputs, so each key word is read once per batch.
+//   row(m) = m (m < l) or L + m - l (special rows).  The key slice of two adjacent
+// coefficients is held in registers and reused for all B inputs, so each key word is read
+// once per batch; 16-byte loads keep two coefficients in flight per access.
 template <int BMAX>
-__global__ void k_ks_inner(DevTables t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k,
-                           int beta) {
+__global__ void __launch_bounds__(128) k_ks_inner(DevTables t, const u64* ext, u64* u, const u64* key, int B, int l,
+                                                  int L, int k, int beta) {
     const int m = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= t.n) return;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
     const int logn = t.logn;
     const int E = l + k;
     const int row = m < l ? m : L + m - l;
     const int rows_total = L + k;
     const DPrime P = load_prime(t.primes, row);
-    u64 kb[BMAX], ka[BMAX];
+    const size_t xo = 2 * (size_t)x2;
+    ulonglong2 kb[BMAX], ka[BMAX];
 #pragma unroll
     for (int j = 0; j < BMAX; j++) {
         if (j < beta) {
-            kb[j] = __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x);
-            ka[j] = __ldg(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + x);
+            kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + xo));
+            ka[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + xo));
         }
     }
     for (int b = 0; b < B; b++) {
         const u64* eb = ext + ((size_t)b * beta * E << logn);
-        U128 s0 = {0, 0}, s1 = {0, 0};
+        ulonglong2 v[BMAX];
+#pragma unroll
+        for (int j = 0; j < BMAX; j++)
+            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(eb + (((size_t)j * E + m) << logn) + xo));
+        U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
 #pragma unroll
         for (int j = 0; j < BMAX; j++) {
-            if (j < beta) {
-                const u64 v = __ldg(eb + (((size_t)j * E + m) << logn) + x);
-                mac_wide(s0, v, kb[j]);
-                mac_wide(s1, v, ka[j]);
-                if ((j & 7) == 7) {
-                    s0.lo = barrett_reduce(s0.hi, s0.lo, P);
-                    s0.hi = 0;
-                    s1.lo = barrett_reduce(s1.hi, s1.lo, P);
-                    s1.hi = 0;
-                }
+            if (j < beta) {  // beta <= 8 here: 128-bit sums of at most 8 products
+                mac_wide(s0x, v[j].x, kb[j].x);
+                mac_wide(s0y, v[j].y, kb[j].y);
+                mac_wide(s1x, v[j].x, ka[j].x);
+                mac_wide(s1y, v[j].y, ka[j].y);
             }
         }
         u64* ub = u + ((size_t)b * 2 * E << logn);
-        ub[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
-        ub[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
+        ulonglong2 r0, r1;
+        r0.x = barrett_reduce(s0x.hi, s0x.lo, P);
+        r0.y = barrett_reduce(s0y.hi, s0y.lo, P);
+        r1.x = barrett_reduce(s1x.hi, s1x.lo, P);
+        r1.y = barrett_reduce(s1y.hi, s1y.lo, P);
+        *reinterpret_cast<ulonglong2*>(ub + ((size_t)m << logn) + xo) = r0;
+        *reinterpret_cast<ulonglong2*>(ub + (((size_t)E + m) << logn) + xo) = r1;
     }
 }
 
@@ -351,12 +393,12 @@ __global__ void k_ks_inner_generic(DevTables t, const u64* ext, u64* u, const u6
 void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k, int beta,
               cudaStream_t st) {
     if (B == 0) return;
-    dim3 grid((unsigned)((t.n + 127) / 128), (unsigned)(l + k));
+    dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(l + k));
+    dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(l + k));
     PFT_PROF("ks_inner", st, (double)t.n * 8.0 * (2.0 * beta * (l + k) + (double)B * beta * (l + k) + 2.0 * B * (l + k)));
-    if (beta <= 4) k_ks_inner<4><<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
-    else if (beta <= 8) k_ks_inner<8><<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
-    else if (beta <= 16) k_ks_inner<16><<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
-    else k_ks_inner_generic<<<grid, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    if (beta <= 4) k_ks_inner<4><<<grid2, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    else if (beta <= 8) k_ks_inner<8><<<grid2, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
+    else k_ks_inner_generic<<<grid1, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
     PFT_LAUNCH_CHECK("ks_inner");
 }
 
