@@ -196,11 +196,10 @@ def run_gpu(args):
     d2h = sum(o.nbytes for o in host_out)
 
     def step_e2e():
-        ins = [pft.pft_ct_import(ctx, arr, sc) for arr, sc in host_in]
+        ins = pft.pft_ct_import_batch(ctx, [arr for arr, _ in host_in], [sc for _, sc in host_in])
         a, b = ins[0::2], ins[1::2]
         step_batched(a, b, C)
-        for i in range(BATCH):
-            pft.pft_ct_export(ctx, C[i], host_out[i])
+        pft.pft_ct_export_batch(ctx, C, host_out)
         for h in ins:
             pft.pft_ct_destroy(h)
 

@@ -194,6 +194,13 @@ int pft_decrypt(pft_ctx* ctx, const pft_ct* ct, pft_pt** out);
 int pft_ct_import(pft_ctx* ctx, const uint64_t* coeffs, int level, double scale, pft_ct** out);
 int pft_ct_export(pft_ctx* ctx, const pft_ct* ct, uint64_t* coeffs, size_t n);
 
+/* Batched transfers: B ciphertexts in one call, one transform launch, and (export) one
+ * stream synchronisation at the end.  coeffs[i] points at [2][levels[i]][N] host words
+ * (pinned host memory makes the copies asynchronous).  Import creates B new handles. */
+int pft_ct_import_batch(pft_ctx* ctx, const uint64_t* const* coeffs, const int* levels, const double* scales, int B,
+                        pft_ct** out);
+int pft_ct_export_batch(pft_ctx* ctx, const pft_ct* const* cts, int B, uint64_t* const* coeffs);
+
 /* ---- homomorphic operations (Sec. 2.3) ------------------------------------
  * `out` must be a handle from pft_ct_create / an op; it is resized as needed. */
 int pft_add(pft_ctx* ctx, const pft_ct* a, const pft_ct* b, pft_ct* out);       /* HADD */

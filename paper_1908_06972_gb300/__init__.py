@@ -77,6 +77,8 @@ def lib():
             "pft_pt_import": [vp, u64, i, d, pp], "pft_pt_export": [vp, vp, u64, c_size_t],
             "pft_encrypt": [vp, vp, i, u32, pp], "pft_decrypt": [vp, vp, pp],
             "pft_ct_import": [vp, u64, i, d, pp], "pft_ct_export": [vp, vp, u64, c_size_t],
+            "pft_ct_import_batch": [vp, pp, ip, POINTER(c_double), i, pp],
+            "pft_ct_export_batch": [vp, pp, i, pp],
             "pft_add": [vp, vp, vp, vp], "pft_sub": [vp, vp, vp, vp], "pft_add_plain": [vp, vp, vp, vp],
             "pft_mul_plain": [vp, vp, vp, vp], "pft_mul_relin": [vp, vp, vp, vp],
             "pft_rescale": [vp, vp, vp], "pft_rotate": [vp, vp, c_int32, vp],
@@ -114,7 +116,8 @@ def exported_symbols():
             "pft_add_batch", "pft_mul_plain_batch", "pft_mul_relin_batch", "pft_rescale_batch",
             "pft_rotate_batch", "pft_ntt", "pft_ft_model_create", "pft_ft_model_import",
             "pft_ft_model_destroy", "pft_fasttext_infer", "pft_fasttext_infer_batch",
-            "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc"]
+            "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc",
+            "pft_ct_import_batch", "pft_ct_export_batch"]
 
 
 def _check(rc, ctx=None):
@@ -335,6 +338,24 @@ def pft_ct_export(ctx, ct, out=None):
         out = np.zeros((2, pft_ct_level(ct), n), np.uint64)
     _check(lib().pft_ct_export(ctx, ct, _u64p(out), out.size), ctx)
     return out
+
+
+def pft_ct_import_batch(ctx, arrays, scales):
+    """arrays: list of uint64 [2][l][N] host arrays (pinned for asynchronous copies)."""
+    B = len(arrays)
+    ptrs = (c_void_p * max(1, B))(*[a.ctypes.data for a in arrays])
+    levels = (c_int * max(1, B))(*[a.shape[1] for a in arrays])
+    sc = (c_double * max(1, B))(*scales)
+    out = (c_void_p * max(1, B))()
+    _check(lib().pft_ct_import_batch(ctx, ptrs, levels, sc, B, out), ctx)
+    return [c_void_p(out[i]) for i in range(B)]
+
+
+def pft_ct_export_batch(ctx, cts, arrays):
+    """Exports cts[i] into the uint64 [2][l][N] host array arrays[i] (one synchronisation)."""
+    ptrs = (c_void_p * max(1, len(arrays)))(*[a.ctypes.data for a in arrays])
+    _check(lib().pft_ct_export_batch(ctx, _arr(cts), len(cts), ptrs), ctx)
+    return arrays
 
 
 # ---- operations -----------------------------------------------------------------------------

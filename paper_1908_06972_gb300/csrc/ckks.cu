@@ -420,27 +420,42 @@ struct KsIO {
     const u64* acc1;  // may be null
     u64* out0;
     u64* out1;
+    int l;  // level of this input
 };
 
-// For each input d (level l): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
-static void keyswitch_group(pft_ctx* c, int l, const u64* key, const std::vector<KsIO>& io) {
-    const int n = c->n, L = c->L, k = c->k, E = l + k, alpha = c->alpha;
-    const int beta = (l + alpha - 1) / alpha;
+// For each input d (any level): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
+// Every stage is one launch (or a few, by descriptor capacity) over all inputs, whatever
+// their levels; the key is read once per stage.
+static void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>& io) {
+    const int L = c->L, k = c->k, alpha = c->alpha;
     const size_t B = io.size();
     if (B == 0) return;
-    const size_t limb = (size_t)n;
-    Scratch Dc(c, B * l * limb * 8), Ext(c, B * beta * E * limb * 8), U(c, B * 2 * E * limb * 8),
-        Cv(c, B * 2 * l * limb * 8);
-    auto dc = [&](size_t b) { return Dc.u() + b * l * limb; };
-    auto ext = [&](size_t b, int j) { return Ext.u() + (b * beta + j) * E * limb; };
-    auto uu = [&](size_t b, int pol) { return U.u() + (b * 2 + pol) * E * limb; };
-    auto cv = [&](size_t b, int pol) { return Cv.u() + (b * 2 + pol) * l * limb; };
+    const size_t limb = (size_t)c->n;
+    std::vector<size_t> oDc(B), oExt(B), oU(B), oCv(B);
+    size_t tDc = 0, tExt = 0, tU = 0, tCv = 0;
+    for (size_t b = 0; b < B; b++) {
+        const int l = io[b].l, E = l + k, beta = (l + alpha - 1) / alpha;
+        oDc[b] = tDc;
+        tDc += l;
+        oExt[b] = tExt;
+        tExt += (size_t)beta * E;
+        oU[b] = tU;
+        tU += 2 * (size_t)E;
+        oCv[b] = tCv;
+        tCv += 2 * (size_t)l;
+    }
+    Scratch Dc(c, tDc * limb * 8), Ext(c, tExt * limb * 8), U(c, tU * limb * 8), Cv(c, tCv * limb * 8);
+    auto Eof = [&](size_t b) { return io[b].l + k; };
+    auto dc = [&](size_t b) { return Dc.u() + oDc[b] * limb; };
+    auto ext = [&](size_t b, int j) { return Ext.u() + (oExt[b] + (size_t)j * Eof(b)) * limb; };
+    auto uu = [&](size_t b, int pol) { return U.u() + (oU[b] + (size_t)pol * Eof(b)) * limb; };
+    auto cv = [&](size_t b, int pol) { return Cv.u() + (oCv[b] + (size_t)pol * io[b].l) * limb; };
     // 1. coefficient form of d
     {
         std::vector<PolyRef> in, out;
         for (size_t b = 0; b < B; b++) {
-            in.push_back(ref((u64*)io[b].d, l));
-            out.push_back(ref(dc(b), l));
+            in.push_back(ref((u64*)io[b].d, io[b].l));
+            out.push_back(ref(dc(b), io[b].l));
         }
         ntt_inv(c, in, out);
     }
@@ -448,7 +463,8 @@ static void keyswitch_group(pft_ctx* c, int l, const u64* key, const std::vector
     {
         std::vector<BconvJob> jobs;
         std::vector<PolyRef> cin, cout;
-        for (size_t b = 0; b < B; b++)
+        for (size_t b = 0; b < B; b++) {
+            const int l = io[b].l, E = l + k, beta = (l + alpha - 1) / alpha;
             for (int j = 0; j < beta; j++) {
                 const int lo = j * alpha, hi = std::min(l, lo + alpha);
                 BconvJob J;
@@ -467,27 +483,40 @@ static void keyswitch_group(pft_ctx* c, int l, const u64* key, const std::vector
                 cin.push_back(ref((u64*)io[b].d + (size_t)lo * limb, hi - lo, lo));
                 cout.push_back(ref(ext(b, j) + (size_t)lo * limb, hi - lo, lo));
             }
+        }
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
         ew(c, EwOp::Copy, cin, {}, cout);
     }
     // 3. evaluation form of the converted rows
     {
         std::vector<PolyRef> rows;
-        for (size_t b = 0; b < B; b++)
+        for (size_t b = 0; b < B; b++) {
+            const int l = io[b].l, E = l + k, beta = (l + alpha - 1) / alpha;
             for (int j = 0; j < beta; j++) {
                 const int lo = j * alpha, hi = std::min(l, lo + alpha);
                 if (lo > 0) rows.push_back(ref(ext(b, j), lo, 0));
                 rows.push_back(ref(ext(b, j) + (size_t)hi * limb, E - hi, hi, l - hi, L));
             }
+        }
         ntt_fwd(c, rows, rows);
     }
-    // 4. inner product with the key
-    ks_inner(c->tabs, Ext.u(), U.u(), key, (int)B, l, L, k, beta, c->stream);
+    // 4. inner product with the key (one pass over the key for all inputs)
+    {
+        std::vector<KsDesc> d(B);
+        for (size_t b = 0; b < B; b++) {
+            d[b].ext = ext(b, 0);
+            d[b].u = uu(b, 0);
+            d[b].l = io[b].l;
+            d[b].pad = 0;
+        }
+        ks_inner_multi(c->tabs, d.data(), (int)B, key, L, k, alpha, c->stream);
+    }
     // 5. ModDown: coefficient form of the special rows, conversion to q_0..q_{l-1}, evaluation form
     {
         std::vector<PolyRef> sp, cvr;
         std::vector<BconvJob> jobs;
-        for (size_t b = 0; b < B; b++)
+        for (size_t b = 0; b < B; b++) {
+            const int l = io[b].l;
             for (int pol = 0; pol < 2; pol++) {
                 sp.push_back(ref(uu(b, pol) + (size_t)l * limb, k, 0, 0, L));
                 cvr.push_back(ref(cv(b, pol), l));
@@ -505,6 +534,7 @@ static void keyswitch_group(pft_ctx* c, int l, const u64* key, const std::vector
                 J.pad = 0;
                 jobs.push_back(J);
             }
+        }
         ntt_inv(c, sp, sp);
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
         ntt_fwd(c, cvr, cvr);
@@ -520,6 +550,7 @@ static void keyswitch_group(pft_ctx* c, int l, const u64* key, const std::vector
         }
         NEED(all0 && (all1 || none1), PFT_ERR_ARG, "internal: mixed accumulators");
         for (size_t b = 0; b < B; b++) {
+            const int l = io[b].l;
             x.push_back(ref(uu(b, 0), l));
             y.push_back(ref(cv(b, 0), l));
             acc.push_back(ref((u64*)io[b].acc0, l));
@@ -600,31 +631,35 @@ static void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct*
         NEED(out[i], PFT_ERR_ARG, "null output");
         NEED(a[i]->level == b[i]->level, PFT_ERR_LEVEL_MISMATCH, "HMUL operands at different levels");
     }
+    if (B == 0) return;
     const size_t limb = c->n;
-    for (auto& kv : by_level(a, B)) {
-        const int l = kv.first;
-        const std::vector<int>& idx = kv.second;
-        Scratch D(c, idx.size() * 3 * l * limb * 8);
-        std::vector<PolyRef> ra, rb, rd;
-        for (size_t g = 0; g < idx.size(); g++) {
-            ra.push_back(ref(a[idx[g]]->data, l));
-            rb.push_back(ref(b[idx[g]]->data, l));
-            rd.push_back(ref(D.u() + g * 3 * l * limb, l));
-        }
-        chunks(rd.size(), [&](size_t x, size_t y) {
-            ew_tensor(c->tabs, mkset(ra, x, y), mkset(rb, x, y), mkset(rd, x, y), c->stream);
-        });
-        std::vector<KsIO> io;
-        for (size_t g = 0; g < idx.size(); g++) {
-            pft_ct* o = out[idx[g]];
-            const double sc = a[idx[g]]->scale * b[idx[g]]->scale;
-            ensure_ct(c, o, l);
-            o->scale = sc;
-            u64* d = D.u() + g * 3 * l * limb;
-            io.push_back(KsIO{d + 2 * l * limb, d, d + l * limb, o->data, o->data + l * limb});
-        }
-        keyswitch_group(c, l, c->keys[0], io);
+    std::vector<size_t> off(B);
+    size_t tot = 0;
+    for (int i = 0; i < B; i++) {
+        off[i] = tot;
+        tot += 3 * (size_t)a[i]->level;
     }
+    Scratch D(c, tot * limb * 8);
+    std::vector<PolyRef> ra, rb, rd;
+    for (int i = 0; i < B; i++) {
+        const int l = a[i]->level;
+        ra.push_back(ref(a[i]->data, l));
+        rb.push_back(ref(b[i]->data, l));
+        rd.push_back(ref(D.u() + off[i] * limb, l));
+    }
+    chunks(rd.size(), [&](size_t x, size_t y) {
+        ew_tensor(c->tabs, mkset(ra, x, y), mkset(rb, x, y), mkset(rd, x, y), c->stream);
+    });
+    std::vector<KsIO> io;
+    for (int i = 0; i < B; i++) {
+        const int l = a[i]->level;
+        const double sc = a[i]->scale * b[i]->scale;
+        ensure_ct(c, out[i], l);
+        out[i]->scale = sc;
+        u64* d = D.u() + off[i] * limb;
+        io.push_back(KsIO{d + 2 * l * limb, d, d + l * limb, out[i]->data, out[i]->data + l * limb, l});
+    }
+    keyswitch_batch(c, c->keys[0], io);
 }
 
 static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out) {
@@ -646,30 +681,35 @@ static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t s
         return;
     }
     NEED(c->keys.count(g), PFT_ERR_NO_KEY, "no rotation key for step " + std::to_string(step));
-    for (auto& kv : by_level(a, B)) {
-        const int l = kv.first;
-        const std::vector<int>& idx = kv.second;
-        Scratch R(c, idx.size() * 2 * l * limb * 8);
-        std::vector<PolyRef> rin, rout;
-        for (size_t i = 0; i < idx.size(); i++)
-            for (int pol = 0; pol < 2; pol++) {
-                rin.push_back(cpoly(a[idx[i]]->data, l, c->n, pol));
-                rout.push_back(cpoly(R.u() + i * 2 * l * limb, l, c->n, pol));
-            }
-        chunks(rout.size(), [&](size_t x, size_t y) {
-            automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
-        });
-        std::vector<KsIO> io;
-        for (size_t i = 0; i < idx.size(); i++) {
-            pft_ct* o = out[idx[i]];
-            const double sc = a[idx[i]]->scale;
-            ensure_ct(c, o, l);
-            o->scale = sc;
-            u64* r = R.u() + i * 2 * l * limb;
-            io.push_back(KsIO{r + l * limb, r, nullptr, o->data, o->data + l * limb});
-        }
-        keyswitch_group(c, l, c->keys[g], io);
+    if (B == 0) return;
+    std::vector<size_t> off(B);
+    size_t tot = 0;
+    for (int i = 0; i < B; i++) {
+        off[i] = tot;
+        tot += 2 * (size_t)a[i]->level;
     }
+    Scratch R(c, tot * limb * 8);
+    std::vector<PolyRef> rin, rout;
+    for (int i = 0; i < B; i++) {
+        const int l = a[i]->level;
+        for (int pol = 0; pol < 2; pol++) {
+            rin.push_back(cpoly(a[i]->data, l, c->n, pol));
+            rout.push_back(cpoly(R.u() + off[i] * limb, l, c->n, pol));
+        }
+    }
+    chunks(rout.size(), [&](size_t x, size_t y) {
+        automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
+    });
+    std::vector<KsIO> io;
+    for (int i = 0; i < B; i++) {
+        const int l = a[i]->level;
+        const double sc = a[i]->scale;
+        ensure_ct(c, out[i], l);
+        out[i]->scale = sc;
+        u64* r = R.u() + off[i] * limb;
+        io.push_back(KsIO{r + l * limb, r, nullptr, out[i]->data, out[i]->data + l * limb, l});
+    }
+    keyswitch_batch(c, c->keys[g], io);
 }
 
 static void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
@@ -835,9 +875,10 @@ static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* cons
                 std::vector<KsIO> io;
                 for (size_t i = t0; i < t1; i++) {
                     u64* r = R.u() + (i - t0) * 2 * l * limb;
-                    io.push_back(KsIO{r + l * limb, T[i].data, T[i].data + l * limb, T[i].data, T[i].data + l * limb});
+                    io.push_back(
+                        KsIO{r + l * limb, T[i].data, T[i].data + l * limb, T[i].data, T[i].data + l * limb, l});
                 }
-                keyswitch_group(c, l, c->keys[g], io);
+                keyswitch_batch(c, c->keys[g], io);
             }
         }
     }
@@ -1238,6 +1279,57 @@ int pft_ct_export(pft_ctx* c, const pft_ct* ct, uint64_t* coeffs, size_t nw) {
         std::vector<PolyRef> o{cpoly(t.u(), ct->level, c->n, 0), cpoly(t.u(), ct->level, c->n, 1)};
         ntt_inv(c, in, o);
         PFT_CUDA(cudaMemcpyAsync(coeffs, t.p, words * 8, cudaMemcpyDeviceToHost, c->stream));
+        PFT_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+int pft_ct_import_batch(pft_ctx* c, const uint64_t* const* coeffs, const int* levels, const double* scales, int B,
+                        pft_ct** out) {
+    return guard(c, [&] {
+        NEED(c && coeffs && levels && scales && out && B >= 0, PFT_ERR_ARG, "bad arguments");
+        std::vector<std::unique_ptr<pft_ct>> cts;
+        std::vector<PolyRef> r;
+        for (int i = 0; i < B; i++) {
+            NEED(coeffs[i] && levels[i] >= 1 && levels[i] <= c->L, PFT_ERR_ARG, "bad ciphertext " + std::to_string(i));
+            cts.emplace_back(new pft_ct());
+            pft_ct* ct = cts.back().get();
+            ct->ctx = c;
+            ensure_ct(c, ct, levels[i]);
+            ct->scale = scales[i];
+            PFT_CUDA(cudaMemcpyAsync(ct->data, coeffs[i], (size_t)2 * levels[i] * c->n * 8, cudaMemcpyHostToDevice,
+                                     c->stream));
+            r.push_back(cpoly(ct->data, levels[i], c->n, 0));
+            r.push_back(cpoly(ct->data, levels[i], c->n, 1));
+        }
+        ntt_fwd(c, r, r);
+        for (int i = 0; i < B; i++) out[i] = cts[i].release();
+    });
+}
+
+int pft_ct_export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs) {
+    return guard(c, [&] {
+        NEED(c && cts && coeffs && B >= 0, PFT_ERR_ARG, "bad arguments");
+        size_t tot = 0;
+        std::vector<size_t> off(B);
+        for (int i = 0; i < B; i++) {
+            check_ct(cts[i]);
+            NEED(coeffs[i], PFT_ERR_ARG, "null output buffer");
+            off[i] = tot;
+            tot += (size_t)2 * cts[i]->level * c->n;
+        }
+        Scratch t(c, tot * 8);
+        std::vector<PolyRef> in, o;
+        for (int i = 0; i < B; i++) {
+            const int l = cts[i]->level;
+            for (int pol = 0; pol < 2; pol++) {
+                in.push_back(cpoly(cts[i]->data, l, c->n, pol));
+                o.push_back(cpoly(t.u() + off[i], l, c->n, pol));
+            }
+        }
+        ntt_inv(c, in, o);
+        for (int i = 0; i < B; i++)
+            PFT_CUDA(cudaMemcpyAsync(coeffs[i], t.u() + off[i], (size_t)2 * cts[i]->level * c->n * 8,
+                                     cudaMemcpyDeviceToHost, c->stream));
         PFT_CUDA(cudaStreamSynchronize(c->stream));
     });
 }

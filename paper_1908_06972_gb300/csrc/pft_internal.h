@@ -121,10 +121,18 @@ struct BconvJob {
 };
 void bconv(const DevTables& t, const BconvJob* jobs_host, int n_jobs, cudaStream_t st);  // jobs: host array
 
-// Key inner product for B inputs at level l sharing one key [beta_max][2][L+k][N]:
-//   u[b][pol][m] = sum_j ext[b][j][m] * key[j][pol][row(m)],  ext: [B][beta][l+k][N], u: [B][2][l+k][N].
-void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k, int beta,
-              cudaStream_t st);
+// Key inner product: u[b][pol][m] = sum_j ext[b][j][m] * key[j][pol][row(m)] over B inputs at
+// any levels in one launch (the key is read once for all);
+// input b has level l, ext [beta(l)][l+k][N], u [2][l+k][N].
+struct KsDesc {
+    const u64* ext;
+    u64* u;
+    int l;
+    int pad;
+};
+constexpr int kMaxKs = 128;  // inputs per launch (by-value parameters)
+void ks_inner_multi(const DevTables& t, const KsDesc* descs_host, int B, const u64* key, int L, int k, int alpha,
+                    cudaStream_t st);
 // r = (last + h) mod p, h = floor(p/2), p = prime nlimbs(out); limb k of out = (r - h) mod q_k.
 void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st);
 

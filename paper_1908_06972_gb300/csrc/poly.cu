@@ -15,6 +15,10 @@ static constexpr int kEwThreads = 256;
 struct BconvBatch {
     BconvJob j[kMaxBconv];
 };
+struct KsBatch {
+    KsDesc d[kMaxKs];
+    uint8_t need[kMaxPrimes];  // per key row: digits used by any input of the batch (0: row unused)
+};
 
 static dim3 ew_grid(int n, const PolySet& s) {
     return dim3((unsigned)((n / 2 + kEwThreads - 1) / kEwThreads), (unsigned)s.max_limbs, (unsigned)s.count);
@@ -307,74 +311,80 @@ void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st
     }
 }
 
-// ---- key-switching inner product ---------------------------------------------------------
-//   u[b][pol][m] = sum_{j < beta} ext[b][j][m] * key[j][pol][row(m)],  m < l + k,
-//   row(m) = m (m < l) or L + m - l (special rows).  The key slice of two adjacent
-// coefficients is held in registers and reused for all B inputs, so each key word is read
-// once per batch; 16-byte loads keep two coefficients in flight per access.
+// ---- key inner product over inputs at different levels -----------------------------------
+// Row `row` of the key (q rows 0..L-1, special rows L..L+k-1) is used by every input whose
+// level l exceeds it (q rows) or by every input (special rows); for input b its extended row
+// is m = row (q rows) or l + row - L.  The key slice of two coefficients (digits up to the
+// largest the participating inputs need) stays in registers across all inputs.
 template <int BMAX>
-__global__ void __launch_bounds__(128) k_ks_inner(DevTables t, const u64* ext, u64* u, const u64* key, int B, int l,
-                                                  int L, int k, int beta) {
-    const int m = blockIdx.y;
+__global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt, int B, const u64* key, int L, int k,
+                                                        int alpha) {
+    const int row = blockIdx.y;
     const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * x2 >= t.n) return;
     const int logn = t.logn;
-    const int E = l + k;
-    const int row = m < l ? m : L + m - l;
     const int rows_total = L + k;
+    const int need = bt.need[row];
+    if (need == 0) return;
     const DPrime P = load_prime(t.primes, row);
     const size_t xo = 2 * (size_t)x2;
     ulonglong2 kb[BMAX], ka[BMAX];
 #pragma unroll
     for (int j = 0; j < BMAX; j++) {
-        if (j < beta) {
+        if (j < need) {
             kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + xo));
             ka[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + xo));
         }
     }
     for (int b = 0; b < B; b++) {
-        const u64* eb = ext + ((size_t)b * beta * E << logn);
+        const KsDesc D = bt.d[b];
+        const int l = D.l;
+        if (row < L && row >= l) continue;
+        const int m = row < L ? row : l + row - L;
+        const int E = l + k;
+        const int beta = (l + alpha - 1) / alpha;
         ulonglong2 v[BMAX];
 #pragma unroll
         for (int j = 0; j < BMAX; j++)
-            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(eb + (((size_t)j * E + m) << logn) + xo));
+            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(D.ext + (((size_t)j * E + m) << logn) + xo));
         U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
 #pragma unroll
         for (int j = 0; j < BMAX; j++) {
-            if (j < beta) {  // beta <= 8 here: 128-bit sums of at most 8 products
+            if (j < beta) {  // beta <= 8: 128-bit sums of at most 8 products
                 mac_wide(s0x, v[j].x, kb[j].x);
                 mac_wide(s0y, v[j].y, kb[j].y);
                 mac_wide(s1x, v[j].x, ka[j].x);
                 mac_wide(s1y, v[j].y, ka[j].y);
             }
         }
-        u64* ub = u + ((size_t)b * 2 * E << logn);
         ulonglong2 r0, r1;
         r0.x = barrett_reduce(s0x.hi, s0x.lo, P);
         r0.y = barrett_reduce(s0y.hi, s0y.lo, P);
         r1.x = barrett_reduce(s1x.hi, s1x.lo, P);
         r1.y = barrett_reduce(s1y.hi, s1y.lo, P);
-        *reinterpret_cast<ulonglong2*>(ub + ((size_t)m << logn) + xo) = r0;
-        *reinterpret_cast<ulonglong2*>(ub + (((size_t)E + m) << logn) + xo) = r1;
+        *reinterpret_cast<ulonglong2*>(D.u + ((size_t)m << logn) + xo) = r0;
+        *reinterpret_cast<ulonglong2*>(D.u + (((size_t)E + m) << logn) + xo) = r1;
     }
 }
 
-// Same sum for any number of digits, re-reading the key for every input.
-__global__ void k_ks_inner_generic(DevTables t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k,
-                                   int beta) {
-    const int m = blockIdx.y;
+// Any number of digits: the key is re-read for every input.
+__global__ void k_ks_inner_multi_generic(DevTables t, KsBatch bt, int B, const u64* key, int L, int k, int alpha) {
+    const int row = blockIdx.y;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= t.n) return;
     const int logn = t.logn;
-    const int E = l + k;
-    const int row = m < l ? m : L + m - l;
     const int rows_total = L + k;
     const DPrime P = load_prime(t.primes, row);
     for (int b = 0; b < B; b++) {
-        const u64* eb = ext + ((size_t)b * beta * E << logn);
+        const KsDesc D = bt.d[b];
+        const int l = D.l;
+        if (row < L && row >= l) continue;
+        const int m = row < L ? row : l + row - L;
+        const int E = l + k;
+        const int beta = (l + alpha - 1) / alpha;
         U128 s0 = {0, 0}, s1 = {0, 0};
         for (int j = 0; j < beta; j++) {
-            const u64 v = __ldg(eb + (((size_t)j * E + m) << logn) + x);
+            const u64 v = __ldg(D.ext + (((size_t)j * E + m) << logn) + x);
             mac_wide(s0, v, __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x));
             mac_wide(s1, v, __ldg(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + x));
             if ((j & 7) == 7) {
@@ -384,22 +394,37 @@ __global__ void k_ks_inner_generic(DevTables t, const u64* ext, u64* u, const u6
                 s1.hi = 0;
             }
         }
-        u64* ub = u + ((size_t)b * 2 * E << logn);
-        ub[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
-        ub[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
+        D.u[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
+        D.u[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
     }
 }
 
-void ks_inner(const DevTables& t, const u64* ext, u64* u, const u64* key, int B, int l, int L, int k, int beta,
-              cudaStream_t st) {
-    if (B == 0) return;
-    dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(l + k));
-    dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(l + k));
-    PFT_PROF("ks_inner", st, (double)t.n * 8.0 * (2.0 * beta * (l + k) + (double)B * beta * (l + k) + 2.0 * B * (l + k)));
-    if (beta <= 4) k_ks_inner<4><<<grid2, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
-    else if (beta <= 8) k_ks_inner<8><<<grid2, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
-    else k_ks_inner_generic<<<grid1, 128, 0, st>>>(t, ext, u, key, B, l, L, k, beta);
-    PFT_LAUNCH_CHECK("ks_inner");
+void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const u64* key, int L, int k, int alpha,
+                    cudaStream_t st) {
+    const int beta_max = (L + alpha - 1) / alpha;
+    for (int a = 0; a < B; a += kMaxKs) {
+        const int cnt = B - a < kMaxKs ? B - a : kMaxKs;
+        KsBatch bt;
+        double bytes = 0;
+        int lmax = 0;
+        for (int r = 0; r < kMaxPrimes; r++) bt.need[r] = 0;
+        for (int i = 0; i < cnt; i++) {
+            bt.d[i] = descs[a + i];
+            const int l = descs[a + i].l, E = l + k, beta = (l + alpha - 1) / alpha;
+            bytes += (double)(beta + 2) * E * t.n * 8.0;
+            lmax = max(lmax, l);
+            for (int r = 0; r < L + k; r++)
+                if ((r >= L || r < l) && bt.need[r] < beta) bt.need[r] = (uint8_t)beta;
+        }
+        bytes += 2.0 * ((lmax + alpha - 1) / alpha) * (lmax + k) * t.n * 8.0;  // key rows and digits read
+        dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(L + k));
+        dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(L + k));
+        PFT_PROF("ks_inner", st, bytes);
+        if (beta_max <= 4) k_ks_inner_multi<4><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        else if (beta_max <= 8) k_ks_inner_multi<8><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        else k_ks_inner_multi_generic<<<grid1, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        PFT_LAUNCH_CHECK("ks_inner_multi");
+    }
 }
 
 // ---- rescale broadcast: r = (c_{l-1} + h) mod p, h = floor(p/2), per coefficient; every

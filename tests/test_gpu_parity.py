@@ -249,3 +249,16 @@ def test_ops_bit_exact_n16(p16):
         rt = p16.empty()
         pf.pft_rotate(ctx, ga, 5, rt)
         p16.assert_equal(rt, o.rotate(a, 5), "rotate n16 l=%d" % lvl)
+
+
+def test_batched_import_export_round_trip(p1):
+    o, pf = p1.orc, p1.pft
+    cts = [o.encrypt_sk(o.encode(synth.slots(900 + i, 64), level=lvl), 600 + i) for i, lvl in enumerate([3, 1, 2])]
+    hs = pf.pft_ct_import_batch(p1.ctx, [c.c for c in cts], [c.scale for c in cts])
+    p1.handles += [("ct", h) for h in hs]
+    for c, h in zip(cts, hs):
+        p1.assert_equal(h, c, "import_batch")
+    outs = [np.zeros_like(c.c) for c in cts]
+    pf.pft_ct_export_batch(p1.ctx, hs, outs)
+    for c, arr in zip(cts, outs):
+        assert np.array_equal(arr, c.c)
