@@ -173,8 +173,10 @@ static PolyRef cpoly(u64* data, int l, int n, int pol) { return ref(data + (size
 
 // ---- context construction ---------------------------------------------------------------
 static u64 shoup(u64 w, u64 q) { return (u64)(((unsigned __int128)w << 64) / q); }
-// basis-conversion constants are stored as (c mod 2^30) | (c >> 30) << 32
+// basis-conversion constants are stored in Montgomery form c 2^64 mod t, split as
+// (c' mod 2^30) | (c' >> 30) << 32
 static u64 split30_host(u64 c) { return (c & 0x3fffffffull) | ((c >> 30) << 32); }
+static u64 mont_host(u64 c, u64 t) { return (u64)((((unsigned __int128)c) << 64) % t); }
 static int bitlen(u64 x) { return 64 - __builtin_clzll(x); }
 
 static const int kSecureLogQP[17] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 27, 54, 109, 218, 438, 881, 1772};
@@ -202,6 +204,9 @@ static void build_tables(pft_ctx* c) {
         dp[i].q = q;
         dp[i].mu = (u64)((((unsigned __int128)1) << (64 + s)) / q);
         dp[i].r64 = (u64)((((unsigned __int128)1) << 64) % q);
+        u64 inv = 1;  // q^-1 mod 2^64 by Newton iteration (q odd)
+        for (int it = 0; it < 6; it++) inv *= 2 - q * inv;
+        dp[i].mneg = 0 - inv;
         dp[i].s = (u32)s;
         dp[i].pad = 0;
     }
@@ -260,7 +265,7 @@ static void build_tables(pft_ctx* c) {
         c->pmodq_consts.push_back(tab_upload(c, v));
     }
     // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [targets][ns] qhat mod target
-    // (30-bit split), targets = rows 0..l+k-1 outside the digit, in order
+    // (Montgomery form, 30-bit split), targets = rows 0..l+k-1 outside the digit, in order
     c->modup_tab.assign((size_t)L * c->beta_max, nullptr);
     for (int l = 1; l <= L; l++) {
         const int beta = (l + c->alpha - 1) / c->alpha, E = l + k;
@@ -283,14 +288,15 @@ static void build_tables(pft_ctx* c) {
                     u64 hm = 1;
                     for (int i2 = 0; i2 < ns; i2++)
                         if (i2 != i) hm = mulmod_host(hm, c->primes[lo + i2] % t, t);
-                    tab[2 * ns + (size_t)mi * ns + i] = split30_host(hm);
+                    tab[2 * ns + (size_t)mi * ns + i] = split30_host(mont_host(hm, t));
                     mi++;
                 }
             }
             c->modup_tab[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
         }
     }
-    // ModDown tables per level: [k]{phat_inv, shoup}, then [l][k] phat mod q_m (30-bit split)
+    // ModDown tables per level: [k]{phat_inv, shoup}, then [l][k] phat mod q_m (Montgomery form,
+    // 30-bit split)
     c->moddown_tab.assign(L, nullptr);
     for (int l = 1; l <= L; l++) {
         std::vector<u64> tab(2 * k + (size_t)k * l);
@@ -307,7 +313,7 @@ static void build_tables(pft_ctx* c) {
                 u64 hm = 1;
                 for (int i2 = 0; i2 < k; i2++)
                     if (i2 != i) hm = mulmod_host(hm, c->primes[L + i2] % t, t);
-                tab[2 * k + (size_t)m * k + i] = split30_host(hm);
+                tab[2 * k + (size_t)m * k + i] = split30_host(mont_host(hm, t));
             }
         }
         c->moddown_tab[l - 1] = tab_upload(c, tab);

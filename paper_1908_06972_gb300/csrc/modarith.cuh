@@ -95,11 +95,21 @@ __device__ __forceinline__ u64 addmod(u64 a, u64 b, u64 q) {
 }
 __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
+// Montgomery reduction with R = 2^64: for x = hi 2^64 + lo < q 2^63, returns x 2^-64 mod q
+// in [0, q).  m = lo (-q^-1) makes lo + m q = 0 mod 2^64 (carry out iff lo != 0), and
+// (x + m q) / 2^64 < 1.5 q.
+__device__ __forceinline__ u64 mont_reduce(u64 hi, u64 lo, u64 q, u64 mneg) {
+    const u64 m = lo * mneg;
+    u64 r = hi + mulhi(m, q) + (lo != 0 ? 1 : 0);
+    return r >= q ? r - q : r;
+}
+
 __device__ __forceinline__ DPrime load_prime(const DPrime* tab, int i) {
     DPrime p;
     p.q = __ldg(&tab[i].q);
     p.mu = __ldg(&tab[i].mu);
     p.r64 = __ldg(&tab[i].r64);
+    p.mneg = __ldg(&tab[i].mneg);
     p.s = __ldg(&tab[i].s);
     return p;
 }

@@ -27,10 +27,13 @@ namespace cg = cooperative_groups;
 namespace pft {
 
 // ---- butterflies ---------------------------------------------------------------------------
+// Shoup product x W mod q in [0, 2q), formed as x w + hq (-q) (mod 2^64) so that the
+// subtraction folds into the multiply-adds; nq = -q mod 2^64.
+__device__ __forceinline__ u64 shoup_nq(u64 x, ulonglong2 W, u64 nq) { return x * W.x + mulhi(x, W.y) * nq; }
 // Cooley-Tukey (Harvey): X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q)
 __device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
     if (X >= q2) X -= q2;
-    const u64 T = mul_shoup_lazy(Y, W.x, W.y, q);
+    const u64 T = shoup_nq(Y, W, 0 - q);
     Y = X - T + q2;
     X = X + T;
 }
@@ -40,7 +43,7 @@ __device__ __forceinline__ void gs_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64
     if (S >= q2) S -= q2;
     const u64 D = X - Y + q2;
     X = S;
-    Y = mul_shoup_lazy(D, W.x, W.y, q);
+    Y = shoup_nq(D, W, 0 - q);
 }
 __device__ __forceinline__ u64 canon4(u64 v, u64 q, u64 q2) {
     if (v >= q2) v -= q2;

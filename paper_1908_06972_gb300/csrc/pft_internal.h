@@ -27,7 +27,8 @@ constexpr int kMaxBconv = 96;    // basis-conversion jobs per launch (by-value p
 struct DPrime {
     u64 q;
     u64 mu;
-    u64 r64;  // 2^64 mod q
+    u64 r64;   // 2^64 mod q
+    u64 mneg;  // -q^-1 mod 2^64 (Montgomery reduction)
     u32 s;
     u32 pad;
 };

@@ -220,10 +220,10 @@ void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g,
 // ---- fast basis conversion (ModUp of one digit, or ModDown from the special primes) ------
 // For each coefficient: y_i = x_i * qhat_i^-1 mod s_i (Shoup), then for every target row m
 // (rows [0, nrows) except [skip_lo, skip_hi), enumerated in order as targets 0..nt-1):
-//   out_m = sum_i y_i * (qhat_i mod t_m) mod t_m   (128-bit sum, one Barrett reduction).
+//   out_m = sum_i y_i * (qhat_i mod t_m) mod t_m   (128-bit sum, one Montgomery reduction).
 // Target prime of row m: m < split ? m : base2 + m - split.  Table: [ns] {inv, inv_shoup},
-// then [nt][ns] qhat_i mod t_m (target-major, each split into 30-bit halves: low word =
-// c mod 2^30, high word = c >> 30).  NS (the number of source primes) is a
+// then [nt][ns] qhat_i 2^64 mod t_m (Montgomery form, target-major, each split into 30-bit
+// halves: low word = c mod 2^30, high word = c >> 30).  NS (the number of source primes) is a
 // compile-time constant; each thread converts two adjacent coefficients for two targets at
 // a time (four independent accumulation chains).
 template <int NS>
@@ -263,22 +263,26 @@ __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
             acc3_mac(a1, ya0[i], ya1[i], c1.x, c1.y);
             acc3_mac(b1, yb0[i], yb1[i], c1.x, c1.y);
         }
+        // constants are c 2^64 mod t, so a Montgomery reduction of the sum (< t 2^63) gives
+        // sum y_i c_i mod t
         {
             const int m = m0 < J.skip_lo ? m0 : m0 + gap;
-            const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
+            const int tp = m < J.split ? m : J.base2 + m - J.split;
+            const u64 q = __ldg(&t.primes[tp].q), mneg = __ldg(&t.primes[tp].mneg);
             const U128 va = acc3_value(a0), vb = acc3_value(b0);
             ulonglong2 r;
-            r.x = barrett_reduce(va.hi, va.lo, P);
-            r.y = barrett_reduce(vb.hi, vb.lo, P);
+            r.x = mont_reduce(va.hi, va.lo, q, mneg);
+            r.y = mont_reduce(vb.hi, vb.lo, q, mneg);
             *reinterpret_cast<ulonglong2*>(J.dst + ((size_t)m << logn) + 2 * (size_t)x2) = r;
         }
         if (m0 + 1 < nt) {
             const int m = m1i < J.skip_lo ? m1i : m1i + gap;
-            const DPrime P = load_prime(t.primes, m < J.split ? m : J.base2 + m - J.split);
+            const int tp = m < J.split ? m : J.base2 + m - J.split;
+            const u64 q = __ldg(&t.primes[tp].q), mneg = __ldg(&t.primes[tp].mneg);
             const U128 va = acc3_value(a1), vb = acc3_value(b1);
             ulonglong2 r;
-            r.x = barrett_reduce(va.hi, va.lo, P);
-            r.y = barrett_reduce(vb.hi, vb.lo, P);
+            r.x = mont_reduce(va.hi, va.lo, q, mneg);
+            r.y = mont_reduce(vb.hi, vb.lo, q, mneg);
             *reinterpret_cast<ulonglong2*>(J.dst + ((size_t)m << logn) + 2 * (size_t)x2) = r;
         }
     }
