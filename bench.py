@@ -53,6 +53,24 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x, device):
+    """Maximum of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(units_per_rank, world, max_seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time.
+    Ranks work on independent batches (weak scaling, no data-path collective)."""
+    return units_per_rank * world / max_seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -159,13 +177,7 @@ def run_gpu(args):
             fn()
         e1.record()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reduce_max(e0.elapsed_time(e1), "cuda")
 
     for _ in range(args.warmup):
         step_batched(A, B, C)
@@ -175,14 +187,14 @@ def run_gpu(args):
         ms = timed(lambda: step_batched(A, B, C), args.steps)
     k_ms, k_launches, all_launches, k_work = pft.pft_prof_stop()
     ms_step = ms / args.steps
-    value = BATCH * world * args.steps / (ms / 1e3)
+    value = throughput(BATCH * args.steps, world, ms / 1e3)
 
     # plain one-op-per-launch path (same GPU, same inputs)
     plain = None
     if args.plain_steps > 0:
         step_plain(A, B, C)
         pm = timed(lambda: step_plain(A, B, C), args.plain_steps)
-        plain = BATCH * world * args.plain_steps / (pm / 1e3)
+        plain = throughput(BATCH * args.plain_steps, world, pm / 1e3)
 
     # end to end through the C ABI from pinned host buffers
     host_in = []
@@ -209,8 +221,8 @@ def run_gpu(args):
     for _ in range(args.steps):
         step_e2e()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e = BATCH * world * args.steps / e2e_s
+    e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
+    e2e = throughput(BATCH * args.steps, world, e2e_s)
 
     # roofline of the timed kernel family
     roof = None
