@@ -189,6 +189,12 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = throughput(BATCH * args.steps, world, ms / 1e3)
 
+    # the same step captured once as a CUDA graph and replayed (separate context: graph capture
+    # needs the stream-ordered default allocator and a non-default stream)
+    graph_value = None
+    if args.graph:
+        graph_value = graph_measure(pft, torch, synth, args.steps, args.warmup, rank, world)
+
     # plain one-op-per-launch path (same GPU, same inputs)
     plain = None
     if args.plain_steps > 0:
@@ -259,6 +265,7 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (%.1f GB of ciphertexts)" % (h2d / 1e9),
                       "parallelism": "replicas" if world > 1 else "single"},
            "plain_value": round(plain, 3) if plain else None,
+           "graph_value": round(graph_value, 3) if graph_value else None,
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": int(all_launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
@@ -271,6 +278,50 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def graph_measure(pft, torch, synth, steps, warmup, rank, world):
+    stream = torch.cuda.Stream()
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED, allocator=None,
+                             stream=stream.cuda_stream)
+    pft.pft_keygen(ctx, STEPS_ROT, True)
+    A, B = [], []
+    for i, l in enumerate(levels()):
+        pa = pft.pft_encode(ctx, synth.slots(1000 + i + 7919 * rank, 256), SCALE, l)
+        pb = pft.pft_encode(ctx, synth.slots(5000 + i + 7919 * rank, 256), SCALE, l)
+        A.append(pft.pft_encrypt(ctx, pa, pft.PFT_ENC_SK, 2 * i))
+        B.append(pft.pft_encrypt(ctx, pb, pft.PFT_ENC_SK, 2 * i + 1))
+        pft.pft_pt_destroy(pa)
+        pft.pft_pt_destroy(pb)
+    C = [pft.pft_ct_create(ctx) for _ in range(BATCH)]
+
+    def step():
+        pft.pft_mul_relin_batch(ctx, A, B, C)
+        for s in STEPS_ROT:
+            pft.pft_rotate_batch(ctx, C, s, C)
+
+    step()
+    pft.pft_graph_begin(ctx)
+    step()
+    g = pft.pft_graph_end(ctx)
+    for _ in range(warmup):
+        pft.pft_graph_launch(ctx, g)
+    stream.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        pft.pft_graph_launch(ctx, g)
+    e1.record(stream)
+    stream.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1), "cuda")
+    pft.pft_graph_destroy(g)
+    for h in A + B + C:
+        pft.pft_ct_destroy(h)
+    pft.pft_ctx_destroy(ctx)
+    return throughput(BATCH * steps, world, ms / 1e3)
 
 
 # ---- encrypted fastText inference (Sec. 3.1, Fig. 3) ------------------------------------------------
@@ -501,6 +552,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
     ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
+    ap.add_argument("--graph", type=int, default=1, help="also measure the step as one CUDA-graph launch")
     args = ap.parse_args()
     if args.case == "ntt":
         run_case_ntt(args)

@@ -228,6 +228,23 @@ int pft_mul_relin_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_ct* cons
 int pft_rescale_batch(pft_ctx* ctx, const pft_ct* const* a, int B, pft_ct* const* out);
 int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out);
 
+/* ---- CUDA graphs of batched operations ------------------------------------
+ * pft_graph_begin starts capturing the work the following calls queue on the context
+ * stream; pft_graph_end instantiates it; pft_graph_launch replays it on the context stream
+ * (a whole batched step becomes one graph launch).  Requirements: a non-default context
+ * stream and the default (stream-ordered, capturable) allocator -- a context created with a
+ * custom allocator returns PFT_ERR_ARG.  Replaying is valid for calls whose output handles
+ * already hold buffers of the right size and keep them (HADD, HMULPLAIN, mul_relin, rotate
+ * and their batched forms, after one eager warm-up call); calls that copy host data
+ * (import/export, encode/decode, encryption, the fastText entry points) or replace output
+ * buffers (rescale) are not capturable.  Keep the captured handles alive while the graph is
+ * used. */
+typedef struct pft_graph pft_graph;
+int pft_graph_begin(pft_ctx* ctx);
+int pft_graph_end(pft_ctx* ctx, pft_graph** out);
+int pft_graph_launch(pft_ctx* ctx, const pft_graph* graph);
+int pft_graph_destroy(pft_graph* graph);
+
 /* ---- rescale without allocation --------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot obtain
  * device memory at the moment they call the library -- for example an application whose

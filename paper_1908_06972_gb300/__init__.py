@@ -87,6 +87,8 @@ def lib():
             "pft_rotate_batch": [vp, pp, i, c_int32, pp],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
+            "pft_graph_begin": [vp], "pft_graph_end": [vp, pp], "pft_graph_launch": [vp, vp],
+            "pft_graph_destroy": [vp],
             "pft_ft_model_create": [vp, POINTER(c_double), POINTER(c_double), i, i, i, i, pp],
             "pft_ft_model_import": [vp, pp, pp, i, i, i, pp], "pft_ft_model_destroy": [vp],
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
@@ -117,7 +119,8 @@ def exported_symbols():
             "pft_rotate_batch", "pft_ntt", "pft_ft_model_create", "pft_ft_model_import",
             "pft_ft_model_destroy", "pft_fasttext_infer", "pft_fasttext_infer_batch",
             "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc",
-            "pft_ct_import_batch", "pft_ct_export_batch"]
+            "pft_ct_import_batch", "pft_ct_export_batch", "pft_graph_begin", "pft_graph_end",
+            "pft_graph_launch", "pft_graph_destroy"]
 
 
 def _check(rc, ctx=None):
@@ -421,6 +424,24 @@ def pft_rescale_noalloc(ctx, in_ptr, level, out_ptr):
     for callers that cannot allocate device memory when they call the library.  The library
     uses a fixed 32 MiB array as working space (shared by all calls on a device)."""
     _op("pft_rescale_noalloc", ctx, c_void_p(in_ptr), level, c_void_p(out_ptr))
+
+
+def pft_graph_begin(ctx):
+    _check(lib().pft_graph_begin(ctx), ctx)
+
+
+def pft_graph_end(ctx):
+    out = c_void_p()
+    _check(lib().pft_graph_end(ctx, ctypes.byref(out)), ctx)
+    return out
+
+
+def pft_graph_launch(ctx, graph):
+    _check(lib().pft_graph_launch(ctx, graph), ctx)
+
+
+def pft_graph_destroy(graph):
+    _check(lib().pft_graph_destroy(graph))
 
 
 def pft_ft_model_create(ctx, H, O, level):

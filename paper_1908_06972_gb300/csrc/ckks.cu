@@ -54,6 +54,10 @@ struct pft_pt {
     int level = 0;
     double scale = 1.0;
 };
+struct pft_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 struct pft_ft_model {
     pft_ctx* ctx = nullptr;
     int m = 0, n = 0, c = 0, chunks = 0, level = 0;
@@ -1471,6 +1475,40 @@ int pft_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pf
         NEED(c && a && out && B >= 0, PFT_ERR_ARG, "bad arguments");
         op_rotate_batch(c, a, B, step, out);
     });
+}
+
+int pft_graph_begin(pft_ctx* c) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "null context");
+        NEED(c->stream != nullptr, PFT_ERR_ARG, "graph capture needs a non-default context stream");
+        NEED(!c->has_alloc, PFT_ERR_ARG, "graph capture needs the stream-ordered default allocator");
+        PFT_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    });
+}
+
+int pft_graph_end(pft_ctx* c, pft_graph** out) {
+    return guard(c, [&] {
+        NEED(c && out, PFT_ERR_ARG, "bad arguments");
+        std::unique_ptr<pft_graph> g(new pft_graph());
+        PFT_CUDA(cudaStreamEndCapture(c->stream, &g->graph));
+        PFT_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+        *out = g.release();
+    });
+}
+
+int pft_graph_launch(pft_ctx* c, const pft_graph* g) {
+    return guard(c, [&] {
+        NEED(c && g && g->exec, PFT_ERR_ARG, "bad arguments");
+        PFT_CUDA(cudaGraphLaunch(g->exec, c->stream));
+    });
+}
+
+int pft_graph_destroy(pft_graph* g) {
+    if (!g) return PFT_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return PFT_OK;
 }
 
 int pft_rescale_noalloc(pft_ctx* c, const uint64_t* in, int level, uint64_t* out) {

@@ -262,3 +262,44 @@ def test_batched_import_export_round_trip(p1):
     pf.pft_ct_export_batch(p1.ctx, hs, outs)
     for c, arr in zip(cts, outs):
         assert np.array_equal(arr, c.c)
+
+
+def test_graph_replay_matches_oracle(gpu):
+    """A captured batched step (mul_relin then rotate) replayed twice equals the oracle."""
+    import torch
+    from oracle import ckks as K
+
+    pf = gpu
+    stream = torch.cuda.Stream()
+    seed = (0x5EED, 11, 22, 33)
+    orc = K.Oracle(12, 3, 1, 1, 60, 40, 60, 2.0 ** 40, seed)
+    orc.keygen([1], True)
+    ctx = pf.pft_ctx_create(12, 3, 1, 1, 60, 40, 60, 2.0 ** 40, seed, flags=pf.PFT_ALLOW_INSECURE, allocator=None,
+                            stream=stream.cuda_stream)
+    graph = None
+    hs = []
+    try:
+        pf.pft_keygen(ctx, [1], True)
+        A = [orc.encrypt_sk(orc.encode(synth.slots(70 + i, 64), level=lvl), 80 + i) for i, lvl in enumerate([3, 2])]
+        B = [orc.encrypt_sk(orc.encode(synth.slots(90 + i, 64), level=lvl), 95 + i) for i, lvl in enumerate([3, 2])]
+        gA = [pf.pft_ct_import(ctx, x.c, x.scale) for x in A]
+        gB = [pf.pft_ct_import(ctx, x.c, x.scale) for x in B]
+        C = [pf.pft_ct_create(ctx) for _ in A]
+        hs = gA + gB + C
+        pf.pft_mul_relin_batch(ctx, gA, gB, C)  # eager warm-up sizes the outputs
+        pf.pft_rotate_batch(ctx, C, 1, C)
+        pf.pft_graph_begin(ctx)
+        pf.pft_mul_relin_batch(ctx, gA, gB, C)
+        pf.pft_rotate_batch(ctx, C, 1, C)
+        graph = pf.pft_graph_end(ctx)
+        want = [orc.rotate(orc.mul_relin(a, b), 1) for a, b in zip(A, B)]
+        for _ in range(2):
+            pf.pft_graph_launch(ctx, graph)
+            for h, w in zip(C, want):
+                assert np.array_equal(pf.pft_ct_export(ctx, h), w.c)
+    finally:
+        if graph is not None:
+            pf.pft_graph_destroy(graph)
+        for h in hs:
+            pf.pft_ct_destroy(h)
+        pf.pft_ctx_destroy(ctx)
