@@ -139,6 +139,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     pft.build()
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    tuned, tune_us = pft.pft_autotune(ctx)
     pft.pft_keygen(ctx, STEPS_ROT, True)
     lv = levels()
     n = 1 << LOGN
@@ -268,7 +269,9 @@ def run_gpu(args):
            "graph_value": round(graph_value, 3) if graph_value else None,
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
-           "gpu_launches": int(all_launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+           "gpu_launches": int(all_launches), "roofline": roof,
+           "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
+                        "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
            "fasttext": ft}
     if rank == 0:
         print(json.dumps(out))

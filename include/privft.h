@@ -228,6 +228,17 @@ int pft_mul_relin_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_ct* cons
 int pft_rescale_batch(pft_ctx* ctx, const pft_ct* const* a, int B, pft_ct* const* out);
 int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out);
 
+/* ---- autotuning -----------------------------------------------------------
+ * Times every N = 2^16 transform variant of the library (two-pass with 3 or 4 resident CTAs
+ * per SM, one-launch 8-CTA cluster, generic staged passes) on a forward + inverse transform
+ * of 2 x 32 limbs and keeps the fastest for this context.  us_out (may be NULL) receives up to
+ * `cap` per-variant times in microseconds, chosen the selected index.  Other ring degrees
+ * have a single variant.  The environment variable PFT_NTT16 (twopass, twopass4, cluster,
+ * generic) overrides the choice. */
+int pft_autotune(pft_ctx* ctx, double* us_out, int cap, int* chosen);
+/* Pin the N = 2^16 transform variant (0..3 in the order above) without timing. */
+int pft_set_transform_variant(pft_ctx* ctx, int variant);
+
 /* ---- CUDA graphs of batched operations ------------------------------------
  * pft_graph_begin starts capturing the work the following calls queue on the context
  * stream; pft_graph_end instantiates it; pft_graph_launch replays it on the context stream

@@ -89,6 +89,7 @@ def lib():
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
             "pft_graph_begin": [vp], "pft_graph_end": [vp, pp], "pft_graph_launch": [vp, vp],
             "pft_graph_destroy": [vp],
+            "pft_autotune": [vp, POINTER(c_double), i, ip], "pft_set_transform_variant": [vp, i],
             "pft_ft_model_create": [vp, POINTER(c_double), POINTER(c_double), i, i, i, i, pp],
             "pft_ft_model_import": [vp, pp, pp, i, i, i, pp], "pft_ft_model_destroy": [vp],
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
@@ -120,7 +121,7 @@ def exported_symbols():
             "pft_ft_model_destroy", "pft_fasttext_infer", "pft_fasttext_infer_batch",
             "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc",
             "pft_ct_import_batch", "pft_ct_export_batch", "pft_graph_begin", "pft_graph_end",
-            "pft_graph_launch", "pft_graph_destroy"]
+            "pft_graph_launch", "pft_graph_destroy", "pft_autotune", "pft_set_transform_variant"]
 
 
 def _check(rc, ctx=None):
@@ -424,6 +425,18 @@ def pft_rescale_noalloc(ctx, in_ptr, level, out_ptr):
     for callers that cannot allocate device memory when they call the library.  The library
     uses a fixed 32 MiB array as working space (shared by all calls on a device)."""
     _op("pft_rescale_noalloc", ctx, c_void_p(in_ptr), level, c_void_p(out_ptr))
+
+
+def pft_autotune(ctx):
+    """Times the transform variants, keeps the fastest; returns (chosen index, times in us)."""
+    us = (c_double * 8)()
+    chosen = c_int()
+    _check(lib().pft_autotune(ctx, us, 8, ctypes.byref(chosen)), ctx)
+    return chosen.value, [us[i] for i in range(8)]
+
+
+def pft_set_transform_variant(ctx, variant):
+    _check(lib().pft_set_transform_variant(ctx, variant), ctx)
 
 
 def pft_graph_begin(ctx):

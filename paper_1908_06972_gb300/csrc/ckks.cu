@@ -1477,6 +1477,58 @@ int pft_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pf
     });
 }
 
+int pft_autotune(pft_ctx* c, double* us_out, int cap, int* chosen) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "null context");
+        const int nv = c->logn == 16 ? kNttVariants : 1;
+        std::vector<double> us(nv, 0.0);
+        if (nv > 1) {
+            // a representative launch: 64 limbs of the chain, forward then inverse, 3 repetitions
+            const int limbs = std::min(c->L + c->k, 32), polys = 2;
+            Scratch buf(c, (size_t)polys * limbs * c->n * 8);
+            PFT_CUDA(cudaMemsetAsync(buf.p, 0, (size_t)polys * limbs * c->n * 8, c->stream));
+            std::vector<PolyRef> r;
+            for (int i = 0; i < polys; i++) r.push_back(ref(buf.u() + (size_t)i * limbs * c->n, limbs));
+            cudaEvent_t e0, e1;
+            PFT_CUDA(cudaEventCreate(&e0));
+            PFT_CUDA(cudaEventCreate(&e1));
+            const int keep = c->tabs.ntt_variant;
+            for (int v = 0; v < nv; v++) {
+                c->tabs.ntt_variant = v;
+                ntt_fwd(c, r, r);  // warm-up (and one-time kernel attributes)
+                ntt_inv(c, r, r);
+                PFT_CUDA(cudaEventRecord(e0, c->stream));
+                for (int rep = 0; rep < 3; rep++) {
+                    ntt_fwd(c, r, r);
+                    ntt_inv(c, r, r);
+                }
+                PFT_CUDA(cudaEventRecord(e1, c->stream));
+                PFT_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                PFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                us[v] = 1e3 * ms / 3;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            int best = 0;
+            for (int v = 1; v < nv; v++)
+                if (us[v] < us[best]) best = v;
+            c->tabs.ntt_variant = best;
+            (void)keep;
+        }
+        if (chosen) *chosen = c->tabs.ntt_variant;
+        if (us_out)
+            for (int v = 0; v < nv && v < cap; v++) us_out[v] = us[v];
+    });
+}
+
+int pft_set_transform_variant(pft_ctx* c, int variant) {
+    return guard(c, [&] {
+        NEED(c && variant >= 0 && variant < kNttVariants, PFT_ERR_ARG, "variant out of range");
+        c->tabs.ntt_variant = variant;
+    });
+}
+
 int pft_graph_begin(pft_ctx* c) {
     return guard(c, [&] {
         NEED(c, PFT_ERR_ARG, "null context");

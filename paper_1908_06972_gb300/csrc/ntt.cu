@@ -342,15 +342,8 @@ static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const 
     }
 }
 
-// Resident CTAs per SM the two-pass kernels are compiled for: 3 (80 registers, default)
-// or 4 (64 registers) with PFT_NTT_MINB=4.
-static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
+static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse, int minb,
                                  cudaStream_t st) {
-    static int minb = 0;
-    if (!minb) {
-        const char* e = getenv("PFT_NTT_MINB");
-        minb = (e && e[0] == '4') ? 4 : 3;
-    }
     if (minb == 4) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
     else launch_ntt16_twopass_v<3>(t, in, out, inverse, st);
 }
@@ -370,32 +363,25 @@ static void launch_ntt16_cluster_v(const DevTables& t, const PolySet& in, const 
     PFT_LAUNCH_CHECK("ntt16 cluster");
 }
 
-// Resident CTAs per SM the cluster kernel is compiled for: 2 (64 registers) by default,
-// 1 (no register cap) with PFT_NTT16_MINB=1.
-static int ntt16_minb() {
-    static int v = 0;
-    if (!v) {
-        const char* e = getenv("PFT_NTT16_MINB");
-        v = (e && e[0] == '1') ? 1 : 2;
-    }
-    return v;
-}
-
 template <bool INV>
 static void launch_ntt16_cluster(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
-    if (ntt16_minb() == 1) launch_ntt16_cluster_v<INV, 1>(t, in, out, st);
-    else launch_ntt16_cluster_v<INV, 2>(t, in, out, st);
+    launch_ntt16_cluster_v<INV, 2>(t, in, out, st);
 }
 
-// N = 2^16 path: the register-direct two-pass kernels (default); PFT_NTT16=cluster selects the
-// one-launch cluster kernel, PFT_NTT16=generic the generic shared-memory-staged passes.
-static int ntt16_path() {
-    static int v = -1;
-    if (v < 0) {
+// N = 2^16 variant: the context's choice (pft_autotune), unless PFT_NTT16 names one
+// (twopass, twopass4, cluster, generic).
+static int ntt16_variant(const DevTables& t) {
+    static int env = -2;
+    if (env == -2) {
         const char* e = getenv("PFT_NTT16");
-        v = (e && strcmp(e, "cluster") == 0) ? 1 : (e && strcmp(e, "generic") == 0) ? 2 : 0;
+        env = !e ? -1
+                 : strcmp(e, "twopass") == 0  ? 0
+                 : strcmp(e, "twopass4") == 0 ? 1
+                 : strcmp(e, "cluster") == 0  ? 2
+                 : strcmp(e, "generic") == 0  ? 3
+                                              : -1;
     }
-    return v;
+    return env >= 0 ? env : t.ntt_variant;
 }
 
 template <int S, int C, bool INV>
@@ -590,9 +576,10 @@ static void run(const DevTables& t, const PolySet& in, const PolySet& out, bool 
         else run_single<false>(t, in, out, st);
         return;
     }
-    if (t.logn == 16 && ntt16_path() == 0) {
-        launch_ntt16_twopass(t, in, out, inverse, st);
-    } else if (t.logn == 16 && ntt16_path() == 1) {
+    const int v16 = t.logn == 16 ? ntt16_variant(t) : -1;
+    if (v16 == 0 || v16 == 1) {
+        launch_ntt16_twopass(t, in, out, inverse, v16 == 1 ? 4 : 3, st);
+    } else if (v16 == 2) {
         if (!inverse) launch_ntt16_cluster<false>(t, in, out, st);
         else launch_ntt16_cluster<true>(t, in, out, st);
     } else if (t.logn == 16) {

@@ -61,7 +61,10 @@ struct DevTables {
     ulonglong2* inv;       // [P][N] (psi^-brv(i), shoup)
     ulonglong2* ninv;      // [P] (N^-1, shoup)
     ulonglong2* inv1ninv;  // [P] (psi^-brv(1) N^-1, shoup)
+    int ntt_variant;       // N = 2^16 transform: 0 two-pass (3 CTAs/SM), 1 two-pass (4 CTAs/SM),
+                           // 2 one-launch cluster, 3 generic staged passes
 };
+constexpr int kNttVariants = 4;
 
 struct Error {
     int code;

@@ -303,3 +303,20 @@ def test_graph_replay_matches_oracle(gpu):
         for h in hs:
             pf.pft_ct_destroy(h)
         pf.pft_ctx_destroy(ctx)
+
+
+def test_every_transform_variant_bit_exact(p16):
+    """pft_autotune picks among the N = 2^16 transform variants; each one gives the same bits."""
+    o, pf, ctx = p16.orc, p16.pft, p16.ctx
+    chosen, us = pf.pft_autotune(ctx)
+    assert 0 <= chosen < 4 and all(u > 0 for u in us[:4])
+    a = o.encrypt_sk(o.encode(synth.slots(31, 512), level=6), 41)
+    b = o.encrypt_sk(o.encode(synth.slots(32, 512), level=6), 42)
+    want = o.mul_relin(a, b)
+    ga, gb = p16.ct(a), p16.ct(b)
+    for v in range(4):
+        pf.pft_set_transform_variant(ctx, v)
+        m = p16.empty()
+        pf.pft_mul_relin(ctx, ga, gb, m)
+        p16.assert_equal(m, want, "mul_relin with transform variant %d" % v)
+    pf.pft_set_transform_variant(ctx, chosen)
