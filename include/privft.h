@@ -220,6 +220,13 @@ int pft_rescale(pft_ctx* ctx, const pft_ct* a, pft_ct* out);
  * key switching with the rotation key of g.  Steps with no key -> PFT_ERR_NO_KEY. */
 int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
 
+/* Rotations of one ciphertext by n steps that share one ModUp of c1 (hoisting): the
+ * extended digits are computed once and permuted by each step's automorphism before the
+ * inner product with that step's key and ModDown.  Fast basis conversion does not commute
+ * exactly with the sign changes of the automorphism, so results equal pft_rotate's in
+ * meaning, up to key-switching noise, not bit for bit.  outs[i] must differ from a. */
+int pft_rotate_hoisted(pft_ctx* ctx, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs);
+
 /* Batched forms: one launch per stage over all B ciphertexts (levels may differ
  * between ciphertexts; pairs must match).  Keys are read once per level group. */
 int pft_add_batch(pft_ctx* ctx, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out);

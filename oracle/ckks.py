@@ -301,6 +301,33 @@ class Oracle:
         q = self._q(ct)
         return Ciphertext(np.stack([C.vadd(r.c[0], k0, q), k1]), ct.scale)
 
+    def rotate_hoisted(self, ct, steps):
+        """Rotations of one ciphertext sharing one ModUp (hoisting): the digits of c1 are
+        extended once, and for each step the automorphism is applied to the extended digits
+        (coefficient rows, mod each row's prime) before the inner product with that step's
+        key and ModDown.  Fast basis conversion does not commute exactly with negating
+        coefficients, so the result differs from rotate() by small noise, not in meaning."""
+        l = ct.level
+        basis = self.q[:l] + self.p
+        rows = list(range(l)) + list(range(self.L, self.L + self.k))
+        q = self._q(ct)
+        beta = -(-l // self.alpha)
+        exts = [self.modup_digit(ct.c[1], j) for j in range(beta)]
+        out = []
+        for step in steps:
+            g = galois_element(step, self.N)
+            K = self.keys[g]
+            u0 = np.zeros((l + self.k, self.N), np.uint64)
+            u1 = np.zeros((l + self.k, self.N), np.uint64)
+            for j in range(beta):
+                e = C.automorph(exts[j], basis, g)
+                u0 = C.vadd(u0, C.polymul(e, K[j, 0][rows], basis), basis)
+                u1 = C.vadd(u1, C.polymul(e, K[j, 1][rows], basis), basis)
+            k0, k1 = self.moddown(u0, l), self.moddown(u1, l)
+            c0 = C.automorph(ct.c[0], q, g)
+            out.append(Ciphertext(np.stack([C.vadd(c0, k0, q), k1]), ct.scale))
+        return out
+
     def rescale(self, ct, rounding=True):
         """Drop q_{l-1}: c'_k = (c_k + h - r) * p^-1 mod q_k, r = (c_{l-1} + h) mod p,
         h = floor(p/2) when rounding (h = 0 reproduces the floor of Eq. 1)."""

@@ -85,6 +85,7 @@ def lib():
             "pft_add_batch": [vp, pp, pp, i, pp], "pft_mul_plain_batch": [vp, pp, pp, i, pp],
             "pft_mul_relin_batch": [vp, pp, pp, i, pp], "pft_rescale_batch": [vp, pp, i, pp],
             "pft_rotate_batch": [vp, pp, i, c_int32, pp],
+            "pft_rotate_hoisted": [vp, vp, POINTER(c_int32), i, pp],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
             "pft_graph_begin": [vp], "pft_graph_end": [vp, pp], "pft_graph_launch": [vp, vp],
@@ -121,7 +122,8 @@ def exported_symbols():
             "pft_ft_model_destroy", "pft_fasttext_infer", "pft_fasttext_infer_batch",
             "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc",
             "pft_ct_import_batch", "pft_ct_export_batch", "pft_graph_begin", "pft_graph_end",
-            "pft_graph_launch", "pft_graph_destroy", "pft_autotune", "pft_set_transform_variant"]
+            "pft_graph_launch", "pft_graph_destroy", "pft_autotune", "pft_set_transform_variant",
+            "pft_rotate_hoisted"]
 
 
 def _check(rc, ctx=None):
@@ -413,6 +415,11 @@ def pft_rescale_batch(ctx, a, out):
 
 def pft_rotate_batch(ctx, a, step, out):
     _op("pft_rotate_batch", ctx, _arr(a), len(a), c_int32(step), _arr(out))
+
+
+def pft_rotate_hoisted(ctx, a, steps, outs):
+    st = (c_int32 * max(1, len(steps)))(*steps)
+    _op("pft_rotate_hoisted", ctx, a, st, len(steps), _arr(outs))
 
 
 def pft_ntt(ctx, data_ptr, n_polys, n_limbs, inverse):

@@ -722,6 +722,109 @@ static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t s
     keyswitch_batch(c, c->keys[g], io);
 }
 
+// Rotations of one ciphertext by several steps sharing one ModUp of c1 (hoisting): the
+// extended digits (evaluation form) are permuted by each step's automorphism, then go through
+// the inner product with that step's key and ModDown; out_i = (aut(c0) + u0', u1').
+static void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs) {
+    check_ct(a);
+    NEED(n >= 0 && (n == 0 || (steps && outs)), PFT_ERR_ARG, "bad arguments");
+    const int l = a->level, k = c->k, L = c->L, alpha = c->alpha, E = l + k, beta = (l + alpha - 1) / alpha;
+    const size_t limb = (size_t)c->n;
+    std::vector<u32> gs(n);
+    for (int i = 0; i < n; i++) {
+        NEED(outs[i] && outs[i] != a, PFT_ERR_ARG, "outputs must be distinct from the input");
+        gs[i] = galois_of(c->n, steps[i]);
+        NEED(gs[i] == 1 || c->keys.count(gs[i]), PFT_ERR_NO_KEY, "no rotation key for step " + std::to_string(steps[i]));
+    }
+    if (n == 0) return;
+    Scratch Dc(c, l * limb * 8), Ext(c, (size_t)beta * E * limb * 8), ExtG(c, (size_t)beta * E * limb * 8),
+        U(c, 2 * (size_t)E * limb * 8), Cv(c, 2 * (size_t)l * limb * 8), A0(c, l * limb * 8);
+    u64* c1 = a->data + (size_t)l * limb;
+    auto ext = [&](u64* base, int j) { return base + (size_t)j * E * limb; };
+    // ModUp of c1, once
+    {
+        std::vector<PolyRef> in{ref(c1, l)}, out{ref(Dc.u(), l)};
+        ntt_inv(c, in, out);
+        std::vector<BconvJob> jobs;
+        std::vector<PolyRef> cin, cout, rows;
+        for (int j = 0; j < beta; j++) {
+            const int lo = j * alpha, hi = std::min(l, lo + alpha);
+            BconvJob J;
+            J.src = Dc.u() + (size_t)lo * limb;
+            J.dst = ext(Ext.u(), j);
+            J.table = c->modup_tab[(size_t)(l - 1) * c->beta_max + j];
+            J.ns = hi - lo;
+            J.src_p0 = lo;
+            J.nrows = E;
+            J.skip_lo = lo;
+            J.skip_hi = hi;
+            J.split = l;
+            J.base2 = L;
+            J.pad = 0;
+            jobs.push_back(J);
+            cin.push_back(ref(c1 + (size_t)lo * limb, hi - lo, lo));
+            cout.push_back(ref(ext(Ext.u(), j) + (size_t)lo * limb, hi - lo, lo));
+            if (lo > 0) rows.push_back(ref(ext(Ext.u(), j), lo, 0));
+            rows.push_back(ref(ext(Ext.u(), j) + (size_t)hi * limb, E - hi, hi, l - hi, L));
+        }
+        bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
+        ew(c, EwOp::Copy, cin, {}, cout);
+        ntt_fwd(c, rows, rows);
+    }
+    for (int i = 0; i < n; i++) {
+        pft_ct* o = outs[i];
+        const double sc = a->scale;
+        ensure_ct(c, o, l);
+        o->scale = sc;
+        if (gs[i] == 1) {
+            PFT_CUDA(cudaMemcpyAsync(o->data, a->data, 2 * l * limb * 8, cudaMemcpyDeviceToDevice, c->stream));
+            continue;
+        }
+        // automorphism of the extended digits and of c0
+        std::vector<PolyRef> ein, eout;
+        for (int j = 0; j < beta; j++) {
+            ein.push_back(ref(ext(Ext.u(), j), E, 0, l, L));
+            eout.push_back(ref(ext(ExtG.u(), j), E, 0, l, L));
+        }
+        ein.push_back(ref(a->data, l));
+        eout.push_back(ref(A0.u(), l));
+        chunks(eout.size(), [&](size_t x, size_t y) {
+            automorph(c->tabs, mkset(ein, x, y), mkset(eout, x, y), gs[i], c->stream);
+        });
+        KsDesc d{ExtG.u(), U.u(), l, 0};
+        ks_inner_multi(c->tabs, &d, 1, c->keys[gs[i]], L, k, alpha, c->stream);
+        // ModDown
+        std::vector<PolyRef> sp, cvr;
+        std::vector<BconvJob> jobs;
+        for (int pol = 0; pol < 2; pol++) {
+            u64* up = U.u() + (size_t)pol * E * limb;
+            sp.push_back(ref(up + (size_t)l * limb, k, 0, 0, L));
+            cvr.push_back(ref(Cv.u() + (size_t)pol * l * limb, l));
+            BconvJob J;
+            J.src = up + (size_t)l * limb;
+            J.dst = Cv.u() + (size_t)pol * l * limb;
+            J.table = c->moddown_tab[l - 1];
+            J.ns = k;
+            J.src_p0 = L;
+            J.nrows = l;
+            J.skip_lo = 0;
+            J.skip_hi = 0;
+            J.split = l;
+            J.base2 = L;
+            J.pad = 0;
+            jobs.push_back(J);
+        }
+        ntt_inv(c, sp, sp);
+        bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
+        ntt_fwd(c, cvr, cvr);
+        std::vector<PolyRef> x0{ref(U.u(), l)}, y0{ref(Cv.u(), l)}, a0{ref(A0.u(), l)}, o0{ref(o->data, l)};
+        std::vector<PolyRef> x1{ref(U.u() + (size_t)E * limb, l)}, y1{ref(Cv.u() + (size_t)l * limb, l)},
+            o1{ref(o->data + (size_t)l * limb, l)};
+        subscale(c, x0, &y0, &a0, o0, c->moddown_consts);
+        subscale(c, x1, &y1, nullptr, o1, c->moddown_consts);
+    }
+}
+
 static void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
         check_ct(a[i]);
@@ -1445,6 +1548,9 @@ int pft_rescale(pft_ctx* c, const pft_ct* a, pft_ct* out) {
 }
 int pft_rotate(pft_ctx* c, const pft_ct* a, int32_t step, pft_ct* out) {
     return guard(c, [&] { op_rotate_batch(c, &a, 1, step, &out); });
+}
+int pft_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs) {
+    return guard(c, [&] { op_rotate_hoisted(c, a, steps, n, outs); });
 }
 int pft_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out) {
     return guard(c, [&] {

@@ -320,3 +320,17 @@ def test_every_transform_variant_bit_exact(p16):
         pf.pft_mul_relin(ctx, ga, gb, m)
         p16.assert_equal(m, want, "mul_relin with transform variant %d" % v)
     pf.pft_set_transform_variant(ctx, chosen)
+
+
+@pytest.mark.parametrize("which", ["p1", "p16"])
+def test_hoisted_rotations_bit_exact(which, request):
+    p = request.getfixturevalue(which)
+    o, pf, ctx = p.orc, p.pft, p.ctx
+    steps = [1, -1] if which == "p16" else [1, 2, -1, 3, 1024]
+    lvl = o.L if which == "p1" else 5
+    a = o.encrypt_sk(o.encode(synth.slots(55, 256), level=lvl), 56)
+    ga = p.ct(a)
+    outs = [p.empty() for _ in steps]
+    pf.pft_rotate_hoisted(ctx, ga, steps, outs)
+    for h, w, st in zip(outs, o.rotate_hoisted(a, steps), steps):
+        p.assert_equal(h, w, "hoisted rotate %d" % st)

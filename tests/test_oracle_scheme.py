@@ -211,3 +211,18 @@ def test_fasttext_single_token_and_encrypted_sequence(small):
     assert S.level == l - 2
     got = orc.decode(orc.decrypt(S))[:c].real
     assert np.max(np.abs(got - fasttext.plain_scores(v, H, O))) < 2 ** -20
+
+
+def test_hoisted_rotations_meaning_and_noise(small):
+    """Hoisted rotations decrypt to the rotated slots and differ from plain rotations only
+    by key-switching noise (bounded like the key switch itself)."""
+    orc = small
+    z = _z(orc.N // 2)
+    ct = orc.encrypt_sk(orc.encode(z), 33)
+    steps = [1, 2, -1, 3]
+    hs = orc.rotate_hoisted(ct, steps)
+    for step, h in zip(steps, hs):
+        assert np.max(np.abs(orc.decode(orc.decrypt(h)) - np.roll(z, -step))) < 2 ** -20
+        plain = orc.rotate(ct, step)
+        d = C.vsub(orc.decrypt(h).m, orc.decrypt(plain).m, orc.q)
+        assert max(abs(int(v)) for v in ckks.crt_centered(d, orc.q)) <= 2 * _ks_bound(orc, orc.L)
