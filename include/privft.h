@@ -300,6 +300,19 @@ int pft_ft_model_create(pft_ctx* ctx, const double* H, const double* O, int m, i
 int pft_ft_model_import(pft_ctx* ctx, const pft_pt* const* H_pts, const pft_pt* const* O_pts, int m, int n,
                         int c, pft_ft_model** out);
 int pft_ft_model_destroy(pft_ft_model* model);
+/* Rotation-light variant (not in the paper): diagonal packing D_k[i] = H[(i+k) mod t, i mod n]
+ * (k < n, at `level`) and P[n c' + j] = O[j, c'] (one plaintext, level-1).  Inference computes
+ * Q = sum_k rot(v, k) D_k with n-1 hoisted rotations, Q += rot(Q, n 2^s) while n 2^s < t,
+ * rescale, S = Q P, S += rot(S, 2^s) while 2^s < n, rescale: n - 1 + log2(t/n) + log2(n)
+ * rotations (78 for n = 64, t = 32768) instead of n log2(t) (960), n - 1 of them sharing one
+ * ModUp.  Needs m <= t, n a power of two dividing t, n c <= t, rotation keys for 1..n-1 and
+ * n 2^s.  Scores land in slots n c' (c' < c), not 0..c-1.  The input is rotated before its
+ * plaintext product, so key-switching noise is relative to the input's scale: encrypt v at a
+ * scale of 2^50 or more (instead of 2^40) to keep the scores within 2^-20. */
+int pft_ft_model_create_diag(pft_ctx* ctx, const double* H, const double* O, int m, int n, int c, int level,
+                             pft_ft_model** out);
+int pft_ft_model_import_diag(pft_ctx* ctx, const pft_pt* const* D_pts, const pft_pt* P_pt, int m, int n, int c,
+                             pft_ft_model** out);
 /* Scores of one document: v = ceil(m/t) ciphertexts at the model level (the
  * client's count vector, already divided by w).  Sequence: h_j = TotalSum(sum_i
  * v_i * H_{j,i}) with TotalSum rotating by 2^i, i = 0..log2(t)-1 (Algorithm 2),

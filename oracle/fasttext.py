@@ -65,3 +65,51 @@ def column_total_sum(orc, v_cts, H_pts_j):
     for i in range(1, len(v_cts)):
         t = orc.add(t, orc.mul_plain(v_cts[i], H_pts_j[i]))
     return orc.rescale(orc.total_sum(t))
+
+
+# ---- rotation-light variant (diagonal packing; not in the paper) -----------------------------
+# h_j = sum_u v_u H[u, j] for n columns (n a power of two dividing t, m <= t):
+#   Q = sum_{k<n} rot(v, k) * D_k,  D_k[i] = H[(i + k) mod t, i mod n]   (hoisted rotations)
+#   Q[i] = sum_k v[i+k] H[i+k, i mod n]; summing Q over the slots i + n r (r < t/n) -- a
+#   rotate-and-sum with steps n 2^s -- gives h_{i mod n} in every slot i.
+# Output layer: S = Q * P with P[n c + j] = O[j, c]; a rotate-and-sum with steps 2^s, s < log2 n,
+# leaves s_c = sum_j h_j O[j, c] in slot n c.
+
+def pack_diag(H, O, t):
+    """Slot vectors of the diagonal packing: D [n][t] and P [t]."""
+    m, n = H.shape
+    c = O.shape[1]
+    Hp = np.zeros((t, n))
+    Hp[:m] = H
+    i = np.arange(t)
+    D = np.stack([Hp[(i + k) % t, i % n] for k in range(n)])
+    P = np.zeros(t)
+    for cc in range(c):
+        P[n * cc: n * cc + n] = O[:, cc]
+    return D, P
+
+
+def diag_score_slots(n, c):
+    """Slots holding the c scores in the diagonal variant."""
+    return [n * cc for cc in range(c)]
+
+
+def encrypted_scores_diag(orc, v_ct, D_pts, P_pt):
+    """The rotation-light sequence on the oracle (one input ciphertext, m <= t)."""
+    n = len(D_pts)
+    t = orc.N // 2
+    R = [v_ct] + orc.rotate_hoisted(v_ct, list(range(1, n)))
+    Q = orc.mul_plain(R[0], D_pts[0])
+    for k in range(1, n):
+        Q = orc.add(Q, orc.mul_plain(R[k], D_pts[k]))
+    s = n
+    while s < t:
+        Q = orc.add(Q, orc.rotate(Q, s))
+        s *= 2
+    Q = orc.rescale(Q)
+    S = orc.mul_plain(Q, P_pt)
+    s = 1
+    while s < n:
+        S = orc.add(S, orc.rotate(S, s))
+        s *= 2
+    return orc.rescale(S)

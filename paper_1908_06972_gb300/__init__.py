@@ -93,6 +93,8 @@ def lib():
             "pft_autotune": [vp, POINTER(c_double), i, ip], "pft_set_transform_variant": [vp, i],
             "pft_ft_model_create": [vp, POINTER(c_double), POINTER(c_double), i, i, i, i, pp],
             "pft_ft_model_import": [vp, pp, pp, i, i, i, pp], "pft_ft_model_destroy": [vp],
+            "pft_ft_model_create_diag": [vp, POINTER(c_double), POINTER(c_double), i, i, i, i, pp],
+            "pft_ft_model_import_diag": [vp, pp, vp, i, i, i, pp],
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
             "pft_fasttext_train_step": [vp, vp, pp, i],
             "pft_prof_start": [ctypes.c_char_p],
@@ -123,7 +125,7 @@ def exported_symbols():
             "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc",
             "pft_ct_import_batch", "pft_ct_export_batch", "pft_graph_begin", "pft_graph_end",
             "pft_graph_launch", "pft_graph_destroy", "pft_autotune", "pft_set_transform_variant",
-            "pft_rotate_hoisted"]
+            "pft_rotate_hoisted", "pft_ft_model_create_diag", "pft_ft_model_import_diag"]
 
 
 def _check(rc, ctx=None):
@@ -476,6 +478,22 @@ def pft_ft_model_create(ctx, H, O, level):
 def pft_ft_model_import(ctx, H_pts, O_pts, m, n, c):
     out = c_void_p()
     _check(lib().pft_ft_model_import(ctx, _arr(H_pts), _arr(O_pts), m, n, c, ctypes.byref(out)), ctx)
+    return out
+
+
+def pft_ft_model_create_diag(ctx, H, O, level):
+    H = np.ascontiguousarray(H, np.float64)
+    O = np.ascontiguousarray(O, np.float64)
+    out = c_void_p()
+    _check(lib().pft_ft_model_create_diag(ctx, H.ctypes.data_as(POINTER(c_double)),
+                                          O.ctypes.data_as(POINTER(c_double)), H.shape[0], H.shape[1], O.shape[1],
+                                          level, ctypes.byref(out)), ctx)
+    return out
+
+
+def pft_ft_model_import_diag(ctx, D_pts, P_pt, m, n, c):
+    out = c_void_p()
+    _check(lib().pft_ft_model_import_diag(ctx, _arr(D_pts), P_pt, m, n, c, ctypes.byref(out)), ctx)
     return out
 
 

@@ -61,7 +61,8 @@ struct pft_graph {
 struct pft_ft_model {
     pft_ctx* ctx = nullptr;
     int m = 0, n = 0, c = 0, chunks = 0, level = 0;
-    std::vector<pft_pt*> H, O;  // owned copies
+    int variant = 0;            // 0: Fig. 3 packing; 1: diagonal packing (rotation-light)
+    std::vector<pft_pt*> H, O;  // owned copies (variant 1: H = diagonals D_k, O = {P})
 };
 
 namespace pft {
@@ -911,8 +912,62 @@ static int ilog2(int x) {
     return r;
 }
 
+// T[i] += rotate(T[i], g) for every ciphertext of T: c0 + aut(c0) first, then the key switch
+// of aut(c1) with (T.c0, T.c1) as accumulators, in place; tiled to bound the scratch memory.
+static void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g) {
+    NEED(c->keys.count(g), PFT_ERR_NO_KEY, "missing rotation key");
+    const int n = c->n;
+    const size_t limb = n;
+    size_t i0 = 0;
+    const size_t budget = (size_t)24 << 30;
+    while (i0 < T.size()) {
+        size_t i1 = i0, bytes = 0;
+        while (i1 < T.size()) {
+            const int l = T[i1]->level, E = l + c->k, beta = (l + c->alpha - 1) / c->alpha;
+            const size_t per = (size_t)(2 * l + l + beta * E + 2 * E + 2 * l) * limb * 8;
+            if (i1 > i0 && bytes + per > budget) break;
+            bytes += per;
+            i1++;
+        }
+        std::vector<size_t> off;
+        size_t tot = 0;
+        for (size_t i = i0; i < i1; i++) {
+            off.push_back(tot);
+            tot += 2 * (size_t)T[i]->level;
+        }
+        Scratch R(c, tot * limb * 8);
+        std::vector<PolyRef> rin, rout, tin0, rc0;
+        std::vector<KsIO> io;
+        for (size_t i = i0; i < i1; i++) {
+            const int l = T[i]->level;
+            u64* r = R.u() + off[i - i0] * limb;
+            for (int pol = 0; pol < 2; pol++) {
+                rin.push_back(cpoly(T[i]->data, l, n, pol));
+                rout.push_back(cpoly(r, l, n, pol));
+            }
+            tin0.push_back(cpoly(T[i]->data, l, n, 0));
+            rc0.push_back(cpoly(r, l, n, 0));
+            io.push_back(KsIO{r + l * limb, T[i]->data, T[i]->data + l * limb, T[i]->data, T[i]->data + l * limb, l});
+        }
+        chunks(rout.size(), [&](size_t x, size_t y) {
+            automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
+        });
+        ew(c, EwOp::Add, tin0, rc0, tin0);
+        keyswitch_batch(c, c->keys[g], io);
+        i0 = i1;
+    }
+}
+
+static void fasttext_diag_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int B,
+                                pft_ct* const* scores);
+
 static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int chunks_in, int B,
                            pft_ct* const* scores) {
+    if (M && M->variant == 1) {
+        NEED(chunks_in == 1, PFT_ERR_ARG, "the diagonal variant takes one input ciphertext per document");
+        fasttext_diag_batch(c, M, v, B, scores);
+        return;
+    }
     NEED(M && M->ctx == c, PFT_ERR_ARG, "model from another context");
     NEED(chunks_in == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
     const int l = M->level, n = c->n, cols = M->n;
@@ -960,41 +1015,7 @@ static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* cons
                c->stream);
     }
     // 2. TotalSum (Algorithm 2): T += rotate(T, 2^s), s = 0..log2(t)-1, all columns share each key
-    {
-        const int E = l + c->k, beta = (l + c->alpha - 1) / c->alpha;
-        const size_t per_ct = (size_t)(2 * l + l + beta * E + 2 * E + 2 * l + 3 * l) * limb * 8;
-        const size_t budget = (size_t)24 << 30;
-        const size_t tile = std::max<size_t>(1, std::min(nT, budget / per_ct));
-        for (int s = 0; s < steps; s++) {
-            const u32 g = galois_of(n, 1 << s);
-            for (size_t t0 = 0; t0 < nT; t0 += tile) {
-                const size_t t1 = std::min(nT, t0 + tile);
-                Scratch R(c, (t1 - t0) * 2 * l * limb * 8);
-                std::vector<PolyRef> rin, rout, tin0, rc0;
-                for (size_t i = t0; i < t1; i++)
-                    for (int pol = 0; pol < 2; pol++) {
-                        rin.push_back(cpoly(T[i].data, l, n, pol));
-                        rout.push_back(cpoly(R.u() + (i - t0) * 2 * l * limb, l, n, pol));
-                    }
-                chunks(rout.size(), [&](size_t x, size_t y) {
-                    automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
-                });
-                // c0' + T.c0 first, then key switch c1' with T.c0/T.c1 as accumulators (in place)
-                for (size_t i = t0; i < t1; i++) {
-                    tin0.push_back(cpoly(T[i].data, l, n, 0));
-                    rc0.push_back(cpoly(R.u() + (i - t0) * 2 * l * limb, l, n, 0));
-                }
-                ew(c, EwOp::Add, tin0, rc0, tin0);
-                std::vector<KsIO> io;
-                for (size_t i = t0; i < t1; i++) {
-                    u64* r = R.u() + (i - t0) * 2 * l * limb;
-                    io.push_back(
-                        KsIO{r + l * limb, T[i].data, T[i].data + l * limb, T[i].data, T[i].data + l * limb, l});
-                }
-                keyswitch_batch(c, c->keys[g], io);
-            }
-        }
-    }
+    for (int s = 0; s < steps; s++) rot_accumulate(c, Tp, galois_of(n, 1 << s));
     // 3. rescale every column
     op_rescale_batch(c, Tp.data(), (int)nT, Tp.data());
     // 4. s = sum_j h_j * O_j  (Fig. 3 horizontal packing), 5. rescale
@@ -1019,6 +1040,83 @@ static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* cons
                c->stream);
         op_rescale_batch(c, (const pft_ct* const*)scores, B, scores);
     }
+}
+
+// ---- rotation-light fastText (diagonal packing; not in the paper) ---------------------------
+//   Q = sum_{k<n} rot(v, k) D_k  (n-1 hoisted rotations, D_k[i] = H[(i+k) mod t, i mod n]),
+//   Q += rot(Q, n 2^s) for n 2^s < t  ->  h_{i mod n} in slot i;  rescale;
+//   S = Q P (P[n c + j] = O[j, c]);  S += rot(S, 2^s) for 2^s < n  ->  s_c in slot n c;  rescale.
+static void fasttext_diag_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int B,
+                                pft_ct* const* scores) {
+    const int l = M->level, n = c->n, cols = M->n, t = n / 2;
+    const size_t limb = n;
+    NEED(l >= 3, PFT_ERR_LEVEL_MISMATCH, "inference needs three levels");
+    for (int b = 0; b < B; b++) {
+        check_ct(v[b]);
+        NEED(v[b]->level == l, PFT_ERR_LEVEL_MISMATCH, "input level differs from the model level");
+    }
+    std::vector<int32_t> hsteps;
+    for (int k = 1; k < cols; k++) hsteps.push_back(k);
+    for (int st = cols; st < t; st *= 2) NEED(c->keys.count(galois_of(n, st)), PFT_ERR_NO_KEY, "missing rotation key");
+    for (int32_t st : hsteps) NEED(c->keys.count(galois_of(n, st)), PFT_ERR_NO_KEY, "missing rotation key");
+    // 1. Q_b = sum_k rot(v_b, k) D_k, documents in chunks that bound the rotated copies' memory
+    std::vector<pft_ct> Q(B);
+    std::vector<pft_ct*> Qp(B);
+    struct Cleanup {
+        pft_ctx* c;
+        std::vector<pft_ct>* T;
+        ~Cleanup() {
+            for (auto& x : *T) dfree(c, x.data);
+        }
+    } cleanup{c, &Q};
+    for (int b = 0; b < B; b++) {
+        Q[b].ctx = c;
+        ensure_ct(c, &Q[b], l);
+        Q[b].scale = v[b]->scale * M->H[0]->scale;
+        Qp[b] = &Q[b];
+    }
+    const size_t per_doc = (size_t)(cols - 1) * 2 * l * limb * 8;
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(B, ((size_t)16 << 30) / per_doc));
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        const int b1 = std::min(B, b0 + chunk);
+        std::vector<pft_ct> R((size_t)(b1 - b0) * (cols - 1));
+        struct CleanR {
+            pft_ctx* c;
+            std::vector<pft_ct>* T;
+            ~CleanR() {
+                for (auto& x : *T) dfree(c, x.data);
+            }
+        } cleanR{c, &R};
+        for (auto& x : R) x.ctx = c;
+        for (int b = b0; b < b1; b++) {
+            std::vector<pft_ct*> outs;
+            for (int k = 0; k < cols - 1; k++) outs.push_back(&R[(size_t)(b - b0) * (cols - 1) + k]);
+            op_rotate_hoisted(c, v[b], hsteps.data(), cols - 1, outs.data());
+        }
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int k = 0; k < cols; k++) Bv.push_back(M->H[k]->data);
+        for (int b = b0; b < b1; b++)
+            for (int pol = 0; pol < 2; pol++) {
+                A.push_back(v[b]->data + (size_t)pol * l * limb);
+                for (int k = 1; k < cols; k++)
+                    A.push_back(R[(size_t)(b - b0) * (cols - 1) + k - 1].data + (size_t)pol * l * limb);
+                O.push_back(Q[b].data + (size_t)pol * l * limb);
+            }
+        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
+        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l,
+               c->stream);
+    }
+    // 2. stride-n rotate-and-sum
+    for (int st = cols; st < t; st *= 2) rot_accumulate(c, Qp, galois_of(n, st));
+    // 3. rescale
+    op_rescale_batch(c, Qp.data(), B, Qp.data());
+    // 4. S = Q P, 5. block sum, 6. rescale
+    std::vector<const pft_pt*> Pp(B, M->O[0]);
+    op_mul_plain_batch(c, Qp.data(), Pp.data(), B, scores);
+    std::vector<pft_ct*> Sp(scores, scores + B);
+    for (int st = 1; st < cols; st *= 2) rot_accumulate(c, Sp, galois_of(n, st));
+    op_rescale_batch(c, (const pft_ct* const*)scores, B, scores);
 }
 
 // ---- allocation-free rescale ---------------------------------------------------------------
@@ -1780,6 +1878,90 @@ int pft_ft_model_create(pft_ctx* c, const double* H, const double* O, int m, int
         M->level = level;
         M->H = hp;
         M->O = op;
+        *out = M.release();
+    });
+}
+
+int pft_ft_model_create_diag(pft_ctx* c, const double* H, const double* O, int m, int n, int cl, int level,
+                             pft_ft_model** out) {
+    return guard(c, [&] {
+        const int t = c ? c->n / 2 : 0;
+        NEED(c && H && O && out && m >= 1 && m <= t && n >= 2 && cl >= 1, PFT_ERR_ARG, "bad arguments");
+        NEED((n & (n - 1)) == 0 && t % n == 0 && (size_t)n * cl <= (size_t)t, PFT_ERR_ARG,
+             "diagonal packing needs n a power of two dividing N/2 and n c <= N/2");
+        NEED(level >= 3 && level <= c->L, PFT_ERR_ARG, "model level must be in 3..L");
+        std::vector<pft_pt*> dp, op;
+        auto cleanup = [&] {
+            for (auto p : dp) pft_pt_destroy(p);
+            for (auto p : op) pft_pt_destroy(p);
+        };
+        std::vector<double> slots(2 * (size_t)t);
+        int rc = PFT_OK;
+        for (int k = 0; k < n && rc == PFT_OK; k++) {  // D_k[i] = H[(i + k) mod t, i mod n] (zero rows >= m)
+            std::fill(slots.begin(), slots.end(), 0.0);
+            for (int i = 0; i < t; i++) {
+                const int row = (i + k) % t;
+                if (row < m) slots[2 * (size_t)i] = H[(size_t)row * n + (i % n)];
+            }
+            pft_pt* p = nullptr;
+            rc = pft_encode(c, slots.data(), t, c->prm.scale, level, &p);
+            if (rc == PFT_OK) dp.push_back(p);
+        }
+        if (rc == PFT_OK) {  // P[n c + j] = O[j, c]
+            std::fill(slots.begin(), slots.end(), 0.0);
+            for (int cc = 0; cc < cl; cc++)
+                for (int j = 0; j < n; j++) slots[2 * ((size_t)n * cc + j)] = O[(size_t)j * cl + cc];
+            pft_pt* p = nullptr;
+            rc = pft_encode(c, slots.data(), t, c->prm.scale, level - 1, &p);
+            if (rc == PFT_OK) op.push_back(p);
+        }
+        if (rc != PFT_OK) {
+            cleanup();
+            fail(rc, c->err);
+        }
+        std::unique_ptr<pft_ft_model> M(new pft_ft_model());
+        M->ctx = c;
+        M->m = m;
+        M->n = n;
+        M->c = cl;
+        M->chunks = 1;
+        M->level = level;
+        M->variant = 1;
+        M->H = dp;
+        M->O = op;
+        *out = M.release();
+    });
+}
+
+int pft_ft_model_import_diag(pft_ctx* c, const pft_pt* const* D_pts, const pft_pt* P_pt, int m, int n, int cl,
+                             pft_ft_model** out) {
+    return guard(c, [&] {
+        const int t = c ? c->n / 2 : 0;
+        NEED(c && D_pts && P_pt && out && m >= 1 && m <= t && n >= 2 && cl >= 1, PFT_ERR_ARG, "bad arguments");
+        NEED((n & (n - 1)) == 0 && t % n == 0 && (size_t)n * cl <= (size_t)t, PFT_ERR_ARG,
+             "diagonal packing needs n a power of two dividing N/2 and n c <= N/2");
+        std::unique_ptr<pft_ft_model> M(new pft_ft_model());
+        M->ctx = c;
+        M->m = m;
+        M->n = n;
+        M->c = cl;
+        M->chunks = 1;
+        M->level = D_pts[0]->level;
+        M->variant = 1;
+        auto copy_pt = [&](const pft_pt* p) {
+            check_pt(p);
+            pft_pt* q = new_pt(c);
+            ensure_pt(c, q, p->level);
+            q->scale = p->scale;
+            PFT_CUDA(cudaMemcpyAsync(q->data, p->data, (size_t)p->level * c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+            return q;
+        };
+        for (int k = 0; k < n; k++) {
+            NEED(D_pts[k]->level == M->level, PFT_ERR_LEVEL_MISMATCH, "diagonal plaintexts at different levels");
+            M->H.push_back(copy_pt(D_pts[k]));
+        }
+        NEED(P_pt->level == M->level - 1, PFT_ERR_LEVEL_MISMATCH, "output plaintext must sit one level below");
+        M->O.push_back(copy_pt(P_pt));
         *out = M.release();
     });
 }

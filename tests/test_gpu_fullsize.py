@@ -107,3 +107,34 @@ def test_fasttext_full_model_batched_tolerance(p3):
             pf.pft_ct_destroy(h)
     finally:
         pf.pft_ft_model_destroy(model)
+
+
+def test_fasttext_diagonal_full_model_batched_tolerance(p3):
+    """Rotation-light variant on the 32768 x 64 x 14 model: 4 documents in one call, scores in
+    slots 64 c, within 2^-20 of the FP64 Algorithm 1.  The input is rotated before its
+    plaintext product, so it is encrypted at scale 2^50 to keep key-switching noise small."""
+    pf, ctx = p3.pft, p3.ctx
+    t = p3.N // 2
+    m, n, c = 32768, 64, 14
+    pf.pft_add_rotation_keys(ctx, list(range(1, n)) + [n << s for s in range(9)])
+    H, O = synth.fasttext_weights(43, m, n, c)
+    docs = synth.documents(44, m, 4)
+    model = pf.pft_ft_model_create_diag(ctx, H, O, 3)
+    try:
+        vs = []
+        for d in range(4):
+            pt = pf.pft_encode(ctx, docs[d], 2.0 ** 50, 3)
+            vs.append(pf.pft_encrypt(ctx, pt, pf.PFT_ENC_SK, 8000 + d))
+            pf.pft_pt_destroy(pt)
+        scores = [p3.empty() for _ in range(4)]
+        pf.pft_fasttext_infer_batch(ctx, model, vs, 1, scores)
+        for d in range(4):
+            dec = pf.pft_decrypt(ctx, scores[d])
+            got = pf.pft_decode(ctx, dec, t).real[[n * cc for cc in range(c)]]
+            pf.pft_pt_destroy(dec)
+            want = OF.plain_scores(docs[d], H, O)
+            assert np.max(np.abs(got - want)) < 2.0 ** -20, np.max(np.abs(got - want))
+        for h in vs:
+            pf.pft_ct_destroy(h)
+    finally:
+        pf.pft_ft_model_destroy(model)

@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 def p1(gpu):
     # toy smoke-test chain: N = 2^12, q0 60-bit, two 40-bit primes, one 60-bit special prime,
     # one prime per digit (the paper's "one key holds l ciphertexts" structure)
-    p = Pair(gpu, 12, 3, 1, 1, rot_steps=[1, -1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 3])
+    p = Pair(gpu, 12, 3, 1, 1, rot_steps=[1, -1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 3, 5, 6, 7])
     yield p
     p.close()
 
@@ -175,7 +175,7 @@ def test_errors(p1, cts1):
         pf.pft_add(ctx, ga, low, out)
     assert e.value.code == pf.PFT_ERR_LEVEL_MISMATCH
     with pytest.raises(pf.PftError) as e:
-        pf.pft_rotate(ctx, ga, 5, out)
+        pf.pft_rotate(ctx, ga, 9, out)
     assert e.value.code == pf.PFT_ERR_NO_KEY
     with pytest.raises(pf.PftError) as e:
         pf.pft_fasttext_train_step(ctx, None, [])
@@ -334,3 +334,27 @@ def test_hoisted_rotations_bit_exact(which, request):
     pf.pft_rotate_hoisted(ctx, ga, steps, outs)
     for h, w, st in zip(outs, o.rotate_hoisted(a, steps), steps):
         p.assert_equal(h, w, "hoisted rotate %d" % st)
+
+
+def test_fasttext_diagonal_bit_exact_n12(p1):
+    """Rotation-light matvec (diagonal packing, hoisted rotations) against the oracle's sequence."""
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    t = p1.N // 2
+    m, n, c = t - 100, 8, 3
+    H, O = synth.fasttext_weights(19, m, n, c)
+    v = np.zeros(t)
+    v[:m] = synth.documents(20, m, 1, 20, 60)[0]
+    D, P = OF.pack_diag(H, O, t)
+    D_o = [o.encode(D[k], level=3) for k in range(n)]
+    P_o = o.encode(P, level=2)
+    model = pf.pft_ft_model_import_diag(ctx, [p1.pt(x) for x in D_o], p1.pt(P_o), m, n, c)
+    try:
+        v_o = o.encrypt_sk(o.encode(v, level=3), 123)
+        s = p1.empty()
+        pf.pft_fasttext_infer(ctx, model, [p1.ct(v_o)], s)
+        want = OF.encrypted_scores_diag(o, v_o, D_o, P_o)
+        p1.assert_equal(s, want, "fasttext diagonal")
+        got = o.decode(o.decrypt(want)).real[OF.diag_score_slots(n, c)]
+        assert np.max(np.abs(got - OF.plain_scores(v[:m], H, O))) < 2.0 ** -20
+    finally:
+        pf.pft_ft_model_destroy(model)

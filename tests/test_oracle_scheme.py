@@ -120,7 +120,7 @@ def test_decode_encode_precision():
 def small():
     orc = ckks.Oracle(logn=10, n_limbs=3, n_special=2, alpha=2, first_bits=60, mid_bits=40, special_bits=60,
                       seed=(11, 22, 33, 44))
-    orc.keygen(rot_steps=[1, 2, 4, 8, 16, 32, 64, 128, 256, -1, 3], relin=True)
+    orc.keygen(rot_steps=[1, 2, 4, 8, 16, 32, 64, 128, 256, -1, 3, 5, 6, 7], relin=True)
     return orc
 
 
@@ -226,3 +226,26 @@ def test_hoisted_rotations_meaning_and_noise(small):
         plain = orc.rotate(ct, step)
         d = C.vsub(orc.decrypt(h).m, orc.decrypt(plain).m, orc.q)
         assert max(abs(int(v)) for v in ckks.crt_centered(d, orc.q)) <= 2 * _ks_bound(orc, orc.L)
+
+
+def test_fasttext_diagonal_variant(small):
+    """The rotation-light matvec: diagonal packing identity in FP64, and the encrypted
+    sequence within 2^-20 of Algorithm 1 (scores in slots n c)."""
+    orc = small
+    t = orc.N // 2
+    m, n, c = t - 13, 8, 3
+    H = rng.normal(0, 0.1, (m, n))
+    O = rng.normal(0, 0.1, (n, c))
+    v = np.bincount(rng.integers(0, m, 30), minlength=t)[:t] / 30.0
+    v[m:] = 0
+    D, P = fasttext.pack_diag(H, O, t)
+    # plaintext identity of the packing
+    Q = sum(np.roll(v, -k) * D[k] for k in range(n))
+    h = np.array([Q[j::n].sum() for j in range(n)])
+    assert np.allclose(h, v[:m] @ H, atol=1e-12)
+    l = orc.L
+    D_pts = [orc.encode(D[k], level=l) for k in range(n)]
+    P_pt = orc.encode(P, level=l - 1)
+    S = fasttext.encrypted_scores_diag(orc, orc.encrypt_sk(orc.encode(v, level=l), 77), D_pts, P_pt)
+    got = orc.decode(orc.decrypt(S)).real[fasttext.diag_score_slots(n, c)]
+    assert np.max(np.abs(got - fasttext.plain_scores(v[:m], H, O))) < 2 ** -20
