@@ -254,6 +254,10 @@ def run_gpu(args):
     if args.fasttext:
         ft = fasttext_measure(pft, torch, max(1, args.steps // 2), 1)
 
+    sv = None
+    if args.serve > 0:
+        sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_low_load)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_level)
@@ -272,7 +276,7 @@ def run_gpu(args):
            "gpu_launches": int(all_launches), "roofline": roof,
            "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
                         "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
-           "fasttext": ft}
+           "fasttext": ft, "serving": sv}
     if rank == 0:
         print(json.dumps(out))
     for h in A + B + C:
@@ -333,8 +337,12 @@ FT_WORKLOAD = ("vocab 32768, dim 64, 14 classes, weights N(0, 0.1^2); Zipf(1.1) 
                "N=2^16, chain 60 + 29x40 bits + 4 special (60 bits), digits of 4 primes, inputs at level 3")
 
 
+def fp64_scores(v, H, O):
+    """Algorithm 1, steps 2-3 in FP64 (the reported accuracy check): s = (v H) O."""
+    return (np.asarray(v, np.float64) @ H) @ O
+
+
 def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
-    from oracle import fasttext as OF  # FP64 Algorithm 1 for the reported accuracy check only
     from paper_1908_06972_gb300 import synth
 
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, 60, 40, 60, 2.0 ** 40, SEED)
@@ -372,7 +380,7 @@ def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
     dec = pft.pft_decrypt(ctx, scores[0])
     got = pft.pft_decode(ctx, dec, FT_C)[:FT_C].real
     pft.pft_pt_destroy(dec)
-    err = float(np.max(np.abs(got - OF.plain_scores(docs[0], H, O))))
+    err = float(np.max(np.abs(got - fp64_scores(docs[0], H, O))))
     # plain path: one library call per op per ciphertext
     Hp = [pft.pft_encode(ctx, H[:, j], 2.0 ** 40, FT_LEVEL) for j in range(FT_N)]
     Op = []
@@ -412,7 +420,7 @@ def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
     dec = pft.pft_decrypt(ctx, scores[0])
     dgot = pft.pft_decode(ctx, dec, t).real[[FT_N * cc for cc in range(FT_C)]]
     pft.pft_pt_destroy(dec)
-    derr = float(np.max(np.abs(dgot - OF.plain_scores(docs[0], H, O))))
+    derr = float(np.max(np.abs(dgot - fp64_scores(docs[0], H, O))))
     pft.pft_ft_model_destroy(dmodel)
     for h in dvs:
         pft.pft_ct_destroy(h)
@@ -428,6 +436,100 @@ def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
             "max_abs_err_vs_fp64": err, "rotations_per_inference": FT_N * 15,
             "diagonal_variant": {"batched_value": round(FT_BATCH * steps / tdb, 3), "max_abs_err_vs_fp64": derr,
                                  "rotations_per_inference": FT_N - 1 + 9 + 6, "input_scale": "2^50"}}
+
+
+# ---- serving loop: Poisson arrivals, continuous batching ------------------------------------------
+SV_RINGS = [  # (log_n, limbs, special primes, primes per digit, request levels)
+    (16, 30, 4, 4, (12, 30)),
+    (15, 18, 2, 2, (12, 18)),
+]
+SV_WORKLOAD = ("Poisson arrivals of encrypted fastText inferences (vocab 32768, dim 64, 14 classes, the Fig. 3 "
+               "sequence); two rings, half the requests each: N=2^16 (60 + 29x40 bits + 4 special, digits of 4; "
+               "request levels U{12..30}) and N=2^15 (60 + 17x40 bits + 2 special, digits of 2; U{12..18}, "
+               "vocabulary in 2 ciphertexts); keys and models resident; inputs and scores in host memory")
+
+
+def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, seed=31):
+    from paper_1908_06972_gb300 import serving, synth
+
+    H, O = synth.fasttext_weights(77, FT_M, FT_N, FT_C)
+    streams, ctxs, models = [], [], []
+    for logn, lim, ksp, alpha, _ in SV_RINGS:
+        st = torch.cuda.Stream()
+        ctx = pft.pft_ctx_create(logn, lim, ksp, alpha, 60, 40, 60, 2.0 ** 40, SEED, stream=st.cuda_stream)
+        pft.pft_keygen(ctx, [1 << i for i in range(logn - 1)], False)
+        models.append(pft.pft_ft_model_create(ctx, H, O, lim))
+        streams.append(st)
+        ctxs.append(ctx)
+    torch.cuda.synchronize()
+
+    def trace(count, rate_, tseed):
+        rng = np.random.default_rng(tseed)
+        times = serving.poisson_arrivals(rate_, count, tseed)
+        docs = synth.documents(tseed + 1, FT_M, count)
+        reqs = []
+        for i in range(count):
+            r = int(rng.integers(0, 2))
+            logn, _, _, _, (lo, hi) = SV_RINGS[r]
+            level = int(rng.integers(lo, hi + 1))
+            n, t = 1 << logn, 1 << (logn - 1)
+            chunks = -(-FT_M // t)
+            coeffs = np.zeros((chunks, 2, level, n), np.uint64)
+            for c in range(chunks):
+                pt = pft.pft_encode(ctxs[r], docs[i][c * t:(c + 1) * t], 2.0 ** 40, level)
+                ct = pft.pft_encrypt(ctxs[r], pt, pft.PFT_ENC_SK, 40000 + 4 * i + c)
+                pft.pft_ct_export(ctxs[r], ct, coeffs[c])
+                pft.pft_ct_destroy(ct)
+                pft.pft_pt_destroy(pt)
+            out = np.zeros((2, level - 2, n), np.uint64)
+            reqs.append(serving.Request(t=float(times[i]), ring=r, level=level, scale=2.0 ** 40, coeffs=coeffs,
+                                        out=out, tag=i))
+        return reqs, docs
+
+    def run(reqs):
+        srv = pft.pft_server_create(ctxs, models, int(budget_gib * 2 ** 30))
+        try:
+            return serving.replay(srv, reqs)
+        finally:
+            pft.pft_server_destroy(srv)
+
+    def summary(res, reqs, rate_):
+        return {"requests": len(reqs), "offered_rate": round(rate_, 3), "throughput": round(res.throughput(), 3),
+                "p50_s": round(res.percentile(50), 3), "p99_s": round(res.percentile(99), 3),
+                "makespan_s": round(res.makespan, 3), "max_active": res.max_active, "iterations": res.iterations,
+                "peak_resident_gib": round(res.peak_bytes / 2 ** 30, 2),
+                "requests_per_ring": [sum(1 for q in reqs if q.ring == r) for r in range(len(SV_RINGS))],
+                "mean_level": round(float(np.mean([q.level for q in reqs])), 2)}
+
+    warm, _ = trace(2, 1000.0, seed + 100)  # kernels loaded, allocator pools grown
+    run(warm)
+    reqs, docs = trace(n_req, rate, seed)
+    res = run(reqs)
+    out = {"workload": SV_WORKLOAD, "unit": "inferences/s", "budget_gib": budget_gib,
+           "saturated": summary(res, reqs, rate)}
+    # accuracy: decrypt the first request of each ring against FP64 Algorithm 1
+    err = 0.0
+    for r in range(len(SV_RINGS)):
+        q = next((q for q in reqs if q.ring == r), None)
+        if q is None:
+            continue
+        sc = res.done[q.tag]["scale"]
+        h = pft.pft_ct_import(ctxs[r], q.out, sc)
+        dec = pft.pft_decrypt(ctxs[r], h)
+        got = pft.pft_decode(ctxs[r], dec, FT_C)[:FT_C].real
+        pft.pft_pt_destroy(dec)
+        pft.pft_ct_destroy(h)
+        err = max(err, float(np.max(np.abs(got - fp64_scores(docs[q.tag], H, O)))))
+    out["max_abs_err_vs_fp64"] = err
+    if low_load > 0:
+        rate_low = low_load * res.throughput()
+        reqs_low, _ = trace(n_req, rate_low, seed + 7)
+        out["under_capacity"] = summary(run(reqs_low), reqs_low, rate_low)
+    for m in models:
+        pft.pft_ft_model_destroy(m)
+    for c in ctxs:
+        pft.pft_ctx_destroy(c)
+    return out
 
 
 # ---- isolated kernel case (for ncu captures and burst rooflines) --------------------------------
@@ -576,6 +678,11 @@ def main():
     ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
     ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
     ap.add_argument("--graph", type=int, default=1, help="also measure the step as one CUDA-graph launch")
+    ap.add_argument("--serve", type=int, default=24, help="requests in the serving trace (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
+    ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")
+    ap.add_argument("--serve-low-load", type=float, default=0.7,
+                    help="second trace offered at this fraction of the measured throughput (0: skip)")
     args = ap.parse_args()
     if args.case == "ntt":
         run_case_ntt(args)

@@ -220,6 +220,12 @@ int pft_rescale(pft_ctx* ctx, const pft_ct* a, pft_ct* out);
  * key switching with the rotation key of g.  Steps with no key -> PFT_ERR_NO_KEY. */
 int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
 
+/* Sums of HMULPLAIN products (the inner step of Sec. 3.1's matrix products):
+ * outs[o] = sum_{k<K} cts[o K + k] * pts[pts_shared ? k : o K + k], all at one level, the
+ * products of one output at one scale; one launch for all outputs. */
+int pft_dot_plain_batch(pft_ctx* ctx, const pft_ct* const* cts, const pft_pt* const* pts, int K, int n_out,
+                        int pts_shared, pft_ct* const* outs);
+
 /* Rotations of one ciphertext by n steps that share one ModUp of c1 (hoisting): the
  * extended digits are computed once and permuted by each step's automorphism before the
  * inner product with that step's key and ModDown.  Fast basis conversion does not commute
@@ -313,17 +319,74 @@ int pft_ft_model_create_diag(pft_ctx* ctx, const double* H, const double* O, int
                              pft_ft_model** out);
 int pft_ft_model_import_diag(pft_ctx* ctx, const pft_pt* const* D_pts, const pft_pt* P_pt, int m, int n, int c,
                              pft_ft_model** out);
-/* Scores of one document: v = ceil(m/t) ciphertexts at the model level (the
- * client's count vector, already divided by w).  Sequence: h_j = TotalSum(sum_i
- * v_i * H_{j,i}) with TotalSum rotating by 2^i, i = 0..log2(t)-1 (Algorithm 2),
- * rescale; s = sum_j h_j * O_j; rescale.  Needs rotation keys for 2^i.
- * `scores` receives s in slots 0..c-1 at level-2. */
+/* Scores of one document: v = ceil(m/t) ciphertexts at one level l, 3 <= l <= the model
+ * level (the client's count vector, already divided by w; a model encoded at level L serves
+ * every l <= L through the first l limbs of its plaintexts, which equal the encoding at
+ * level l).  Sequence: h_j = TotalSum(sum_i v_i * H_{j,i}) with TotalSum rotating by 2^i,
+ * i = 0..log2(t)-1 (Algorithm 2), rescale; s = sum_j h_j * O_j; rescale.  Needs rotation
+ * keys for 2^i.  `scores` receives s in slots 0..c-1 at level l-2. */
 int pft_fasttext_infer(pft_ctx* ctx, const pft_ft_model* model, const pft_ct* const* v, int n_chunks,
                        pft_ct* scores);
-/* B documents: v[b * n_chunks + i]; all columns of all documents share each
- * rotation key read. */
+/* B documents: v[b * n_chunks + i], each at its own level; all columns of all documents
+ * share each rotation key read. */
 int pft_fasttext_infer_batch(pft_ctx* ctx, const pft_ft_model* model, const pft_ct* const* v, int n_chunks,
                              int B, pft_ct* const* scores);
+/* ---- request server: continuous batching of fastText inferences ----------
+ * The serving side of Sec. 3.1 (the server evaluates clients' encrypted documents with
+ * its own model); the paper measures single inferences and has no request loop.
+ * A server drives n_rings rings, each a context (with its rotation keys, its model and
+ * its own stream) and a model; rings of different N run concurrently on their streams.
+ * Each request is one document for one ring at level 3..model level.  pft_server_step
+ * runs one iteration: retire finished requests, admit waiting ones in arrival order
+ * while the sum of admitted footprints (pft_server_footprint: the request's inputs,
+ * working ciphertexts and score on the device) stays within budget_bytes (0: no
+ * limit), then advance every admitted request by one stage of its sequence (column
+ * products; one rotate-and-sum step; the output layer), requests at the same stage
+ * of a ring forming one batched call.  It returns once the previous iteration has
+ * finished on the device.  The key-switching work space of each call is allocated
+ * per call besides the budget.  A result equals that of pft_fasttext_infer on the
+ * same input, whatever else was in flight.  Destroy the server before its contexts
+ * and models.  Calls on one server must not overlap;
+ * after an error other than PFT_ERR_ARG / _LEVEL_MISMATCH / _OOM from
+ * pft_server_submit, destroy the server. */
+typedef struct pft_server pft_server;
+typedef struct {
+    uint64_t tag;
+    int ring;
+    int level;      /* level of the score ciphertext (request level - 2) */
+    double scale;   /* scale of the score ciphertext */
+    double t_submit; /* server clock (seconds) at pft_server_submit */
+    double t_done;   /* server clock when the score had reached host memory (CUDA event) */
+} pft_server_done;
+typedef struct {
+    int waiting, active, exporting, max_active;
+    long completed, iterations;
+    size_t bytes_in_use, peak_bytes, budget;
+} pft_server_stats;
+int pft_server_create(pft_ctx* const* ctxs, const pft_ft_model* const* models, int n_rings, size_t budget_bytes,
+                      pft_server** out);
+int pft_server_destroy(pft_server* srv);
+/* Text of the last error on srv; srv = NULL: of the last failed pft_server_create. */
+const char* pft_server_last_error(const pft_server* srv);
+/* Queues one request.  in: host [chunks][2][level][N] u64 in coefficient form, canonical
+ * residues (chunks = ceil(m/t), 1 for the diagonal variant), at `scale`; out: host
+ * buffer of 2 (level-2) N words that receives the score in the same form.  Both stay
+ * owned by the caller and must stay valid until the request is returned by
+ * pft_server_poll (the inputs are read at admission).  PFT_ERR_OOM if the request's
+ * footprint alone exceeds the budget. */
+int pft_server_submit(pft_server* srv, int ring, const uint64_t* in, int level, double scale, uint64_t* out,
+                      uint64_t tag);
+/* One iteration; *n_pending (may be NULL) = requests not yet returned by poll's retire. */
+int pft_server_step(pft_server* srv, int* n_pending);
+/* Steps until every queued request has completed. */
+int pft_server_drain(pft_server* srv);
+/* Completed requests, oldest first, up to max; *n = how many were written. */
+int pft_server_poll(pft_server* srv, pft_server_done* done, int max, int* n);
+/* Seconds since pft_server_create (host steady clock; the time base of submit/done). */
+int pft_server_clock(pft_server* srv, double* t);
+int pft_server_get_stats(pft_server* srv, pft_server_stats* stats);
+int pft_server_footprint(pft_server* srv, int ring, int level, size_t* bytes);
+
 /* Encrypted minibatch training step (Algorithm 5): not implemented yet. */
 int pft_fasttext_train_step(pft_ctx* ctx, pft_ft_model* model, const pft_ct* const* docs, int n_docs);
 

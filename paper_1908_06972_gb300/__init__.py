@@ -49,6 +49,17 @@ class pft_allocator(Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
 
 
+class pft_server_done(Structure):
+    _fields_ = [("tag", c_uint64), ("ring", c_int), ("level", c_int), ("scale", c_double),
+                ("t_submit", c_double), ("t_done", c_double)]
+
+
+class pft_server_stats(Structure):
+    _fields_ = [("waiting", c_int), ("active", c_int), ("exporting", c_int), ("max_active", c_int),
+                ("completed", ctypes.c_long), ("iterations", ctypes.c_long), ("bytes_in_use", c_size_t),
+                ("peak_bytes", c_size_t), ("budget", c_size_t)]
+
+
 def build(force=False):
     """Compile the CUDA library (nvcc, sm_103a) into the package's _build folder."""
     return _build.build(force=force)
@@ -86,6 +97,7 @@ def lib():
             "pft_mul_relin_batch": [vp, pp, pp, i, pp], "pft_rescale_batch": [vp, pp, i, pp],
             "pft_rotate_batch": [vp, pp, i, c_int32, pp],
             "pft_rotate_hoisted": [vp, vp, POINTER(c_int32), i, pp],
+            "pft_dot_plain_batch": [vp, pp, pp, i, i, i, pp],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
             "pft_graph_begin": [vp], "pft_graph_end": [vp, pp], "pft_graph_launch": [vp, vp],
@@ -97,6 +109,12 @@ def lib():
             "pft_ft_model_import_diag": [vp, pp, vp, i, i, i, pp],
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
             "pft_fasttext_train_step": [vp, vp, pp, i],
+            "pft_server_create": [pp, pp, i, c_size_t, pp], "pft_server_destroy": [vp],
+            "pft_server_submit": [vp, i, u64, i, d, u64, c_uint64], "pft_server_step": [vp, ip],
+            "pft_server_drain": [vp], "pft_server_poll": [vp, POINTER(pft_server_done), i, ip],
+            "pft_server_clock": [vp, POINTER(c_double)],
+            "pft_server_get_stats": [vp, POINTER(pft_server_stats)],
+            "pft_server_footprint": [vp, i, i, POINTER(c_size_t)],
             "pft_prof_start": [ctypes.c_char_p],
             "pft_prof_stop": [POINTER(c_double), POINTER(ctypes.c_longlong), POINTER(ctypes.c_longlong),
                               POINTER(c_double)],
@@ -107,6 +125,8 @@ def lib():
             f.restype = c_int
         L.pft_last_error.argtypes = [vp]
         L.pft_last_error.restype = ctypes.c_char_p
+        L.pft_server_last_error.argtypes = [vp]
+        L.pft_server_last_error.restype = ctypes.c_char_p
         _LIB = L
     return _LIB
 
@@ -125,7 +145,10 @@ def exported_symbols():
             "pft_fasttext_train_step", "pft_prof_start", "pft_prof_stop", "pft_rescale_noalloc",
             "pft_ct_import_batch", "pft_ct_export_batch", "pft_graph_begin", "pft_graph_end",
             "pft_graph_launch", "pft_graph_destroy", "pft_autotune", "pft_set_transform_variant",
-            "pft_rotate_hoisted", "pft_ft_model_create_diag", "pft_ft_model_import_diag"]
+            "pft_rotate_hoisted", "pft_ft_model_create_diag", "pft_ft_model_import_diag",
+            "pft_dot_plain_batch", "pft_server_create", "pft_server_destroy", "pft_server_last_error",
+            "pft_server_submit", "pft_server_step", "pft_server_drain", "pft_server_poll", "pft_server_clock",
+            "pft_server_get_stats", "pft_server_footprint"]
 
 
 def _check(rc, ctx=None):
@@ -419,6 +442,10 @@ def pft_rotate_batch(ctx, a, step, out):
     _op("pft_rotate_batch", ctx, _arr(a), len(a), c_int32(step), _arr(out))
 
 
+def pft_dot_plain_batch(ctx, cts, pts, K, outs, pts_shared=False):
+    _op("pft_dot_plain_batch", ctx, _arr(cts), _arr(pts), K, len(outs), 1 if pts_shared else 0, _arr(outs))
+
+
 def pft_rotate_hoisted(ctx, a, steps, outs):
     st = (c_int32 * max(1, len(steps)))(*steps)
     _op("pft_rotate_hoisted", ctx, a, st, len(steps), _arr(outs))
@@ -511,6 +538,68 @@ def pft_fasttext_infer_batch(ctx, model, v, n_chunks, scores):
 
 def pft_fasttext_train_step(ctx, model, docs):
     _op("pft_fasttext_train_step", ctx, model, _arr(docs), len(docs))
+
+
+# ---- request server -----------------------------------------------------------------------
+def _scheck(rc, srv):
+    if rc != PFT_OK:
+        raise PftError(rc, lib().pft_server_last_error(srv).decode())
+
+
+def pft_server_create(ctxs, models, budget_bytes=0):
+    out = c_void_p()
+    rc = lib().pft_server_create(_arr(ctxs), _arr(models), len(ctxs), budget_bytes, ctypes.byref(out))
+    if rc != PFT_OK:
+        raise PftError(rc, lib().pft_server_last_error(None).decode())
+    return out
+
+
+def pft_server_destroy(srv):
+    _check(lib().pft_server_destroy(srv))
+
+
+def pft_server_submit(srv, ring, coeffs, level, scale, out, tag):
+    """coeffs: uint64 [chunks][2][level][N] (kept alive by the caller until the request is
+    polled); out: uint64 array of 2 (level-2) N words, written on completion."""
+    assert coeffs.dtype == np.uint64 and coeffs.flags.c_contiguous
+    assert out.dtype == np.uint64 and out.flags.c_contiguous and out.flags.writeable
+    _scheck(lib().pft_server_submit(srv, ring, _u64p(coeffs), level, scale, _u64p(out), tag), srv)
+
+
+def pft_server_step(srv):
+    n = c_int()
+    _scheck(lib().pft_server_step(srv, ctypes.byref(n)), srv)
+    return n.value
+
+
+def pft_server_drain(srv):
+    _scheck(lib().pft_server_drain(srv), srv)
+
+
+def pft_server_poll(srv, max_n=256):
+    """Completed requests: list of dicts (tag, ring, level, scale, t_submit, t_done)."""
+    buf = (pft_server_done * max_n)()
+    n = c_int()
+    _scheck(lib().pft_server_poll(srv, buf, max_n, ctypes.byref(n)), srv)
+    return [{f: getattr(buf[k], f) for f, _ in pft_server_done._fields_} for k in range(n.value)]
+
+
+def pft_server_clock(srv):
+    t = c_double()
+    _scheck(lib().pft_server_clock(srv, ctypes.byref(t)), srv)
+    return t.value
+
+
+def pft_server_get_stats(srv):
+    st = pft_server_stats()
+    _scheck(lib().pft_server_get_stats(srv, ctypes.byref(st)), srv)
+    return {f: getattr(st, f) for f, _ in pft_server_stats._fields_}
+
+
+def pft_server_footprint(srv, ring, level):
+    b = c_size_t()
+    _scheck(lib().pft_server_footprint(srv, ring, level, ctypes.byref(b)), srv)
+    return b.value
 
 
 # ---- launch accounting ------------------------------------------------------------------------

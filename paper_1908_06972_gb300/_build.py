@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 SO = os.path.join(OUT, "libprivft.so")
-SOURCES = ["ntt.cu", "poly.cu", "ckks.cu", "hostmath.cpp"]
-HEADERS = ["pft_internal.h", "modarith.cuh", os.path.join("..", "..", "include", "privft.h")]
+SOURCES = ["ntt.cu", "poly.cu", "ckks.cu", "serve.cu", "hostmath.cpp"]
+HEADERS = ["pft_internal.h", "evaluator.h", "modarith.cuh", os.path.join("..", "..", "include", "privft.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -10,60 +10,7 @@
 #include <memory>
 #include <stdexcept>
 
-#include "pft_internal.h"
-
-using namespace pft;
-
-// ---- handles ---------------------------------------------------------------------------
-struct pft_ctx {
-    pft_params prm;
-    int logn = 0, n = 0, L = 0, k = 0, alpha = 0, beta_max = 0;
-    std::vector<u64> primes;  // q_0..q_{L-1}, p_0..p_{k-1}
-    pft_allocator alloc{};
-    bool has_alloc = false;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    DevTables tabs{};
-    std::vector<void*> owned;  // table buffers
-    // basis-conversion tables: modup[(l-1) * beta_max + j], moddown[l-1] (device offsets)
-    std::vector<const u64*> modup_tab, moddown_tab;
-    const u64* moddown_consts = nullptr;           // [L][3] {0, P^-1, shoup}
-    std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {0, p^-1, shoup}
-    std::vector<const u64*> pmodq_consts;          // digit j -> [alpha][3] {0, P mod q_m, shoup}
-    std::vector<u64> P_mod_q;
-    std::vector<u32> cdt;
-    // keys
-    bool have_sk = false;
-    u64* s_ntt = nullptr;  // [L+k][N]
-    std::vector<i64> s_coeff;
-    u64* pk = nullptr;  // [2][L][N]  (b, a)
-    std::map<u32, u64*> keys;
-};
-
-struct pft_ct {
-    pft_ctx* ctx = nullptr;
-    u64* data = nullptr;
-    size_t cap = 0;  // words
-    int level = 0;
-    double scale = 1.0;
-};
-struct pft_pt {
-    pft_ctx* ctx = nullptr;
-    u64* data = nullptr;
-    size_t cap = 0;
-    int level = 0;
-    double scale = 1.0;
-};
-struct pft_graph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-struct pft_ft_model {
-    pft_ctx* ctx = nullptr;
-    int m = 0, n = 0, c = 0, chunks = 0, level = 0;
-    int variant = 0;            // 0: Fig. 3 packing; 1: diagonal packing (rotation-light)
-    std::vector<pft_pt*> H, O;  // owned copies (variant 1: H = diagonals D_k, O = {P})
-};
+#include "evaluator.h"
 
 namespace pft {
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
@@ -71,110 +18,6 @@ void check_cuda(cudaError_t e, const char* what) {
     if (e != cudaSuccess) fail(PFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 }  // namespace pft
-
-// ---- memory --------------------------------------------------------------------------
-static void* dalloc(pft_ctx* c, size_t bytes) {
-    if (bytes == 0) return nullptr;
-    void* p = nullptr;
-    if (c->has_alloc) {
-        p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
-    } else {
-        cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
-        if (e != cudaSuccess) p = nullptr;
-    }
-    if (!p) fail(PFT_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
-    return p;
-}
-static void dfree(pft_ctx* c, void* p) {
-    if (!p) return;
-    if (c->has_alloc) c->alloc.free(p, (void*)c->stream, c->alloc.user);
-    else cudaFreeAsync(p, c->stream);
-}
-struct Scratch {
-    pft_ctx* c;
-    void* p;
-    Scratch(pft_ctx* c_, size_t bytes) : c(c_), p(dalloc(c_, bytes)) {}
-    ~Scratch() { dfree(c, p); }
-    u64* u() const { return (u64*)p; }
-    Scratch(const Scratch&) = delete;
-    Scratch& operator=(const Scratch&) = delete;
-};
-template <class T>
-static T* upload(pft_ctx* c, Scratch& s, const std::vector<T>& v) {
-    PFT_CUDA(cudaMemcpyAsync(s.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-    return (T*)s.p;
-}
-static void ensure_ct(pft_ctx* c, pft_ct* ct, int level) {
-    const size_t need = (size_t)2 * level * c->n;
-    if (ct->cap < need) {
-        dfree(c, ct->data);
-        ct->data = nullptr;
-        ct->cap = 0;
-        ct->data = (u64*)dalloc(c, need * 8);
-        ct->cap = need;
-    }
-    ct->level = level;
-}
-static void ensure_pt(pft_ctx* c, pft_pt* pt, int level) {
-    const size_t need = (size_t)level * c->n;
-    if (pt->cap < need) {
-        dfree(c, pt->data);
-        pt->data = nullptr;
-        pt->cap = 0;
-        pt->data = (u64*)dalloc(c, need * 8);
-        pt->cap = need;
-    }
-    pt->level = level;
-}
-
-// ---- polynomial references ------------------------------------------------------------
-static PolyRef ref(u64* p, int nlimbs, int first = 0, int split = -1, int base2 = 0) {
-    PolyRef r;
-    r.ptr = p;
-    r.nlimbs = (uint16_t)nlimbs;
-    r.first = (uint16_t)first;
-    r.split = (uint16_t)(split < 0 ? nlimbs : split);
-    r.base2 = (uint16_t)base2;
-    return r;
-}
-static PolySet mkset(const std::vector<PolyRef>& v, size_t a, size_t b) {
-    PolySet s;
-    s.count = (int)(b - a);
-    s.max_limbs = 0;
-    for (size_t i = a; i < b; i++) {
-        s.p[i - a] = v[i];
-        s.max_limbs = std::max<int>(s.max_limbs, v[i].nlimbs);
-    }
-    return s;
-}
-template <class F>
-static void chunks(size_t n, F f) {
-    for (size_t i = 0; i < n; i += kMaxSet) f(i, std::min(n, i + (size_t)kMaxSet));
-}
-static void ntt_fwd(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
-    chunks(out.size(), [&](size_t a, size_t b) { ntt_forward(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
-}
-static void ntt_inv(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
-    chunks(out.size(), [&](size_t a, size_t b) { ntt_inverse(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
-}
-static void ew(pft_ctx* c, EwOp op, const std::vector<PolyRef>& a, const std::vector<PolyRef>& b,
-               const std::vector<PolyRef>& out) {
-    chunks(out.size(), [&](size_t x, size_t y) {
-        ew_binary(c->tabs, op, mkset(a, x, y), mkset(b.empty() ? a : b, x, y), mkset(out, x, y), c->stream);
-    });
-}
-static void subscale(pft_ctx* c, const std::vector<PolyRef>& x, const std::vector<PolyRef>* y,
-                     const std::vector<PolyRef>* acc, const std::vector<PolyRef>& out, const u64* consts) {
-    chunks(out.size(), [&](size_t a, size_t b) {
-        PolySet sx = mkset(x, a, b), so = mkset(out, a, b);
-        PolySet sy, sa;
-        if (y) sy = mkset(*y, a, b);
-        if (acc) sa = mkset(*acc, a, b);
-        sub_scale(c->tabs, sx, y ? &sy : nullptr, acc ? &sa : nullptr, so, consts, c->stream);
-    });
-}
-// the two polynomials of a ciphertext buffer [2][l][N]
-static PolyRef cpoly(u64* data, int l, int n, int pol) { return ref(data + (size_t)pol * l * n, l); }
 
 // ---- context construction ---------------------------------------------------------------
 static u64 shoup(u64 w, u64 q) { return (u64)(((unsigned __int128)w << 64) / q); }
@@ -339,27 +182,6 @@ static void build_tables(pft_ctx* c) {
     }
 }
 
-// ---- the C ABI guard ------------------------------------------------------------------
-template <class F>
-static int guard(pft_ctx* c, F f) {
-    try {
-        f();
-        return PFT_OK;
-    } catch (const Error& e) {
-        if (c) c->err = e.msg;
-        return e.code;
-    } catch (const std::bad_alloc&) {
-        if (c) c->err = "host out of memory";
-        return PFT_ERR_OOM;
-    } catch (const std::exception& e) {
-        if (c) c->err = e.what();
-        return PFT_ERR_ARG;
-    }
-}
-#define NEED(cond, code, msg) \
-    do {                      \
-        if (!(cond)) fail(code, msg); \
-    } while (0)
 
 static u32 galois_of(int n, int32_t step) {
     const long long half = n / 2;
@@ -577,8 +399,6 @@ static void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>&
 }
 
 // ---- operations ---------------------------------------------------------------------------
-static void check_ct(const pft_ct* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty ciphertext"); }
-static void check_pt(const pft_pt* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty plaintext"); }
 
 static std::map<int, std::vector<int>> by_level(const pft_ct* const* a, int B) {
     std::map<int, std::vector<int>> g;
@@ -906,12 +726,6 @@ static void encrypt(pft_ctx* c, const pft_pt* pt, int mode, u32 nonce, pft_ct* o
 }
 
 // ---- fastText inference (Sec. 3.1) ----------------------------------------------------------
-static int ilog2(int x) {
-    int r = 0;
-    while ((1 << r) < x) r++;
-    return r;
-}
-
 // T[i] += rotate(T[i], g) for every ciphertext of T: c0 + aut(c0) first, then the key switch
 // of aut(c1) with (T.c0, T.c1) as accumulators, in place; tiled to bound the scratch memory.
 static void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g) {
@@ -958,165 +772,257 @@ static void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g) {
     }
 }
 
-static void fasttext_diag_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int B,
-                                pft_ct* const* scores);
+// Stages of one inference.
+//   Fig. 3 packing: BEGIN (column products T_j = sum_i v_i H_{j,i}), ROT(2^s) for 2^s < t
+//     (TotalSum, Algorithm 2), FINISH (rescale the columns, s = sum_j h_j O_j, rescale).
+//   Diagonal packing (rotation-light, not in the paper): BEGIN (Q = sum_k rot(v, k) D_k with
+//     D_k[i] = H[(i + k) mod t, i mod n], n - 1 hoisted rotations), ROT(n 2^s) while n 2^s < t
+//     (h_{i mod n} in slot i), MID (rescale, S = Q P with P[n c + j] = O[j, c]),
+//     ROT(2^s) while 2^s < n (s_c in slot n c), FINISH (rescale).
+std::vector<FtStage> ft_program(pft_ctx* c, const pft_ft_model* M) {
+    const int n = c->n, t = n / 2, cols = M->n;
+    std::vector<FtStage> p{{FT_BEGIN, 0}};
+    if (M->variant == 0) {
+        for (int st = 1; st < t; st *= 2) p.push_back({FT_ROT, galois_of(n, st)});
+    } else {
+        for (int st = cols; st < t; st *= 2) p.push_back({FT_ROT, galois_of(n, st)});
+        p.push_back({FT_MID, 0});
+        for (int st = 1; st < cols; st *= 2) p.push_back({FT_ROT, galois_of(n, st)});
+    }
+    p.push_back({FT_FINISH, 0});
+    return p;
+}
 
-static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int chunks_in, int B,
-                           pft_ct* const* scores) {
-    if (M && M->variant == 1) {
-        NEED(chunks_in == 1, PFT_ERR_ARG, "the diagonal variant takes one input ciphertext per document");
-        fasttext_diag_batch(c, M, v, B, scores);
-        return;
-    }
+void ft_check_doc(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int n_chunks) {
     NEED(M && M->ctx == c, PFT_ERR_ARG, "model from another context");
-    NEED(chunks_in == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
-    const int l = M->level, n = c->n, cols = M->n;
-    const size_t limb = n;
-    NEED(l >= 3, PFT_ERR_LEVEL_MISMATCH, "inference needs three levels");
-    for (int i = 0; i < B * chunks_in; i++) {
+    if (M->variant == 1)
+        NEED(n_chunks == 1, PFT_ERR_ARG, "the diagonal variant takes one input ciphertext per document");
+    else
+        NEED(n_chunks == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
+    NEED(v, PFT_ERR_ARG, "null input");
+    for (int i = 0; i < n_chunks; i++) {
         check_ct(v[i]);
-        NEED(v[i]->level == l, PFT_ERR_LEVEL_MISMATCH, "input level differs from the model level");
+        NEED(v[i]->level == v[0]->level, PFT_ERR_LEVEL_MISMATCH, "the inputs of one document differ in level");
+        NEED(v[i]->scale == v[0]->scale, PFT_ERR_SCALE_MISMATCH, "the inputs of one document differ in scale");
     }
-    const int steps = ilog2(n / 2);
-    for (int s = 0; s < steps; s++)
-        NEED(c->keys.count(galois_of(n, 1 << s)), PFT_ERR_NO_KEY, "missing rotation key for TotalSum");
-    const double sc_v = v[0]->scale, sc_h = M->H[0]->scale;
-    // 1. column products: T[b][j] = sum_i v[b][i] * H[j][i]   (Fig. 3 vertical packing)
-    const size_t nT = (size_t)B * cols;
-    std::vector<pft_ct> T(nT);
-    std::vector<pft_ct*> Tp(nT);
-    for (size_t i = 0; i < nT; i++) {
-        T[i].ctx = c;
-        ensure_ct(c, &T[i], l);
-        T[i].scale = sc_v * sc_h;
-        Tp[i] = &T[i];
-    }
-    struct Cleanup {
-        pft_ctx* c;
-        std::vector<pft_ct>* T;
-        ~Cleanup() {
-            for (auto& t : *T) dfree(c, t.data);
-        }
-    } cleanup{c, &T};
-    {
-        std::vector<const u64*> A, Bv;
-        std::vector<u64*> O;
-        for (int b = 0; b < B; b++)
-            for (int j = 0; j < cols; j++)
-                for (int pol = 0; pol < 2; pol++) {
-                    for (int i = 0; i < chunks_in; i++) {
-                        A.push_back(v[(size_t)b * chunks_in + i]->data + (size_t)pol * l * limb);
-                        Bv.push_back(M->H[(size_t)j * M->chunks + i]->data);
-                    }
-                    O.push_back(T[(size_t)b * cols + j].data + (size_t)pol * l * limb);
-                }
-        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
-        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), chunks_in, false, l,
-               c->stream);
-    }
-    // 2. TotalSum (Algorithm 2): T += rotate(T, 2^s), s = 0..log2(t)-1, all columns share each key
-    for (int s = 0; s < steps; s++) rot_accumulate(c, Tp, galois_of(n, 1 << s));
-    // 3. rescale every column
-    op_rescale_batch(c, Tp.data(), (int)nT, Tp.data());
-    // 4. s = sum_j h_j * O_j  (Fig. 3 horizontal packing), 5. rescale
-    {
-        std::vector<const u64*> A, Bv;
-        std::vector<u64*> O;
-        for (int j = 0; j < cols; j++) {
-            NEED(M->O[j]->level == l - 1, PFT_ERR_LEVEL_MISMATCH, "output-layer plaintexts must sit one level below");
-            Bv.push_back(M->O[j]->data);
-        }
-        for (int b = 0; b < B; b++) {
-            ensure_ct(c, scores[b], l - 1);
-            scores[b]->scale = T[(size_t)b * cols].scale * M->O[0]->scale;
-            for (int pol = 0; pol < 2; pol++) {
-                for (int j = 0; j < cols; j++) A.push_back(T[(size_t)b * cols + j].data + (size_t)pol * (l - 1) * limb);
-                O.push_back(scores[b]->data + (size_t)pol * (l - 1) * limb);
-            }
-        }
-        // B_k for output p = (b, pol) is O_k for every p: one shared table of `cols` entries
-        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
-        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l - 1,
-               c->stream);
-        op_rescale_batch(c, (const pft_ct* const*)scores, B, scores);
+    const int l = v[0]->level;
+    NEED(l >= 3, PFT_ERR_LEVEL_MISMATCH, "inference needs three levels");
+    NEED(l <= M->level, PFT_ERR_LEVEL_MISMATCH, "input level above the model level");
+    for (const pft_pt* o : M->O) NEED(o->level >= l - 1, PFT_ERR_LEVEL_MISMATCH, "output-layer plaintexts too low");
+    const int n = c->n;
+    if (M->variant == 1)
+        for (int k = 1; k < M->n; k++) NEED(c->keys.count(galois_of(n, k)), PFT_ERR_NO_KEY, "missing rotation key");
+    for (const FtStage& st : ft_program(c, M))
+        if (st.kind == FT_ROT)
+            NEED(c->keys.count(st.g), PFT_ERR_NO_KEY,
+                 M->variant == 0 ? "missing rotation key for TotalSum" : "missing rotation key");
+}
+
+static std::map<int, std::vector<FtDoc*>> docs_by_level(const std::vector<FtDoc*>& docs) {
+    std::map<int, std::vector<FtDoc*>> g;
+    for (FtDoc* d : docs) g[d->l].push_back(d);
+    return g;
+}
+
+static void ft_init_work(pft_ctx* c, FtDoc* d, int count, double scale) {
+    d->W.clear();
+    d->W.resize(count);
+    d->work.clear();
+    for (auto& x : d->W) {
+        x.ctx = c;
+        ensure_ct(c, &x, d->l);
+        x.scale = scale;
+        d->work.push_back(&x);
     }
 }
 
-// ---- rotation-light fastText (diagonal packing; not in the paper) ---------------------------
-//   Q = sum_{k<n} rot(v, k) D_k  (n-1 hoisted rotations, D_k[i] = H[(i+k) mod t, i mod n]),
-//   Q += rot(Q, n 2^s) for n 2^s < t  ->  h_{i mod n} in slot i;  rescale;
-//   S = Q P (P[n c + j] = O[j, c]);  S += rot(S, 2^s) for 2^s < n  ->  s_c in slot n c;  rescale.
-static void fasttext_diag_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int B,
-                                pft_ct* const* scores) {
-    const int l = M->level, n = c->n, cols = M->n, t = n / 2;
-    const size_t limb = n;
-    NEED(l >= 3, PFT_ERR_LEVEL_MISMATCH, "inference needs three levels");
-    for (int b = 0; b < B; b++) {
-        check_ct(v[b]);
-        NEED(v[b]->level == l, PFT_ERR_LEVEL_MISMATCH, "input level differs from the model level");
-    }
-    std::vector<int32_t> hsteps;
-    for (int k = 1; k < cols; k++) hsteps.push_back(k);
-    for (int st = cols; st < t; st *= 2) NEED(c->keys.count(galois_of(n, st)), PFT_ERR_NO_KEY, "missing rotation key");
-    for (int32_t st : hsteps) NEED(c->keys.count(galois_of(n, st)), PFT_ERR_NO_KEY, "missing rotation key");
-    // 1. Q_b = sum_k rot(v_b, k) D_k, documents in chunks that bound the rotated copies' memory
-    std::vector<pft_ct> Q(B);
-    std::vector<pft_ct*> Qp(B);
-    struct Cleanup {
-        pft_ctx* c;
-        std::vector<pft_ct>* T;
-        ~Cleanup() {
-            for (auto& x : *T) dfree(c, x.data);
-        }
-    } cleanup{c, &Q};
-    for (int b = 0; b < B; b++) {
-        Q[b].ctx = c;
-        ensure_ct(c, &Q[b], l);
-        Q[b].scale = v[b]->scale * M->H[0]->scale;
-        Qp[b] = &Q[b];
-    }
-    const size_t per_doc = (size_t)(cols - 1) * 2 * l * limb * 8;
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(B, ((size_t)16 << 30) / per_doc));
-    for (int b0 = 0; b0 < B; b0 += chunk) {
-        const int b1 = std::min(B, b0 + chunk);
-        std::vector<pft_ct> R((size_t)(b1 - b0) * (cols - 1));
-        struct CleanR {
-            pft_ctx* c;
-            std::vector<pft_ct>* T;
-            ~CleanR() {
-                for (auto& x : *T) dfree(c, x.data);
-            }
-        } cleanR{c, &R};
-        for (auto& x : R) x.ctx = c;
-        for (int b = b0; b < b1; b++) {
-            std::vector<pft_ct*> outs;
-            for (int k = 0; k < cols - 1; k++) outs.push_back(&R[(size_t)(b - b0) * (cols - 1) + k]);
-            op_rotate_hoisted(c, v[b], hsteps.data(), cols - 1, outs.data());
-        }
+static void ft_release_work(pft_ctx* c, FtDoc* d) {
+    for (auto& x : d->W) dfree(c, x.data);
+    d->W.clear();
+}
+
+// BEGIN, Fig. 3 packing: T[d][j] = sum_i v[d][i] * H[j][i]; one launch per level present.
+static void ft_begin_columns(pft_ctx* c, const pft_ft_model* M, const std::vector<FtDoc*>& docs) {
+    const int cols = M->n, K = M->chunks;
+    const size_t limb = c->n;
+    for (FtDoc* d : docs) ft_init_work(c, d, cols, d->v[0]->scale * M->H[0]->scale);
+    for (auto& kv : docs_by_level(docs)) {
+        const int l = kv.first;
         std::vector<const u64*> A, Bv;
         std::vector<u64*> O;
-        for (int k = 0; k < cols; k++) Bv.push_back(M->H[k]->data);
-        for (int b = b0; b < b1; b++)
-            for (int pol = 0; pol < 2; pol++) {
-                A.push_back(v[b]->data + (size_t)pol * l * limb);
-                for (int k = 1; k < cols; k++)
-                    A.push_back(R[(size_t)(b - b0) * (cols - 1) + k - 1].data + (size_t)pol * l * limb);
-                O.push_back(Q[b].data + (size_t)pol * l * limb);
-            }
+        for (FtDoc* d : kv.second)
+            for (int j = 0; j < cols; j++)
+                for (int pol = 0; pol < 2; pol++) {
+                    for (int i = 0; i < K; i++) {
+                        A.push_back(d->v[i]->data + (size_t)pol * l * limb);
+                        Bv.push_back(M->H[(size_t)j * K + i]->data);
+                    }
+                    O.push_back(d->W[j].data + (size_t)pol * l * limb);
+                }
         Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
-        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l,
+        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), K, false, l,
                c->stream);
     }
-    // 2. stride-n rotate-and-sum
-    for (int st = cols; st < t; st *= 2) rot_accumulate(c, Qp, galois_of(n, st));
-    // 3. rescale
-    op_rescale_batch(c, Qp.data(), B, Qp.data());
-    // 4. S = Q P, 5. block sum, 6. rescale
-    std::vector<const pft_pt*> Pp(B, M->O[0]);
-    op_mul_plain_batch(c, Qp.data(), Pp.data(), B, scores);
-    std::vector<pft_ct*> Sp(scores, scores + B);
-    for (int st = 1; st < cols; st *= 2) rot_accumulate(c, Sp, galois_of(n, st));
-    op_rescale_batch(c, (const pft_ct* const*)scores, B, scores);
+}
+
+// FINISH, Fig. 3 packing: rescale the columns, s = sum_j h_j * O_j (horizontal packing), rescale.
+static void ft_finish_columns(pft_ctx* c, const pft_ft_model* M, const std::vector<FtDoc*>& docs) {
+    const int cols = M->n;
+    const size_t limb = c->n;
+    std::vector<pft_ct*> T;
+    for (FtDoc* d : docs)
+        for (pft_ct* x : d->work) T.push_back(x);
+    op_rescale_batch(c, T.data(), (int)T.size(), T.data());
+    for (auto& kv : docs_by_level(docs)) {
+        const int l1 = kv.first - 1;
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int j = 0; j < cols; j++) Bv.push_back(M->O[j]->data);
+        for (FtDoc* d : kv.second) {
+            ensure_ct(c, d->score, l1);
+            d->score->scale = d->W[0].scale * M->O[0]->scale;
+            for (int pol = 0; pol < 2; pol++) {
+                for (int j = 0; j < cols; j++) A.push_back(d->W[j].data + (size_t)pol * l1 * limb);
+                O.push_back(d->score->data + (size_t)pol * l1 * limb);
+            }
+        }
+        // the O_j table is shared by every output (document, polynomial)
+        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
+        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l1,
+               c->stream);
+    }
+    std::vector<pft_ct*> S;
+    for (FtDoc* d : docs) {
+        S.push_back(d->score);
+        ft_release_work(c, d);
+        d->work.clear();
+    }
+    op_rescale_batch(c, S.data(), (int)S.size(), S.data());
+}
+
+// BEGIN, diagonal packing: Q = sum_k rot(v, k) D_k, documents in chunks that bound the memory
+// of the rotated copies.
+static void ft_begin_diag(pft_ctx* c, const pft_ft_model* M, const std::vector<FtDoc*>& docs) {
+    const int cols = M->n;
+    const size_t limb = c->n;
+    std::vector<int32_t> hsteps;
+    for (int k = 1; k < cols; k++) hsteps.push_back(k);
+    for (FtDoc* d : docs) ft_init_work(c, d, 1, d->v[0]->scale * M->H[0]->scale);
+    for (auto& kv : docs_by_level(docs)) {
+        const int l = kv.first;
+        const std::vector<FtDoc*>& G = kv.second;
+        const size_t per_doc = (size_t)(cols - 1) * 2 * l * limb * 8;
+        const size_t chunk = std::max<size_t>(1, std::min<size_t>(G.size(), ((size_t)16 << 30) / per_doc));
+        for (size_t b0 = 0; b0 < G.size(); b0 += chunk) {
+            const size_t b1 = std::min(G.size(), b0 + chunk);
+            std::vector<pft_ct> R((b1 - b0) * (cols - 1));
+            struct CleanR {
+                pft_ctx* c;
+                std::vector<pft_ct>* T;
+                ~CleanR() {
+                    for (auto& x : *T) dfree(c, x.data);
+                }
+            } cleanR{c, &R};
+            for (auto& x : R) x.ctx = c;
+            for (size_t b = b0; b < b1; b++) {
+                std::vector<pft_ct*> outs;
+                for (int k = 0; k < cols - 1; k++) outs.push_back(&R[(b - b0) * (cols - 1) + k]);
+                op_rotate_hoisted(c, G[b]->v[0], hsteps.data(), cols - 1, outs.data());
+            }
+            std::vector<const u64*> A, Bv;
+            std::vector<u64*> O;
+            for (int k = 0; k < cols; k++) Bv.push_back(M->H[k]->data);
+            for (size_t b = b0; b < b1; b++)
+                for (int pol = 0; pol < 2; pol++) {
+                    A.push_back(G[b]->v[0]->data + (size_t)pol * l * limb);
+                    for (int k = 1; k < cols; k++)
+                        A.push_back(R[(b - b0) * (cols - 1) + k - 1].data + (size_t)pol * l * limb);
+                    O.push_back(G[b]->W[0].data + (size_t)pol * l * limb);
+                }
+            Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
+            ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l,
+                   c->stream);
+        }
+    }
+}
+
+// MID, diagonal packing: rescale Q, S = Q * P into the score; later steps act on the score.
+static void ft_mid_diag(pft_ctx* c, const pft_ft_model* M, const std::vector<FtDoc*>& docs) {
+    std::vector<pft_ct*> Q;
+    for (FtDoc* d : docs) Q.push_back(&d->W[0]);
+    op_rescale_batch(c, Q.data(), (int)Q.size(), Q.data());
+    const pft_pt* P = M->O[0];
+    std::vector<PolyRef> ra, rb, ro;
+    for (FtDoc* d : docs) {
+        const int l1 = d->W[0].level;
+        ensure_ct(c, d->score, l1);
+        d->score->scale = d->W[0].scale * P->scale;
+        for (int pol = 0; pol < 2; pol++) {
+            ra.push_back(cpoly(d->W[0].data, l1, c->n, pol));
+            rb.push_back(ref(P->data, l1));
+            ro.push_back(cpoly(d->score->data, l1, c->n, pol));
+        }
+    }
+    ew(c, EwOp::Mul, ra, rb, ro);
+    for (FtDoc* d : docs) {
+        ft_release_work(c, d);
+        d->work.assign(1, d->score);
+    }
+}
+
+void ft_stage(pft_ctx* c, const pft_ft_model* M, const FtStage& st, const std::vector<FtDoc*>& docs) {
+    if (docs.empty()) return;
+    switch (st.kind) {
+        case FT_BEGIN:
+            if (M->variant == 0) ft_begin_columns(c, M, docs);
+            else ft_begin_diag(c, M, docs);
+            break;
+        case FT_ROT: {
+            std::vector<pft_ct*> T;
+            for (FtDoc* d : docs)
+                for (pft_ct* x : d->work) T.push_back(x);
+            rot_accumulate(c, T, st.g);
+            break;
+        }
+        case FT_MID:
+            NEED(M->variant == 1, PFT_ERR_ARG, "internal: MID stage of the Fig. 3 sequence");
+            ft_mid_diag(c, M, docs);
+            break;
+        case FT_FINISH:
+            if (M->variant == 0) {
+                ft_finish_columns(c, M, docs);
+            } else {
+                std::vector<pft_ct*> S;
+                for (FtDoc* d : docs) {
+                    S.push_back(d->score);
+                    d->work.clear();
+                }
+                op_rescale_batch(c, S.data(), (int)S.size(), S.data());
+            }
+            break;
+        default:
+            fail(PFT_ERR_ARG, "internal: unknown stage");
+    }
+}
+
+// The whole sequence for B documents at once (each stage is one batched call).
+static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int chunks_in, int B,
+                           pft_ct* const* scores) {
+    NEED(M && M->ctx == c, PFT_ERR_ARG, "model from another context");
+    NEED(B >= 0 && (B == 0 || (v && scores)), PFT_ERR_ARG, "bad arguments");
+    std::vector<std::unique_ptr<FtDoc>> docs;
+    std::vector<FtDoc*> dp;
+    for (int b = 0; b < B; b++) {
+        ft_check_doc(c, M, v + (size_t)b * chunks_in, chunks_in);
+        NEED(scores[b], PFT_ERR_ARG, "null output");
+        docs.emplace_back(new FtDoc());
+        FtDoc* d = docs.back().get();
+        d->v = v + (size_t)b * chunks_in;
+        d->l = d->v[0]->level;
+        d->score = scores[b];
+        dp.push_back(d);
+    }
+    for (const FtStage& st : ft_program(c, M)) ft_stage(c, M, st, dp);
 }
 
 // ---- allocation-free rescale ---------------------------------------------------------------
@@ -1647,6 +1553,52 @@ int pft_rescale(pft_ctx* c, const pft_ct* a, pft_ct* out) {
 int pft_rotate(pft_ctx* c, const pft_ct* a, int32_t step, pft_ct* out) {
     return guard(c, [&] { op_rotate_batch(c, &a, 1, step, &out); });
 }
+int pft_dot_plain_batch(pft_ctx* c, const pft_ct* const* cts, const pft_pt* const* pts, int K, int n_out,
+                        int pts_shared, pft_ct* const* outs) {
+    return guard(c, [&] {
+        NEED(c && cts && pts && outs && K >= 1 && n_out >= 0, PFT_ERR_ARG, "bad arguments");
+        if (n_out == 0) return;
+        const int l = cts[0]->level;
+        const size_t limb = c->n;
+        std::vector<const u64*> A, Bv;
+        std::vector<u64*> O;
+        for (int k = 0; k < (pts_shared ? K : K * n_out); k++) {
+            check_pt(pts[k]);
+            NEED(pts[k]->level == l, PFT_ERR_LEVEL_MISMATCH, "plaintexts must sit at the ciphertexts' level");
+        }
+        std::vector<double> sc(n_out);
+        for (int o = 0; o < n_out; o++) {
+            for (int k = 0; k < K; k++) {
+                const pft_ct* x = cts[(size_t)o * K + k];
+                check_ct(x);
+                NEED(x->level == l, PFT_ERR_LEVEL_MISMATCH, "all ciphertexts must share one level");
+                const double s = x->scale * pts[pts_shared ? k : (size_t)o * K + k]->scale;
+                if (k == 0) sc[o] = s;
+                NEED(s == sc[o], PFT_ERR_SCALE_MISMATCH, "products of one output must share one scale");
+            }
+            NEED(outs[o], PFT_ERR_ARG, "null output");
+            for (int k = 0; k < K; k++) NEED(outs[o] != cts[(size_t)o * K + k], PFT_ERR_ARG, "output aliases an input");
+        }
+        for (int o = 0; o < n_out; o++) {
+            ensure_ct(c, outs[o], l);
+            outs[o]->scale = sc[o];
+        }
+        if (pts_shared)
+            for (int k = 0; k < K; k++) Bv.push_back(pts[k]->data);
+        for (int o = 0; o < n_out; o++)
+            for (int pol = 0; pol < 2; pol++) {
+                for (int k = 0; k < K; k++) {
+                    A.push_back(cts[(size_t)o * K + k]->data + (size_t)pol * l * limb);
+                    if (!pts_shared) Bv.push_back(pts[(size_t)o * K + k]->data);
+                }
+                O.push_back(outs[o]->data + (size_t)pol * l * limb);
+            }
+        Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
+        ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), K, pts_shared != 0, l,
+               c->stream);
+    });
+}
+
 int pft_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs) {
     return guard(c, [&] { op_rotate_hoisted(c, a, steps, n, outs); });
 }

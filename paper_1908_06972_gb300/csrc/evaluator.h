@@ -1,0 +1,219 @@
+// Handles of the evaluator and the host-side helpers shared by its translation units
+// (the operations in ckks.cu, the request server in serve.cu).
+#pragma once
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pft_internal.h"
+
+using namespace pft;
+
+// ---- handles ---------------------------------------------------------------------------
+struct pft_ctx {
+    pft_params prm;
+    int logn = 0, n = 0, L = 0, k = 0, alpha = 0, beta_max = 0;
+    std::vector<u64> primes;  // q_0..q_{L-1}, p_0..p_{k-1}
+    pft_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    DevTables tabs{};
+    std::vector<void*> owned;  // table buffers
+    // basis-conversion tables: modup[(l-1) * beta_max + j], moddown[l-1] (device offsets)
+    std::vector<const u64*> modup_tab, moddown_tab;
+    const u64* moddown_consts = nullptr;           // [L][3] {0, P^-1, shoup}
+    std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {0, p^-1, shoup}
+    std::vector<const u64*> pmodq_consts;          // digit j -> [alpha][3] {0, P mod q_m, shoup}
+    std::vector<u64> P_mod_q;
+    std::vector<u32> cdt;
+    // keys
+    bool have_sk = false;
+    u64* s_ntt = nullptr;  // [L+k][N]
+    std::vector<i64> s_coeff;
+    u64* pk = nullptr;  // [2][L][N]  (b, a)
+    std::map<u32, u64*> keys;
+};
+
+struct pft_ct {
+    pft_ctx* ctx = nullptr;
+    u64* data = nullptr;
+    size_t cap = 0;  // words
+    int level = 0;
+    double scale = 1.0;
+};
+struct pft_pt {
+    pft_ctx* ctx = nullptr;
+    u64* data = nullptr;
+    size_t cap = 0;
+    int level = 0;
+    double scale = 1.0;
+};
+struct pft_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+struct pft_ft_model {
+    pft_ctx* ctx = nullptr;
+    int m = 0, n = 0, c = 0, chunks = 0, level = 0;
+    int variant = 0;            // 0: Fig. 3 packing; 1: diagonal packing (rotation-light)
+    std::vector<pft_pt*> H, O;  // owned copies (variant 1: H = diagonals D_k, O = {P})
+};
+
+// ---- memory --------------------------------------------------------------------------
+inline void* dalloc(pft_ctx* c, size_t bytes) {
+    if (bytes == 0) return nullptr;
+    void* p = nullptr;
+    if (c->has_alloc) {
+        p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+        if (e != cudaSuccess) p = nullptr;
+    }
+    if (!p) fail(PFT_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    return p;
+}
+inline void dfree(pft_ctx* c, void* p) {
+    if (!p) return;
+    if (c->has_alloc) c->alloc.free(p, (void*)c->stream, c->alloc.user);
+    else cudaFreeAsync(p, c->stream);
+}
+struct Scratch {
+    pft_ctx* c;
+    void* p;
+    Scratch(pft_ctx* c_, size_t bytes) : c(c_), p(dalloc(c_, bytes)) {}
+    ~Scratch() { dfree(c, p); }
+    u64* u() const { return (u64*)p; }
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+};
+template <class T>
+inline T* upload(pft_ctx* c, Scratch& s, const std::vector<T>& v) {
+    PFT_CUDA(cudaMemcpyAsync(s.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return (T*)s.p;
+}
+inline void ensure_ct(pft_ctx* c, pft_ct* ct, int level) {
+    const size_t need = (size_t)2 * level * c->n;
+    if (ct->cap < need) {
+        dfree(c, ct->data);
+        ct->data = nullptr;
+        ct->cap = 0;
+        ct->data = (u64*)dalloc(c, need * 8);
+        ct->cap = need;
+    }
+    ct->level = level;
+}
+inline void ensure_pt(pft_ctx* c, pft_pt* pt, int level) {
+    const size_t need = (size_t)level * c->n;
+    if (pt->cap < need) {
+        dfree(c, pt->data);
+        pt->data = nullptr;
+        pt->cap = 0;
+        pt->data = (u64*)dalloc(c, need * 8);
+        pt->cap = need;
+    }
+    pt->level = level;
+}
+
+// ---- polynomial references ------------------------------------------------------------
+inline PolyRef ref(u64* p, int nlimbs, int first = 0, int split = -1, int base2 = 0) {
+    PolyRef r;
+    r.ptr = p;
+    r.nlimbs = (uint16_t)nlimbs;
+    r.first = (uint16_t)first;
+    r.split = (uint16_t)(split < 0 ? nlimbs : split);
+    r.base2 = (uint16_t)base2;
+    return r;
+}
+inline PolySet mkset(const std::vector<PolyRef>& v, size_t a, size_t b) {
+    PolySet s;
+    s.count = (int)(b - a);
+    s.max_limbs = 0;
+    for (size_t i = a; i < b; i++) {
+        s.p[i - a] = v[i];
+        s.max_limbs = std::max<int>(s.max_limbs, v[i].nlimbs);
+    }
+    return s;
+}
+template <class F>
+inline void chunks(size_t n, F f) {
+    for (size_t i = 0; i < n; i += kMaxSet) f(i, std::min(n, i + (size_t)kMaxSet));
+}
+inline void ntt_fwd(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
+    chunks(out.size(), [&](size_t a, size_t b) { ntt_forward(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
+}
+inline void ntt_inv(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
+    chunks(out.size(), [&](size_t a, size_t b) { ntt_inverse(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
+}
+inline void ew(pft_ctx* c, EwOp op, const std::vector<PolyRef>& a, const std::vector<PolyRef>& b,
+               const std::vector<PolyRef>& out) {
+    chunks(out.size(), [&](size_t x, size_t y) {
+        ew_binary(c->tabs, op, mkset(a, x, y), mkset(b.empty() ? a : b, x, y), mkset(out, x, y), c->stream);
+    });
+}
+inline void subscale(pft_ctx* c, const std::vector<PolyRef>& x, const std::vector<PolyRef>* y,
+                     const std::vector<PolyRef>* acc, const std::vector<PolyRef>& out, const u64* consts) {
+    chunks(out.size(), [&](size_t a, size_t b) {
+        PolySet sx = mkset(x, a, b), so = mkset(out, a, b);
+        PolySet sy, sa;
+        if (y) sy = mkset(*y, a, b);
+        if (acc) sa = mkset(*acc, a, b);
+        sub_scale(c->tabs, sx, y ? &sy : nullptr, acc ? &sa : nullptr, so, consts, c->stream);
+    });
+}
+// the two polynomials of a ciphertext buffer [2][l][N]
+inline PolyRef cpoly(u64* data, int l, int n, int pol) { return ref(data + (size_t)pol * l * n, l); }
+
+// ---- the C ABI guard ------------------------------------------------------------------
+template <class F>
+inline int guard(pft_ctx* c, F f) {
+    try {
+        f();
+        return PFT_OK;
+    } catch (const Error& e) {
+        if (c) c->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host out of memory";
+        return PFT_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (c) c->err = e.what();
+        return PFT_ERR_ARG;
+    }
+}
+#define NEED(cond, code, msg) \
+    do {                      \
+        if (!(cond)) fail(code, msg); \
+    } while (0)
+inline void check_ct(const pft_ct* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty ciphertext"); }
+inline void check_pt(const pft_pt* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty plaintext"); }
+
+// ---- fastText inference as a sequence of stages (Sec. 3.1) ---------------------------------
+// One document in flight: its inputs, its working ciphertexts and its score.  A stage runs
+// over any set of documents of one model, whatever their levels (3 <= l <= model level; a
+// model encoded at level L serves level l through the first l limbs of its plaintexts).
+struct FtDoc {
+    const pft_ct* const* v = nullptr;  // model chunks (Fig. 3) or 1 (diagonal) input ciphertexts
+    int l = 0;                          // level of the inputs
+    std::vector<pft_ct> W;              // the n columns (Fig. 3) or Q (diagonal)
+    std::vector<pft_ct*> work;          // ciphertexts the next rotate-and-sum step acts on
+    pft_ct* score = nullptr;
+    FtDoc() = default;
+    FtDoc(const FtDoc&) = delete;
+    FtDoc& operator=(const FtDoc&) = delete;
+    ~FtDoc() {
+        for (auto& x : W) dfree(x.ctx, x.data);
+    }
+};
+enum FtStageKind { FT_BEGIN = 0, FT_ROT = 1, FT_MID = 2, FT_FINISH = 3 };
+struct FtStage {
+    int kind;
+    u32 g;  // Galois element of FT_ROT
+};
+// Stages of one inference with model M, in order.
+std::vector<FtStage> ft_program(pft_ctx* c, const pft_ft_model* M);
+// Checks one document's inputs against the model and the keys its program needs.
+void ft_check_doc(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int n_chunks);
+// Runs one stage for every document of `docs` (all at the same stage of the same model).
+void ft_stage(pft_ctx* c, const pft_ft_model* M, const FtStage& st, const std::vector<FtDoc*>& docs);

@@ -232,6 +232,32 @@ def test_total_sum_and_fasttext_n12(p1):
 
 
 # ---- N = 2^16 ---------------------------------------------------------------------------------
+def test_ops_bit_exact_n15(gpu):
+    """N = 2^15 (the smaller ring of the serving workload): 60 + 3 x 40-bit primes, two
+    special primes, digits of two primes; generic two-pass transform (stages 8 + 7)."""
+    p = Pair(gpu, 15, 4, 2, 2, rot_steps=[1, -3])
+    try:
+        o, pf, ctx = p.orc, p.pft, p.ctx
+        assert np.array_equal(pf.pft_key_export(ctx, 0), o.keys[0])
+        za, zb = synth.slots(31, 2048), synth.slots(32, 2048)
+        for lvl in (4, 3):
+            a = o.encrypt_sk(o.encode(za, level=lvl), 40 + lvl)
+            b = o.encrypt_pk(o.encode(zb, level=lvl), 50 + lvl)
+            ga, gb = p.ct(a), p.ct(b)
+            m = p.empty()
+            pf.pft_mul_relin(ctx, ga, gb, m)
+            mo = o.mul_relin(a, b)
+            p.assert_equal(m, mo, "mul_relin n15 l=%d" % lvl)
+            r = p.empty()
+            pf.pft_rescale(ctx, m, r)
+            p.assert_equal(r, o.rescale(mo), "rescale n15 l=%d" % lvl)
+            rt = p.empty()
+            pf.pft_rotate(ctx, ga, -3, rt)
+            p.assert_equal(rt, o.rotate(a, -3), "rotate n15 l=%d" % lvl)
+    finally:
+        p.close()
+
+
 def test_ops_bit_exact_n16(p16):
     o, pf, ctx = p16.orc, p16.pft, p16.ctx
     za, zb = synth.slots(1, 4096), synth.slots(2, 4096)
