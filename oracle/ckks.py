@@ -61,6 +61,16 @@ class Plaintext:
         return self.m.shape[0]
 
 
+def round_half_away(x):
+    """The integer nearest to the double x, ties away from zero (exact for every double)."""
+    x = float(x)
+    f = math.floor(x)
+    d = x - f  # exact: x and floor(x) are within one unit of each other's exponent range
+    if d > 0.5 or (d == 0.5 and x > 0):
+        return int(f) + 1
+    return int(f)
+
+
 def galois_element(step, n):
     """g = 5^step mod 2N (5 has order N/2 modulo 2N, so negative steps wrap)."""
     return pow(5, step % (n // 2), 2 * n)
@@ -244,6 +254,54 @@ class Oracle:
         d1 = C.vadd(C.polymul(a.c[0], b.c[1], q), C.polymul(a.c[1], b.c[0], q), q)
         d2 = C.polymul(a.c[1], b.c[1], q)
         return d0, d1, d2
+
+    # ---- level and scale management (used by the training step) --------------------------
+    def drop_level(self, ct, level):
+        """The same message with the primes above `level` dropped (exact: the residues
+        modulo q_0..q_{level-1} of the same integers)."""
+        assert 1 <= level <= ct.level
+        return Ciphertext(ct.c[:, :level].copy(), ct.scale)
+
+    def set_scale(self, ct, scale):
+        """Relabel: the same integers read at another scale (message times old/new)."""
+        return Ciphertext(ct.c.copy(), scale)
+
+    def add_const(self, ct, value):
+        """Adds `value` to every slot: the constant polynomial round(value * scale) added to c0."""
+        q = self._q(ct)
+        k = round_half_away(value * ct.scale)
+        c = ct.c.copy()
+        for i, qi in enumerate(q):
+            c[0, i, 0] = np.uint64((int(c[0, i, 0]) + k) % qi)
+        return Ciphertext(c, ct.scale)
+
+    def mul_const(self, ct, value, const_scale):
+        """Multiplies every slot by `value`: both polynomials times the integer
+        round(value * const_scale); the scale is multiplied by const_scale."""
+        q = self._q(ct)
+        k = round_half_away(value * const_scale)
+        kk = [k % qi for qi in q]
+        return Ciphertext(np.stack([C.vscale(ct.c[i], kk, q) for i in range(2)]), ct.scale * const_scale)
+
+    def tensor_sum(self, pairs):
+        """sum_k tensor(a_k, b_k) (three polynomials) and its scale; all products share one
+        level and one scale."""
+        a0, b0 = pairs[0]
+        q = self._q(a0)
+        sc = a0.scale * b0.scale
+        acc = [np.zeros((a0.level, self.N), np.uint64) for _ in range(3)]
+        for a, b in pairs:
+            assert a.level == a0.level and b.level == a0.level and a.scale * b.scale == sc
+            for i, d in enumerate(self.tensor(a, b)):
+                acc[i] = C.vadd(acc[i], d, q)
+        return acc, sc
+
+    def relin(self, d, scale):
+        """(d0, d1, d2) -> (d0 + u0, d1 + u1) with u0 + u1 s ~= d2 s^2 (relinearisation key)."""
+        d0, d1, d2 = d
+        q = self.q[: d0.shape[0]]
+        k0, k1 = self.keyswitch(d2, 0)
+        return Ciphertext(np.stack([C.vadd(d0, k0, q), C.vadd(d1, k1, q)]), scale)
 
     def modup_digit(self, d, j):
         """Digit j of d (rows at level l) extended to the basis q_0..q_{l-1}, p_0..p_{k-1}.

@@ -113,3 +113,102 @@ def encrypted_scores_diag(orc, v_ct, D_pts, P_pt):
         S = orc.add(S, orc.rotate(S, s))
         s *= 2
     return orc.rescale(S)
+
+
+# ---- minibatch training (Sec. 4.2, Algorithm 5) -----------------------------------------------
+# Forward per document: h = v H, s = h O (Algorithm 1 with encrypted weights, HMUL for
+# HMULPLAIN).  The softmax is replaced by the paper's minimax polynomial
+#   P(s) = s^2/8 + s/2 + 1/4,
+# and the loss is the polynomial whose gradient in s is P(s) - y:
+#   L = sum_b sum_c [ s^3/24 + s^2/4 + s/4 - y s ]   (degree 3).
+# Gradients: g = P(s) - y,  dL/dO = sum_b h^T g,  dL/dH = sum_b v^T (g O^T).
+# Minibatch SGD (Algorithm 5): H <- H - eta dH, O <- O - eta dO.
+
+def softmax_poly(s):
+    """The paper's minimax approximation of softmax, P(s) = s^2/8 + s/2 + 1/4."""
+    s = np.asarray(s, np.float64)
+    return s * s / 8.0 + s / 2.0 + 0.25
+
+
+def train_loss_plain(V, Y, H, O):
+    """L(H, O) in FP64 for documents V [B][m] and one-hot labels Y [B][c]."""
+    S = (np.asarray(V, np.float64) @ H) @ O
+    return float(np.sum(S ** 3 / 24.0 + S ** 2 / 4.0 + S / 4.0 - np.asarray(Y, np.float64) * S))
+
+
+def train_grads_plain(V, Y, H, O):
+    """(dL/dH, dL/dO) in FP64."""
+    V = np.asarray(V, np.float64)
+    Hh = V @ H                        # [B][n]
+    S = Hh @ O                        # [B][c]
+    G = softmax_poly(S) - np.asarray(Y, np.float64)
+    return V.T @ (G @ O.T), Hh.T @ G
+
+
+# Encrypted step.  Layout as for inference: H_j holds column j of H over the vocabulary
+# slots (one ciphertext per column, m <= t), O_j holds row j of O in slots 0..c-1, v_b is the
+# document, and the client sends w_b = y_b - 1/4 on the c class slots (zero elsewhere), so the
+# constant term of P never has to be masked on the server.  All constants the server adds
+# are constant polynomials (every slot): with u = s + 2, u^2/8 - 1/2 = s^2/8 + s/2.
+#   forward  h_bj = Rescale(TotalSum(Relin(v_b x H_j)))                      level l0-1
+#            s_b  = Rescale(Relin(sum_j h_bj x O_j))                        level l0-2
+#            U_b  = Rescale(Relin(u_b x u_b)), u_b = s_b + 2                level l0-3
+#            g_b  = [U_b read at 8x its scale] - 1/2 - w_b   (= P(s_b) - y_b)
+#   backward dO_j = Rescale(Relin(sum_b h_bj x g_b))                        level l0-4
+#            e_bj = Rescale(TotalSum(Relin(g_b x O_j)))                     level l0-4
+#            dH_j = Rescale(Relin(sum_b v_b x e_bj))                        level l0-5
+#   update   O_j <- O_j - Align(dO_j), H_j <- H_j - Align(dH_j):  Align multiplies by
+#            eta at the constant scale that brings the result, after one rescale, back to
+#            the model's own scale (then read at exactly that scale).
+# Operands at a higher level than needed are dropped to the lower level first; products
+# summed before one relinearisation share their scale.
+
+def train_label_spec(orc, level, sc_v, sc_H, sc_O):
+    """Level and scale at which the client encrypts w_b for a model at `level`."""
+    q = orc.q
+    sh = sc_v * sc_H / float(q[level - 1])
+    ss = sh * sc_O / float(q[level - 2])
+    su = ss * ss / float(q[level - 3])
+    return level - 3, 8.0 * su
+
+
+def _align(orc, x, eta, target):
+    c_sc = target * float(orc.q[x.level - 1]) / x.scale
+    return orc.set_scale(orc.rescale(orc.mul_const(x, eta, c_sc)), target)
+
+
+def encrypted_train_step(orc, v_cts, w_cts, H_cts, O_cts, eta):
+    """One minibatch step on the oracle.  Returns (dH [n], dO [n], H' [n], O' [n]); with
+    eta == 0 the model is returned unchanged."""
+    B, n = len(v_cts), len(H_cts)
+    l0 = H_cts[0].level
+    assert all(x.level == l0 for x in v_cts + H_cts) and all(o.level == l0 - 1 for o in O_cts)
+    h = [[None] * n for _ in range(B)]
+    g = []
+    for b in range(B):
+        for j in range(n):
+            t = orc.relin(*orc.tensor_sum([(v_cts[b], H_cts[j])]))
+            h[b][j] = orc.rescale(orc.total_sum(t))
+        s = orc.rescale(orc.relin(*orc.tensor_sum([(h[b][j], O_cts[j]) for j in range(n)])))
+        u = orc.add_const(s, 2.0)
+        U = orc.rescale(orc.relin(*orc.tensor_sum([(u, u)])))
+        U = orc.add_const(orc.set_scale(U, 8.0 * U.scale), -0.5)
+        g.append(orc.sub(U, w_cts[b]))
+    lg = l0 - 3
+    dO = [orc.rescale(orc.relin(*orc.tensor_sum([(orc.drop_level(h[b][j], lg), g[b]) for b in range(B)])))
+          for j in range(n)]
+    dH = []
+    for j in range(n):
+        Oj = orc.drop_level(O_cts[j], lg)
+        e = [orc.rescale(orc.total_sum(orc.relin(*orc.tensor_sum([(g[b], Oj)])))) for b in range(B)]
+        dH.append(orc.rescale(orc.relin(*orc.tensor_sum(
+            [(orc.drop_level(v_cts[b], e[b].level), e[b]) for b in range(B)]))))
+    if eta == 0:
+        return dH, dO, list(H_cts), list(O_cts)
+    O_new, H_new = [], []
+    for j in range(n):
+        a = _align(orc, dO[j], eta, O_cts[j].scale)
+        O_new.append(orc.sub(orc.drop_level(O_cts[j], a.level), a))
+        a = _align(orc, dH[j], eta, H_cts[j].scale)
+        H_new.append(orc.sub(orc.drop_level(H_cts[j], a.level), a))
+    return dH, dO, H_new, O_new
