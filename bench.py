@@ -254,6 +254,10 @@ def run_gpu(args):
     if args.fasttext:
         ft = fasttext_measure(pft, torch, max(1, args.steps // 2), 1)
 
+    tr = None
+    if args.train > 0:
+        tr = train_measure(pft, torch, args.train, args.train_plain_docs)
+
     sv = None
     if args.serve > 0:
         sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_low_load)
@@ -276,7 +280,7 @@ def run_gpu(args):
            "gpu_launches": int(all_launches), "roofline": roof,
            "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
                         "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
-           "fasttext": ft, "serving": sv}
+           "fasttext": ft, "serving": sv, "training": tr}
     if rank == 0:
         print(json.dumps(out))
     for h in A + B + C:
@@ -532,6 +536,160 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, seed=31):
     return out
 
 
+# ---- encrypted minibatch training (Sec. 4.2, Algorithm 5) -----------------------------------------
+TR_M, TR_N, TR_C, TR_L, TR_ETA = 8192, 32, 4, 30, 0.25
+TR_WORKLOAD = ("encrypted fastText training step: vocab 8192 (one N=2^16 ciphertext), dim 32, 4 classes, "
+               "Zipf(1.1) documents, one-hot labels; forward with the paper's softmax polynomial, homomorphic "
+               "backward, one SGD update; chain 60 + 29x40 bits + 4 special (60 bits), digits of 4, model at level 30")
+
+
+def fp64_train_grads(V, Y, H, O):
+    """Gradients of L = sum [s^3/24 + s^2/4 + s/4 - y s], s = V H O, in FP64 (the reported
+    accuracy check): g = s^2/8 + s/2 + 1/4 - y, dH = V^T (g O^T), dO = (V H)^T g."""
+    Hh = V @ H
+    S = Hh @ O
+    G = S * S / 8 + S / 2 + 0.25 - Y
+    return V.T @ (G @ O.T), Hh.T @ G
+
+
+def train_measure(pft, torch, n_docs, plain_docs):
+    from paper_1908_06972_gb300 import synth
+
+    sc = 2.0 ** 40
+    ctx = pft.pft_ctx_create(LOGN, TR_L, K_SP, ALPHA, 60, 40, 60, sc, SEED)
+    pft.pft_keygen(ctx, [1 << i for i in range(LOGN - 1)], True)
+    t = (1 << LOGN) // 2
+    handles = []
+
+    def enc(z, level, scale, nonce):
+        pt = pft.pft_encode(ctx, z, scale, level)
+        h = pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, nonce)
+        pft.pft_pt_destroy(pt)
+        handles.append(h)
+        return h
+
+    def new():
+        h = pft.pft_ct_create(ctx)
+        handles.append(h)
+        return h
+
+    def dec(h, k):
+        pt = pft.pft_decrypt(ctx, h)
+        z = pft.pft_decode(ctx, pt, k).real
+        pft.pft_pt_destroy(pt)
+        return z
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    H, O = synth.fasttext_weights(61, TR_M, TR_N, TR_C)
+    V = synth.documents(62, TR_M, n_docs)
+    Y = np.eye(TR_C)[np.random.default_rng(63).integers(0, TR_C, n_docs)]
+    Hc = [enc(H[:, j], TR_L, sc, 10 + j) for j in range(TR_N)]
+    Oc = [enc(O[j], TR_L - 1, sc, 100 + j) for j in range(TR_N)]
+    model = pft.pft_ft_enc_model_create(ctx, Hc, Oc, TR_M, TR_N, TR_C)
+    dl, ll, ls = pft.pft_fasttext_train_spec(ctx, model, sc)
+    docs = [enc(V[b], dl, sc, 1000 + b) for b in range(n_docs)]
+    labels = [enc(Y[b] - 0.25, ll, ls, 2000 + b) for b in range(n_docs)]
+    gH = [new() for _ in range(TR_N)]
+    gO = [new() for _ in range(TR_N)]
+    warm = pft.pft_ft_enc_model_create(ctx, Hc, Oc, TR_M, TR_N, TR_C)
+    pft.pft_fasttext_train_step(ctx, warm, docs[:2], labels[:2], TR_ETA, gH, gO)
+    pft.pft_ft_enc_model_destroy(warm)
+    t_step = timed(lambda: pft.pft_fasttext_train_step(ctx, model, docs, labels, TR_ETA, gH, gO))
+    ref_H, ref_O = fp64_train_grads(V, Y, H, O)
+    got_H = np.stack([dec(gH[j], TR_M) for j in range(TR_N)], 1)
+    got_O = np.stack([dec(gO[j], TR_C) for j in range(TR_N)])
+    err = float(max(np.max(np.abs(got_H - ref_H)), np.max(np.abs(got_O - ref_O))))
+    lvH, lvO = pft.pft_ft_enc_model_levels(model)
+    pft.pft_ft_enc_model_destroy(model)
+
+    # plain path: one library call per operation per ciphertext (products relinearised one by
+    # one), on `plain_docs` documents, then the same update
+    def plain(nd):
+        n = TR_N
+        accO, accH = [None] * n, [None] * n
+        tmp = new()
+        for b in range(nd):
+            v, w = docs[b], labels[b]
+            hs = []
+            for j in range(n):
+                T = new()
+                pft.pft_mul_relin(ctx, v, Hc[j], T)
+                st = 1
+                while st < t:
+                    pft.pft_rotate(ctx, T, st, tmp)
+                    pft.pft_add(ctx, T, tmp, T)
+                    st *= 2
+                pft.pft_rescale(ctx, T, T)
+                hs.append(T)
+            S = new()
+            for j in range(n):
+                pft.pft_mul_relin(ctx, hs[j], Oc[j], tmp if j else S)
+                if j:
+                    pft.pft_add(ctx, S, tmp, S)
+            pft.pft_rescale(ctx, S, S)
+            U = new()
+            pft.pft_add_const(ctx, S, 2.0, U)
+            pft.pft_mul_relin(ctx, U, U, U)
+            pft.pft_rescale(ctx, U, U)
+            pft.pft_ct_set_scale(U, 8.0 * pft.pft_ct_scale(U))
+            pft.pft_add_const(ctx, U, -0.5, U)
+            g = new()
+            pft.pft_sub(ctx, U, w, g)
+            lg = pft.pft_ct_level(g)
+            for j in range(n):
+                a, bb, P = new(), new(), new()
+                pft.pft_drop_level(ctx, hs[j], lg, a)
+                pft.pft_mul_relin(ctx, a, g, P)
+                if accO[j] is None:
+                    accO[j] = P
+                else:
+                    pft.pft_add(ctx, accO[j], P, accO[j])
+                pft.pft_drop_level(ctx, Oc[j], lg, bb)
+                E = new()
+                pft.pft_mul_relin(ctx, g, bb, E)
+                st = 1
+                while st < t:
+                    pft.pft_rotate(ctx, E, st, tmp)
+                    pft.pft_add(ctx, E, tmp, E)
+                    st *= 2
+                pft.pft_rescale(ctx, E, E)
+                vd, P2 = new(), new()
+                pft.pft_drop_level(ctx, v, pft.pft_ct_level(E), vd)
+                pft.pft_mul_relin(ctx, vd, E, P2)
+                if accH[j] is None:
+                    accH[j] = P2
+                else:
+                    pft.pft_add(ctx, accH[j], P2, accH[j])
+        for j in range(n):
+            pft.pft_rescale(ctx, accO[j], accO[j])
+            pft.pft_rescale(ctx, accH[j], accH[j])
+        return accH, accO
+
+    t_plain = None
+    if plain_docs > 0:
+        t_plain = timed(lambda: plain(plain_docs))
+    for h in handles:
+        pft.pft_ct_destroy(h)
+    pft.pft_ctx_destroy(ctx)
+    return {"workload": TR_WORKLOAD, "docs": n_docs, "unit": "s per training step",
+            "step_s": round(t_step, 3), "ms_per_doc": round(1e3 * t_step / n_docs, 2),
+            "rotations_per_doc": 2 * TR_N * (LOGN - 1),
+            "plain": None if t_plain is None else {
+                "docs_timed": plain_docs, "ms_per_doc": round(1e3 * t_plain / plain_docs, 2),
+                "step_s_extrapolated": round(t_plain / plain_docs * n_docs, 3),
+                "note": "one call per operation per ciphertext, products relinearised one by one, "
+                        "update not included"},
+            "max_abs_err_grad_vs_fp64": err, "model_levels_after": [lvH, lvO], "eta": TR_ETA}
+
+
 # ---- isolated kernel case (for ncu captures and burst rooflines) --------------------------------
 def run_case_ntt(args):
     """Forward + inverse transform of 16 polynomials x 30 limbs at N = 2^16 (252 MB > L2)."""
@@ -678,6 +836,8 @@ def main():
     ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
     ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
     ap.add_argument("--graph", type=int, default=1, help="also measure the step as one CUDA-graph launch")
+    ap.add_argument("--train", type=int, default=64, help="documents per encrypted training step (0: skip)")
+    ap.add_argument("--train-plain-docs", type=int, default=2, help="documents timed on the plain training path")
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
     ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")

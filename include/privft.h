@@ -220,6 +220,21 @@ int pft_rescale(pft_ctx* ctx, const pft_ct* a, pft_ct* out);
  * key switching with the rotation key of g.  Steps with no key -> PFT_ERR_NO_KEY. */
 int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
 
+/* ---- level and scale management (used by the training step of Sec. 4.2) ---
+ * The paper keeps every operand of a step at one level and scale; training mixes
+ * operands of different depths, which these exact operations reconcile. */
+/* The same message with the primes above `level` dropped (level <= a's level). */
+int pft_drop_level(pft_ctx* ctx, const pft_ct* a, int level, pft_ct* out);
+/* Adds `value` to every slot: the constant polynomial k = round(value * scale) (nearest
+ * integer, halfway cases away from zero; |value * scale| < 2^63) is added to c0. */
+int pft_add_const(pft_ctx* ctx, const pft_ct* a, double value, pft_ct* out);
+/* Multiplies every slot by `value`: both polynomials times k = round(value * const_scale);
+ * out scale = a's scale * const_scale (a following RESCALE divides it again). */
+int pft_mul_const(pft_ctx* ctx, const pft_ct* a, double value, double const_scale, pft_ct* out);
+/* Relabels ct's scale: the same integers now decrypt to old_scale / scale times the
+ * message (exact; multiplying the scale by 8 divides the message by 8). */
+int pft_ct_set_scale(pft_ct* ct, double scale);
+
 /* Sums of HMULPLAIN products (the inner step of Sec. 3.1's matrix products):
  * outs[o] = sum_{k<K} cts[o K + k] * pts[pts_shared ? k : o K + k], all at one level, the
  * products of one output at one scale; one launch for all outputs. */
@@ -387,8 +402,53 @@ int pft_server_clock(pft_server* srv, double* t);
 int pft_server_get_stats(pft_server* srv, pft_server_stats* stats);
 int pft_server_footprint(pft_server* srv, int ring, int level, size_t* bytes);
 
-/* Encrypted minibatch training step (Algorithm 5): not implemented yet. */
-int pft_fasttext_train_step(pft_ctx* ctx, pft_ft_model* model, const pft_ct* const* docs, int n_docs);
+/* ---- encrypted minibatch training (Sec. 4.2, Algorithm 5) ----------------
+ * Encrypted model: H_j = column j of H over the vocabulary slots (m <= t), at level l0;
+ * O_j = row j of O in slots 0..c-1, at level l0-1; one scale for all H_j, one for all O_j.
+ * Per step the client sends documents v_b (count vectors divided by w) at level l0 and
+ * labels w_b = y_b - 1/4 on the c class slots (one-hot y_b; the constant term of the
+ * softmax polynomial is folded into the label) at the level and scale
+ * pft_fasttext_train_spec gives.  The softmax is the paper's P(s) = s^2/8 + s/2 + 1/4;
+ * the loss is L = sum_b sum_c [s^3/24 + s^2/4 + s/4 - y s], whose gradient in s is
+ * P(s) - y.  Gradients: dO_j = sum_b h_bj g_b (level l0-4, slots 0..c-1), dH_j =
+ * sum_b v_b e_bj with e_bj = sum_c g_bc O_jc (level l0-5), g_b = P(s_b) - y_b.
+ * SGD: O_j <- O_j - eta dO_j (level l0-5), H_j <- H_j - eta dH_j (level l0-6), the
+ * model's scales unchanged.  Needs the relinearisation key and rotation keys 2^i,
+ * i < log2(t).  Six levels per step: a model at level l0 affords floor((l0-1)/6) steps. */
+typedef struct pft_ft_enc_model pft_ft_enc_model;
+typedef struct pft_ft_tape pft_ft_tape; /* forward state kept for the backward pass */
+/* Copies H[0..n-1] and O[0..n-1] into a new encrypted model. */
+int pft_ft_enc_model_create(pft_ctx* ctx, const pft_ct* const* H, const pft_ct* const* O, int m, int n, int c,
+                            pft_ft_enc_model** out);
+/* Copy of H_j (which = 0) or O_j (which = 1) into out. */
+int pft_ft_enc_model_get(pft_ctx* ctx, const pft_ft_enc_model* model, int which, int j, pft_ct* out);
+int pft_ft_enc_model_levels(const pft_ft_enc_model* model, int* level_H, int* level_O);
+int pft_ft_enc_model_destroy(pft_ft_enc_model* model);
+/* Level of the documents and level and scale of the labels for documents encrypted at
+ * input_scale (the scale the forward pass reaches at the softmax). */
+int pft_fasttext_train_spec(pft_ctx* ctx, const pft_ft_enc_model* model, double input_scale, int* doc_level,
+                            int* label_level, double* label_scale);
+/* Forward pass of B documents (levels >= 6): keeps h, s and g in *tape.  docs must stay
+ * alive until the tape is destroyed.  PFT_ERR_SCALE_MISMATCH if a label is not at the
+ * scale of pft_fasttext_train_spec. */
+int pft_fasttext_train_forward(pft_ctx* ctx, const pft_ft_enc_model* model, const pft_ct* const* docs,
+                               const pft_ct* const* labels, int B, pft_ft_tape** tape);
+/* Copy of the encrypted scores s_b of document b (slots 0..c-1, level l0-2). */
+int pft_ft_tape_score(pft_ctx* ctx, const pft_ft_tape* tape, int b, pft_ct* out);
+/* Backward pass (the adjoint of the forward): grad_H[j], grad_O[j] for j < n. */
+int pft_fasttext_train_backward(pft_ctx* ctx, const pft_ft_tape* tape, pft_ct* const* grad_H,
+                                pft_ct* const* grad_O);
+int pft_ft_tape_destroy(pft_ft_tape* tape);
+/* SGD update of the model with the gradients (eta = 0: no change). */
+int pft_fasttext_train_update(pft_ctx* ctx, pft_ft_enc_model* model, const pft_ct* const* grad_H,
+                              const pft_ct* const* grad_O, double eta);
+/* One whole step (forward, backward, update) over B documents, processed in tiles of
+ * documents so that only one tile's forward state is held at a time; results equal the
+ * three calls above.  grad_H / grad_O may be NULL (the gradients are then not returned).
+ * Levels >= 7 when eta != 0. */
+int pft_fasttext_train_step(pft_ctx* ctx, pft_ft_enc_model* model, const pft_ct* const* docs,
+                            const pft_ct* const* labels, int B, double eta, pft_ct* const* grad_H,
+                            pft_ct* const* grad_O);
 
 #ifdef __cplusplus
 }

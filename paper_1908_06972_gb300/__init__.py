@@ -98,6 +98,8 @@ def lib():
             "pft_rotate_batch": [vp, pp, i, c_int32, pp],
             "pft_rotate_hoisted": [vp, vp, POINTER(c_int32), i, pp],
             "pft_dot_plain_batch": [vp, pp, pp, i, i, i, pp],
+            "pft_drop_level": [vp, vp, i, vp], "pft_add_const": [vp, vp, d, vp],
+            "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
             "pft_graph_begin": [vp], "pft_graph_end": [vp, pp], "pft_graph_launch": [vp, vp],
@@ -108,7 +110,13 @@ def lib():
             "pft_ft_model_create_diag": [vp, POINTER(c_double), POINTER(c_double), i, i, i, i, pp],
             "pft_ft_model_import_diag": [vp, pp, vp, i, i, i, pp],
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
-            "pft_fasttext_train_step": [vp, vp, pp, i],
+            "pft_ft_enc_model_create": [vp, pp, pp, i, i, i, pp], "pft_ft_enc_model_get": [vp, vp, i, i, vp],
+            "pft_ft_enc_model_levels": [vp, ip, ip], "pft_ft_enc_model_destroy": [vp],
+            "pft_fasttext_train_spec": [vp, vp, d, ip, ip, POINTER(c_double)],
+            "pft_fasttext_train_forward": [vp, vp, pp, pp, i, pp], "pft_ft_tape_score": [vp, vp, i, vp],
+            "pft_fasttext_train_backward": [vp, vp, pp, pp], "pft_ft_tape_destroy": [vp],
+            "pft_fasttext_train_update": [vp, vp, pp, pp, d],
+            "pft_fasttext_train_step": [vp, vp, pp, pp, i, d, pp, pp],
             "pft_server_create": [pp, pp, i, c_size_t, pp], "pft_server_destroy": [vp],
             "pft_server_submit": [vp, i, u64, i, d, u64, c_uint64], "pft_server_step": [vp, ip],
             "pft_server_drain": [vp], "pft_server_poll": [vp, POINTER(pft_server_done), i, ip],
@@ -148,7 +156,10 @@ def exported_symbols():
             "pft_rotate_hoisted", "pft_ft_model_create_diag", "pft_ft_model_import_diag",
             "pft_dot_plain_batch", "pft_server_create", "pft_server_destroy", "pft_server_last_error",
             "pft_server_submit", "pft_server_step", "pft_server_drain", "pft_server_poll", "pft_server_clock",
-            "pft_server_get_stats", "pft_server_footprint"]
+            "pft_server_get_stats", "pft_server_footprint", "pft_drop_level", "pft_add_const", "pft_mul_const",
+            "pft_ct_set_scale", "pft_ft_enc_model_create", "pft_ft_enc_model_get", "pft_ft_enc_model_levels",
+            "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
+            "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update"]
 
 
 def _check(rc, ctx=None):
@@ -442,6 +453,22 @@ def pft_rotate_batch(ctx, a, step, out):
     _op("pft_rotate_batch", ctx, _arr(a), len(a), c_int32(step), _arr(out))
 
 
+def pft_drop_level(ctx, a, level, out):
+    _op("pft_drop_level", ctx, a, level, out)
+
+
+def pft_add_const(ctx, a, value, out):
+    _op("pft_add_const", ctx, a, float(value), out)
+
+
+def pft_mul_const(ctx, a, value, const_scale, out):
+    _op("pft_mul_const", ctx, a, float(value), float(const_scale), out)
+
+
+def pft_ct_set_scale(ct, scale):
+    _check(lib().pft_ct_set_scale(ct, float(scale)))
+
+
 def pft_dot_plain_batch(ctx, cts, pts, K, outs, pts_shared=False):
     _op("pft_dot_plain_batch", ctx, _arr(cts), _arr(pts), K, len(outs), 1 if pts_shared else 0, _arr(outs))
 
@@ -536,8 +563,61 @@ def pft_fasttext_infer_batch(ctx, model, v, n_chunks, scores):
     _op("pft_fasttext_infer_batch", ctx, model, _arr(v), n_chunks, len(scores), _arr(scores))
 
 
-def pft_fasttext_train_step(ctx, model, docs):
-    _op("pft_fasttext_train_step", ctx, model, _arr(docs), len(docs))
+# ---- encrypted training (Sec. 4.2, Algorithm 5) ---------------------------------------------------
+def pft_ft_enc_model_create(ctx, H, O, m, n, c):
+    out = c_void_p()
+    _check(lib().pft_ft_enc_model_create(ctx, _arr(H), _arr(O), m, n, c, ctypes.byref(out)), ctx)
+    return out
+
+
+def pft_ft_enc_model_get(ctx, model, which, j, out):
+    _op("pft_ft_enc_model_get", ctx, model, which, j, out)
+
+
+def pft_ft_enc_model_levels(model):
+    a, b = c_int(), c_int()
+    _check(lib().pft_ft_enc_model_levels(model, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def pft_ft_enc_model_destroy(model):
+    _check(lib().pft_ft_enc_model_destroy(model))
+
+
+def pft_fasttext_train_spec(ctx, model, input_scale):
+    """(document level, label level, label scale)."""
+    dl, ll, ls = c_int(), c_int(), c_double()
+    _check(lib().pft_fasttext_train_spec(ctx, model, float(input_scale), ctypes.byref(dl), ctypes.byref(ll),
+                                         ctypes.byref(ls)), ctx)
+    return dl.value, ll.value, ls.value
+
+
+def pft_fasttext_train_forward(ctx, model, docs, labels):
+    out = c_void_p()
+    _check(lib().pft_fasttext_train_forward(ctx, model, _arr(docs), _arr(labels), len(docs), ctypes.byref(out)), ctx)
+    return out
+
+
+def pft_ft_tape_score(ctx, tape, b, out):
+    _op("pft_ft_tape_score", ctx, tape, b, out)
+
+
+def pft_fasttext_train_backward(ctx, tape, grad_H, grad_O):
+    _op("pft_fasttext_train_backward", ctx, tape, _arr(grad_H), _arr(grad_O))
+
+
+def pft_ft_tape_destroy(tape):
+    _check(lib().pft_ft_tape_destroy(tape))
+
+
+def pft_fasttext_train_update(ctx, model, grad_H, grad_O, eta):
+    _op("pft_fasttext_train_update", ctx, model, _arr(grad_H), _arr(grad_O), float(eta))
+
+
+def pft_fasttext_train_step(ctx, model, docs, labels, eta, grad_H=None, grad_O=None):
+    gh = _arr(grad_H) if grad_H is not None else None
+    go = _arr(grad_O) if grad_O is not None else None
+    _op("pft_fasttext_train_step", ctx, model, _arr(docs), _arr(labels), len(docs), float(eta), gh, go)
 
 
 # ---- request server -----------------------------------------------------------------------

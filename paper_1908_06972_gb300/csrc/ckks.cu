@@ -183,7 +183,7 @@ static void build_tables(pft_ctx* c) {
 }
 
 
-static u32 galois_of(int n, int32_t step) {
+u32 galois_of(int n, int32_t step) {
     const long long half = n / 2;
     long long r = ((long long)step % half + half) % half;
     u64 g = 1;
@@ -247,19 +247,11 @@ static void add_rot_keys(pft_ctx* c, const int32_t* steps, int n_steps) {
 }
 
 // ---- key switching ---------------------------------------------------------------------------
-struct KsIO {
-    const u64* d;     // [l][N] evaluation form
-    const u64* acc0;  // may be null
-    const u64* acc1;  // may be null
-    u64* out0;
-    u64* out1;
-    int l;  // level of this input
-};
 
 // For each input d (any level): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
 // Every stage is one launch (or a few, by descriptor capacity) over all inputs, whatever
 // their levels; the key is read once per stage.
-static void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>& io) {
+void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>& io) {
     const int L = c->L, k = c->k, alpha = c->alpha;
     const size_t B = io.size();
     if (B == 0) return;
@@ -406,7 +398,7 @@ static std::map<int, std::vector<int>> by_level(const pft_ct* const* a, int B) {
     return g;
 }
 
-static void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out,
+void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out,
                          EwOp op) {
     for (int i = 0; i < B; i++) {
         check_ct(a[i]);
@@ -430,7 +422,7 @@ static void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const
     ew(c, op, ra, rb, ro);
 }
 
-static void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B,
+void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B,
                                pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
         check_ct(a[i]);
@@ -453,7 +445,10 @@ static void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt*
     ew(c, EwOp::Mul, ra, rb, ro);
 }
 
-static void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B,
+static void mul_relin_group(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B,
+                            pft_ct* const* out);
+
+void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B,
                                pft_ct* const* out) {
     NEED(c->keys.count(0), PFT_ERR_NO_KEY, "no relinearisation key");
     for (int i = 0; i < B; i++) {
@@ -463,6 +458,37 @@ static void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct*
         NEED(a[i]->level == b[i]->level, PFT_ERR_LEVEL_MISMATCH, "HMUL operands at different levels");
     }
     if (B == 0) return;
+    // groups whose tensor and key-switching scratch fit the budget, unless an output is also
+    // the input of another entry (then every product must be formed before any output is written)
+    bool cross_alias = false;
+    {
+        std::map<const pft_ct*, int> pos;
+        for (int i = 0; i < B; i++) {
+            pos[a[i]] = i;
+            pos[b[i]] = i;
+        }
+        for (int i = 0; i < B && !cross_alias; i++) {
+            auto it = pos.find(out[i]);
+            cross_alias = it != pos.end() && (it->second != i || a[i] != out[i] && b[i] != out[i]);
+        }
+    }
+    int i0 = 0;
+    while (i0 < B) {
+        int i1 = i0;
+        size_t words = 0;
+        while (i1 < B) {
+            const size_t w = 3 * (size_t)a[i1]->level * c->n + ks_scratch_words(c, a[i1]->level);
+            if (!cross_alias && i1 > i0 && (words + w) * 8 > kKsScratchBudget) break;
+            words += w;
+            i1++;
+        }
+        mul_relin_group(c, a + i0, b + i0, i1 - i0, out + i0);
+        i0 = i1;
+    }
+}
+
+static void mul_relin_group(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B,
+                            pft_ct* const* out) {
     const size_t limb = c->n;
     std::vector<size_t> off(B);
     size_t tot = 0;
@@ -646,7 +672,7 @@ static void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps,
     }
 }
 
-static void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
+void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
         check_ct(a[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
@@ -690,6 +716,123 @@ static void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* 
     }
 }
 
+// ---- level and scale management --------------------------------------------------------------
+void op_drop_level_batch(pft_ctx* c, const pft_ct* const* a, int B, int level, pft_ct* const* out) {
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+        NEED(level >= 1 && level <= a[i]->level, PFT_ERR_LEVEL_MISMATCH, "target level above the input level");
+    }
+    const size_t limb = c->n;
+    std::vector<u64*> nb(B);
+    std::vector<PolyRef> in, o;
+    for (int i = 0; i < B; i++) {
+        nb[i] = (u64*)dalloc(c, 2 * (size_t)level * limb * 8);
+        for (int pol = 0; pol < 2; pol++) {
+            in.push_back(ref(a[i]->data + (size_t)pol * a[i]->level * limb, level));
+            o.push_back(ref(nb[i] + (size_t)pol * level * limb, level));
+        }
+    }
+    ew(c, EwOp::Copy, in, {}, o);
+    std::vector<double> sc(B);
+    for (int i = 0; i < B; i++) sc[i] = a[i]->scale;
+    for (int i = 0; i < B; i++) {
+        // stream-ordered free: the copy above reads an aliased input first; an output that
+        // appears twice gets the last copy
+        if (out[i]->data != nb[i]) dfree(c, out[i]->data);
+        out[i]->data = nb[i];
+        out[i]->cap = 2 * (size_t)level * limb;
+        out[i]->level = level;
+        out[i]->scale = sc[i];
+        out[i]->ctx = c;
+    }
+}
+
+void op_const_batch(pft_ctx* c, const pft_ct* const* a, int B, double value, double const_scale, bool mul,
+                    pft_ct* const* out) {
+    int lmax = 0;
+    for (int i = 0; i < B; i++) {
+        check_ct(a[i]);
+        NEED(out[i], PFT_ERR_ARG, "null output");
+        lmax = std::max(lmax, a[i]->level);
+    }
+    if (B == 0) return;
+    NEED(std::isfinite(value) && (!mul || (std::isfinite(const_scale) && const_scale > 0)), PFT_ERR_ARG,
+         "constant and its scale must be finite (scale positive)");
+    // groups of equal integer constants: k depends on the ciphertext's scale when adding
+    std::map<long long, std::vector<int>> by_k;
+    for (int i = 0; i < B; i++) {
+        const double x = value * (mul ? const_scale : a[i]->scale);
+        NEED(std::fabs(x) < 9.0e18, PFT_ERR_ARG, "constant times scale exceeds 2^63");
+        by_k[std::llround(x)].push_back(i);  // nearest integer, halfway cases away from zero
+    }
+    const size_t limb = c->n;
+    for (auto& kv : by_k) {
+        const long long k = kv.first;
+        std::vector<u64> consts(3 * (size_t)lmax);
+        for (int r = 0; r < lmax; r++) {
+            const u64 q = c->primes[r];
+            long long km = k % (long long)q;
+            const u64 kr = km < 0 ? (u64)(km + (long long)q) : (u64)km;
+            const u64 sm = mul ? kr : 1;
+            consts[3 * r] = mul ? 0 : kr;
+            consts[3 * r + 1] = sm;
+            consts[3 * r + 2] = shoup(sm, q);
+        }
+        Scratch dc(c, consts.size() * 8);
+        const u64* cdev = upload(c, dc, consts);
+        std::vector<PolyRef> x, o, cin, cout;
+        for (int i : kv.second) {
+            const int l = a[i]->level;
+            const double sc = mul ? a[i]->scale * const_scale : a[i]->scale;
+            u64* src = a[i]->data;
+            if (out[i] != a[i]) {
+                ensure_ct(c, out[i], l);
+                out[i]->ctx = c;
+            }
+            out[i]->scale = sc;
+            x.push_back(cpoly(src, l, c->n, 0));
+            o.push_back(cpoly(out[i]->data, l, c->n, 0));
+            if (mul) {
+                x.push_back(cpoly(src, l, c->n, 1));
+                o.push_back(cpoly(out[i]->data, l, c->n, 1));
+            } else if (out[i]->data != src) {
+                cin.push_back(cpoly(src, l, c->n, 1));
+                cout.push_back(cpoly(out[i]->data, l, c->n, 1));
+            }
+        }
+        subscale(c, x, nullptr, nullptr, o, cdev);
+        if (!cin.empty()) ew(c, EwOp::Copy, cin, {}, cout);
+    }
+    (void)limb;
+}
+
+void relin_batch(pft_ctx* c, const std::vector<RelinIO>& io) {
+    NEED(c->keys.count(0), PFT_ERR_NO_KEY, "no relinearisation key");
+    const size_t limb = c->n;
+    size_t i0 = 0;
+    while (i0 < io.size()) {
+        size_t i1 = i0, words = 0;
+        while (i1 < io.size()) {
+            const size_t w = ks_scratch_words(c, io[i1].l);
+            if (i1 > i0 && (words + w) * 8 > kKsScratchBudget) break;
+            words += w;
+            i1++;
+        }
+        std::vector<KsIO> ks;
+        for (size_t i = i0; i < i1; i++) {
+            const RelinIO& r = io[i];
+            ensure_ct(c, r.out, r.l);
+            r.out->ctx = c;
+            r.out->scale = r.scale;
+            ks.push_back(KsIO{r.d + 2 * (size_t)r.l * limb, r.d, r.d + (size_t)r.l * limb, r.out->data,
+                              r.out->data + (size_t)r.l * limb, r.l});
+        }
+        keyswitch_batch(c, c->keys[0], ks);
+        i0 = i1;
+    }
+}
+
 // ---- encryption ----------------------------------------------------------------------------
 static void encrypt(pft_ctx* c, const pft_pt* pt, int mode, u32 nonce, pft_ct* out) {
     NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
@@ -728,7 +871,7 @@ static void encrypt(pft_ctx* c, const pft_pt* pt, int mode, u32 nonce, pft_ct* o
 // ---- fastText inference (Sec. 3.1) ----------------------------------------------------------
 // T[i] += rotate(T[i], g) for every ciphertext of T: c0 + aut(c0) first, then the key switch
 // of aut(c1) with (T.c0, T.c1) as accumulators, in place; tiled to bound the scratch memory.
-static void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g) {
+void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g) {
     NEED(c->keys.count(g), PFT_ERR_NO_KEY, "missing rotation key");
     const int n = c->n;
     const size_t limb = n;
@@ -1553,6 +1696,20 @@ int pft_rescale(pft_ctx* c, const pft_ct* a, pft_ct* out) {
 int pft_rotate(pft_ctx* c, const pft_ct* a, int32_t step, pft_ct* out) {
     return guard(c, [&] { op_rotate_batch(c, &a, 1, step, &out); });
 }
+int pft_drop_level(pft_ctx* c, const pft_ct* a, int level, pft_ct* out) {
+    return guard(c, [&] { op_drop_level_batch(c, &a, 1, level, &out); });
+}
+int pft_add_const(pft_ctx* c, const pft_ct* a, double value, pft_ct* out) {
+    return guard(c, [&] { op_const_batch(c, &a, 1, value, 0.0, false, &out); });
+}
+int pft_mul_const(pft_ctx* c, const pft_ct* a, double value, double const_scale, pft_ct* out) {
+    return guard(c, [&] { op_const_batch(c, &a, 1, value, const_scale, true, &out); });
+}
+int pft_ct_set_scale(pft_ct* ct, double scale) {
+    if (!ct || !(scale > 0) || !std::isfinite(scale)) return PFT_ERR_ARG;
+    ct->scale = scale;
+    return PFT_OK;
+}
 int pft_dot_plain_batch(pft_ctx* c, const pft_ct* const* cts, const pft_pt* const* pts, int K, int n_out,
                         int pts_shared, pft_ct* const* outs) {
     return guard(c, [&] {
@@ -1941,9 +2098,5 @@ int pft_fasttext_infer_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* co
     });
 }
 
-int pft_fasttext_train_step(pft_ctx* c, pft_ft_model*, const pft_ct* const*, int) {
-    if (c) c->err = "encrypted training (Algorithm 5) is not implemented";
-    return PFT_ERR_NOT_IMPLEMENTED;
-}
 
 }  // extern "C"

@@ -189,6 +189,47 @@ inline int guard(pft_ctx* c, F f) {
 inline void check_ct(const pft_ct* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty ciphertext"); }
 inline void check_pt(const pft_pt* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty plaintext"); }
 
+// ---- operations shared by the translation units (ckks.cu) ----------------------------------
+// Galois element 5^step mod 2N of a left rotation by `step` slots.
+u32 galois_of(int n, int32_t step);
+struct KsIO {
+    const u64* d;     // [l][N] evaluation form
+    const u64* acc0;  // may be null
+    const u64* acc1;  // may be null
+    u64* out0;
+    u64* out1;
+    int l;  // level of this input
+};
+// For each input d (any level): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
+void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>& io);
+void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out, EwOp op);
+void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B, pft_ct* const* out);
+void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out);
+void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out);
+// T[i] += rotate(T[i], g) for every ciphertext of T (any levels), tiled to bound scratch memory.
+void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g);
+// out[i] = the first `level` limbs of a[i] (the same message at a lower level).
+void op_drop_level_batch(pft_ctx* c, const pft_ct* const* a, int B, int level, pft_ct* const* out);
+// mul = false: out[i] = a[i] + value (the constant round(value * scale) added to c0);
+// mul = true:  out[i] = a[i] * round(value * const_scale), scale multiplied by const_scale.
+void op_const_batch(pft_ctx* c, const pft_ct* const* a, int B, double value, double const_scale, bool mul,
+                    pft_ct* const* out);
+// Relinearisation of three-polynomial buffers [3][l][N] (d0, d1, d2) into out[i] (level l, scale).
+struct RelinIO {
+    const u64* d;
+    int l;
+    double scale;
+    pft_ct* out;
+};
+void relin_batch(pft_ctx* c, const std::vector<RelinIO>& io);
+// Budget for the scratch of one batched key-switching call (inputs are tiled beyond it).
+constexpr size_t kKsScratchBudget = (size_t)24 << 30;
+// Scratch words of one key switch at level l.
+inline size_t ks_scratch_words(const pft_ctx* c, int l) {
+    const int E = l + c->k, beta = (l + c->alpha - 1) / c->alpha;
+    return (size_t)(l + beta * E + 2 * E + 2 * l) * c->n;
+}
+
 // ---- fastText inference as a sequence of stages (Sec. 3.1) ---------------------------------
 // One document in flight: its inputs, its working ciphertexts and its score.  A stage runs
 // over any set of documents of one model, whatever their levels (3 <= l <= model level; a

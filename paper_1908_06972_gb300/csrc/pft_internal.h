@@ -110,6 +110,9 @@ void ew_dot(const DevTables& t, const u64* const* A, const u64* const* B, u64* c
             bool b_shared, int l, cudaStream_t st);
 // out = acc + ((x + c) - y) * s per limb, consts_dev[3 limb + {0,1,2}] = {c, s, s_shoup};
 // y may be null (taken as 0), acc may be null.
+// out[p] (+)= sum_k a (x) b over K pairs (tables in device memory; see poly.cu)
+void ew_tensor_dot(const DevTables& t, const u64* const* A, const u64* const* B, u64* const* O, int n_out, int K,
+                   int l, bool accumulate, cudaStream_t st);
 void sub_scale(const DevTables& t, const PolySet& x, const PolySet* y, const PolySet* acc, const PolySet& out,
                const u64* consts_dev, cudaStream_t st);
 // Galois automorphism X -> X^g in the evaluation layout.

@@ -152,6 +152,67 @@ void ew_dot(const DevTables& t, const u64* const* A, const u64* const* B, u64* c
     PFT_LAUNCH_CHECK("dot");
 }
 
+// ---- sums of HMUL tensors: out[p] (+)= sum_k a[p*K+k] (x) b[p*K+k] ---------------------------
+// (a0, a1) (x) (b0, b1) = (a0 b0, a0 b1 + a1 b0, a1 b1).  Tables: A[(p*K + k)*2 + pol] and
+// B likewise point at polynomial bases (limb r at r*N, so operands of a higher level are
+// read through their leading limbs); O[p*3 + i] at the three output polynomials.  128-bit
+// sums reduced every 4 terms (8 products in the middle term).
+__global__ void k_tensor_dot(DevTables t, const u64* const* A, const u64* const* B, u64* const* O, int K, int l,
+                             int accumulate) {
+    const int p = blockIdx.z, limb = blockIdx.y;
+    if (limb >= l) return;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
+    const DPrime P = load_prime(t.primes, limb);
+    const size_t off = ((size_t)limb << t.logn) + 2 * (size_t)x2;
+    U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0}, s2x = {0, 0}, s2y = {0, 0};
+    for (int k = 0; k < K; k++) {
+        const size_t e = ((size_t)p * K + k) * 2;
+        const ulonglong2 a0 = *reinterpret_cast<const ulonglong2*>(A[e] + off);
+        const ulonglong2 a1 = *reinterpret_cast<const ulonglong2*>(A[e + 1] + off);
+        const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(B[e] + off);
+        const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(B[e + 1] + off);
+        mac_wide(s0x, a0.x, b0.x);
+        mac_wide(s0y, a0.y, b0.y);
+        mac_wide(s1x, a0.x, b1.x);
+        mac_wide(s1x, a1.x, b0.x);
+        mac_wide(s1y, a0.y, b1.y);
+        mac_wide(s1y, a1.y, b0.y);
+        mac_wide(s2x, a1.x, b1.x);
+        mac_wide(s2y, a1.y, b1.y);
+        if ((k & 3) == 3) {
+            s0x = {barrett_reduce(s0x.hi, s0x.lo, P), 0};
+            s0y = {barrett_reduce(s0y.hi, s0y.lo, P), 0};
+            s1x = {barrett_reduce(s1x.hi, s1x.lo, P), 0};
+            s1y = {barrett_reduce(s1y.hi, s1y.lo, P), 0};
+            s2x = {barrett_reduce(s2x.hi, s2x.lo, P), 0};
+            s2y = {barrett_reduce(s2y.hi, s2y.lo, P), 0};
+        }
+    }
+    const U128* S[3][2] = {{&s0x, &s0y}, {&s1x, &s1y}, {&s2x, &s2y}};
+    for (int i = 0; i < 3; i++) {
+        ulonglong2 r;
+        r.x = barrett_reduce(S[i][0]->hi, S[i][0]->lo, P);
+        r.y = barrett_reduce(S[i][1]->hi, S[i][1]->lo, P);
+        u64* dst = O[(size_t)p * 3 + i] + off;
+        if (accumulate) {
+            const ulonglong2 o = *reinterpret_cast<const ulonglong2*>(dst);
+            r.x = addmod(r.x, o.x, P.q);
+            r.y = addmod(r.y, o.y, P.q);
+        }
+        *reinterpret_cast<ulonglong2*>(dst) = r;
+    }
+}
+
+void ew_tensor_dot(const DevTables& t, const u64* const* A, const u64* const* B, u64* const* O, int n_out, int K,
+                   int l, bool accumulate, cudaStream_t st) {
+    if (n_out == 0) return;
+    dim3 g((unsigned)((t.n / 2 + kEwThreads - 1) / kEwThreads), (unsigned)l, (unsigned)n_out);
+    PFT_PROF("tensor_dot", st, (double)n_out * l * t.n * 8.0 * (4 * K + (accumulate ? 6 : 3)));
+    k_tensor_dot<<<g, kEwThreads, 0, st>>>(t, A, B, O, K, l, accumulate ? 1 : 0);
+    PFT_LAUNCH_CHECK("tensor_dot");
+}
+
 // ---- out = acc + (x - y) * s  (s per limb, Shoup pair) ---------------------------------
 // Used by ModDown (s = P^-1, acc = the other tensor part or the rotated c0) and by
 // rescale (x = c + h, y = NTT(r), s = p^-1): consts[limb] = {add_to_x, s, s_shoup}.

@@ -138,3 +138,63 @@ def test_fasttext_diagonal_full_model_batched_tolerance(p3):
             pf.pft_ct_destroy(h)
     finally:
         pf.pft_ft_model_destroy(model)
+
+
+def test_training_step_full_size_vs_fp64(gpu):
+    """Encrypted minibatch step at the training workload's sizes (vocabulary 8192 in one
+    N = 2^16 ciphertext, dimension 32, 4 classes; 60 + 29 x 40-bit chain, 4 special primes,
+    digits of 4) on 4 documents: decrypted gradients and updated weights within 2^-20 of FP64."""
+    from oracle import fasttext as OF
+
+    pf = gpu
+    L, m, n, c, B, eta, sc = 30, 8192, 32, 4, 4, 0.25, 2.0 ** 40
+    ctx = pf.pft_ctx_create(16, L, 4, 4, 60, 40, 60, sc, (0x7A11, 1, 2, 3))
+    handles = []
+
+    def enc(z, level, scale, nonce):
+        pt = pf.pft_encode(ctx, z, scale, level)
+        h = pf.pft_encrypt(ctx, pt, pf.PFT_ENC_SK, nonce)
+        pf.pft_pt_destroy(pt)
+        handles.append(h)
+        return h
+
+    def dec(h, k):
+        pt = pf.pft_decrypt(ctx, h)
+        z = pf.pft_decode(ctx, pt, k).real
+        pf.pft_pt_destroy(pt)
+        return z
+
+    try:
+        pf.pft_keygen(ctx, [1 << i for i in range(15)], True)
+        H, O = synth.fasttext_weights(51, m, n, c)
+        V = synth.documents(52, m, B)
+        Y = np.eye(c)[np.random.default_rng(53).integers(0, c, B)]
+        model = pf.pft_ft_enc_model_create(ctx, [enc(H[:, j], L, sc, 10 + j) for j in range(n)],
+                                           [enc(O[j], L - 1, sc, 100 + j) for j in range(n)], m, n, c)
+        try:
+            dl, ll, ls = pf.pft_fasttext_train_spec(ctx, model, sc)
+            docs = [enc(V[b], dl, sc, 200 + b) for b in range(B)]
+            labels = [enc(Y[b] - 0.25, ll, ls, 300 + b) for b in range(B)]
+            gH = [pf.pft_ct_create(ctx) for _ in range(n)]
+            gO = [pf.pft_ct_create(ctx) for _ in range(n)]
+            handles.extend(gH + gO)
+            pf.pft_fasttext_train_step(ctx, model, docs, labels, eta, gH, gO)
+            ref_H, ref_O = OF.train_grads_plain(V, Y, H, O)
+            got_H = np.stack([dec(gH[j], m) for j in range(n)], 1)
+            got_O = np.stack([dec(gO[j], c) for j in range(n)])
+            assert np.max(np.abs(got_H - ref_H)) < 2.0 ** -20, np.max(np.abs(got_H - ref_H))
+            assert np.max(np.abs(got_O - ref_O)) < 2.0 ** -20, np.max(np.abs(got_O - ref_O))
+            assert pf.pft_ft_enc_model_levels(model) == (L - 6, L - 5)
+            for j in (0, n - 1):
+                for which, want in ((0, H[:, j] - eta * ref_H[:, j]), (1, O[j] - eta * ref_O[j])):
+                    w = pf.pft_ct_create(ctx)
+                    handles.append(w)
+                    pf.pft_ft_enc_model_get(ctx, model, which, j, w)
+                    got = dec(w, want.size)
+                    assert np.max(np.abs(got - want)) < 2.0 ** -20
+        finally:
+            pf.pft_ft_enc_model_destroy(model)
+    finally:
+        for h in handles:
+            pf.pft_ct_destroy(h)
+        pf.pft_ctx_destroy(ctx)

@@ -178,8 +178,8 @@ def test_errors(p1, cts1):
         pf.pft_rotate(ctx, ga, 9, out)
     assert e.value.code == pf.PFT_ERR_NO_KEY
     with pytest.raises(pf.PftError) as e:
-        pf.pft_fasttext_train_step(ctx, None, [])
-    assert e.value.code == pf.PFT_ERR_NOT_IMPLEMENTED
+        pf.pft_fasttext_train_step(ctx, None, [], [], 0.0)
+    assert e.value.code == pf.PFT_ERR_ARG
 
 
 def test_batched_uneven_levels(p1):

@@ -55,7 +55,7 @@ def test_round_half_away():
 
 @pytest.fixture(scope="module")
 def small():
-    o = OK.Oracle(10, 8, 1, 2, 60, 40, 60, 2.0 ** 40, (0x7A, 1, 2, 3))
+    o = OK.Oracle(10, 8, 2, 2, 60, 40, 60, 2.0 ** 40, (0x7A, 1, 2, 3))  # P = 2^120 above every digit
     o.keygen([1 << i for i in range(9)], True)
     return o
 
