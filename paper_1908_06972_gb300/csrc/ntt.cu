@@ -30,9 +30,12 @@ namespace pft {
 // Shoup product x W mod q in [0, 2q), formed as x w + hq (-q) (mod 2^64) so that the
 // subtraction folds into the multiply-adds; nq = -q mod 2^64.
 __device__ __forceinline__ u64 shoup_nq(u64 x, ulonglong2 W, u64 nq) { return x * W.x + mulhi(x, W.y) * nq; }
-// Cooley-Tukey (Harvey): X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q)
+// Cooley-Tukey (Harvey): X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q).  LAZY (primes below
+// 2^58): no correction of X, values grow by less than 2q per stage, so the 16 stages of an
+// N = 2^16 forward transform from [0, 2q) stay below 34q < 2^64.
+template <bool LAZY = false>
 __device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
-    if (X >= q2) X -= q2;
+    if (!LAZY && X >= q2) X -= q2;
     const u64 T = shoup_nq(Y, W, 0 - q);
     Y = X - T + q2;
     X = X + T;
@@ -64,7 +67,7 @@ __device__ __forceinline__ u64 canon4(u64 v, u64 q, u64 q2) {
 // One round = four stages on 16 registers: register e holds element (e << W0) | wpart of
 // the current 256-point sub-transform; DIMHI = 0 for column stages (s = 7 - p), 8 for row
 // stages (s = 15 - p, r = the row being transformed).
-template <bool INV, int W0, int DIMHI>
+template <bool INV, int W0, int DIMHI, bool LAZY = false>
 __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, const ulonglong2* __restrict__ tw,
                                             u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1) {
 #pragma unroll
@@ -78,7 +81,7 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
             const int elem = (e << W0) | wpart;
             const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
             if (!INV) {
-                ct_bfly(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
+                ct_bfly<LAZY>(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
             } else if (s == 0) {  // last inverse stage: N^-1 folded into both outputs
                 u64 S = x[e] + x[e | (1 << lb)];
                 if (S >= q2) S -= q2;
@@ -206,6 +209,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(512, MINB)
 // exchange (odd strides 17 / 273: conflict-free); pass B stages its final store (forward)
 // or first load (inverse) through shared memory to keep the global side coalesced.
 constexpr int kRowStride = 273;  // 256 + 16 padding + 1
+constexpr u64 kLazyBound = 1ull << 58;  // forward butterflies skip the correction below this prime
 
 template <bool INV, int LOGT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet in, PolySet out, int is_final) {
@@ -226,17 +230,20 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet
     const ulonglong2 NI1 = INV ? __ldg(&t.inv1ninv[pi]) : make_ulonglong2(0, 0);
     u64 x[16];
     if (!INV) {
+        const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = src[(size_t)((e << 4) | w) << LOGT];
-        ntt16_round<false, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
+        if (lazy) ntt16_round<false, 4, 0, true>(x, w, 0, tw, q, q2, NI, NI1);
+        else ntt16_round<false, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
 #pragma unroll
         for (int e = 0; e < 16; e++) sm[((e << 4) | w) * 17 + cc] = x[e];
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = sm[((w << 4) | e) * 17 + cc];
-        ntt16_round<false, 0, 0>(x, w << 4, 0, tw, q, q2, NI, NI1);
+        if (lazy) ntt16_round<false, 0, 0, true>(x, w << 4, 0, tw, q, q2, NI, NI1);
+        else ntt16_round<false, 0, 0>(x, w << 4, 0, tw, q, q2, NI, NI1);
 #pragma unroll
-        for (int e = 0; e < 16; e++) dst[(size_t)((w << 4) | e) << LOGT] = is_final ? canon4(x[e], q, q2) : x[e];
+        for (int e = 0; e < 16; e++) dst[(size_t)((w << 4) | e) << LOGT] = x[e];
     } else {
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = src[(size_t)((w << 4) | e) << LOGT];
@@ -272,17 +279,31 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     u64* my = sm + cc * kRowStride;
     u64 x[16];
     if (!INV) {
+        const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = src[((size_t)u << 8) | (e << 4) | w];
-        ntt16_round<false, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
+        if (lazy) ntt16_round<false, 4, 8, true>(x, w, u, tw, q, q2, NI, NI1);
+        else ntt16_round<false, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
 #pragma unroll
         for (int e = 0; e < 16; e++) my[e * 17 + w] = x[e];  // point e*16 + w
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
-        ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
+        if (lazy) {
+            ntt16_round<false, 0, 8, true>(x, w << 4, u, tw, q, q2, NI, NI1);
+            // values below 34q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
+            // (mu = floor(2^(64+s) / q)), then one correction
+            const u64 one_p = __ldg(&t.primes[pi].mu) >> __ldg(&t.primes[pi].s);
 #pragma unroll
-        for (int e = 0; e < 16; e++) my[w * 17 + e] = is_final ? canon4(x[e], q, q2) : x[e];
+            for (int e = 0; e < 16; e++) {
+                u64 r = x[e] - mulhi(x[e], one_p) * q;
+                my[w * 17 + e] = r >= q ? r - q : r;
+            }
+        } else {
+            ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
+#pragma unroll
+            for (int e = 0; e < 16; e++) my[w * 17 + e] = canon4(x[e], q, q2);
+        }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 16; k++) {
