@@ -39,6 +39,10 @@ WORKLOAD = ("N=2^16, 30 limbs (60 + 29x50 bits) + 4 special (60 bits), digits of
 # ALU roofline (derivation in the design doc): 152 SMs x 64 32-bit IMAD per SM per clock x 2.07 GHz,
 # at 10 IMAD per 64-bit Shoup butterfly multiply.
 SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 10
+# DRAM bytes (read + written) per limb and pass of the N = 2^16 transform kernels: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum over the four two-pass launches of the
+# 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes.
+NTT_DRAM_BYTES_PER_LIMB_PASS = 1.0067e6
 
 
 def levels():
@@ -214,31 +218,65 @@ def run_gpu(args):
     h2d = sum(a.nbytes for a, _ in host_in)
     d2h = sum(o.nbytes for o in host_out)
 
-    def step_e2e():
+    # Pipelined through the public API: each step's inputs are copied in (pft_ct_import_batch on
+    # a copy stream) while the previous step computes; results are read back (export, which
+    # synchronises) before the next step starts.
+    S = torch.cuda.current_stream()
+    Cs = torch.cuda.Stream()
+    marks = []
+
+    def import_on_copy_stream():
+        pft.pft_set_stream(ctx, Cs.cuda_stream)
         ins = pft.pft_ct_import_batch(ctx, [arr for arr, _ in host_in], [sc for _, sc in host_in])
-        a, b = ins[0::2], ins[1::2]
-        step_batched(a, b, C)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(Cs)
+        pft.pft_set_stream(ctx, S.cuda_stream)
+        return ins, ev
+
+    def step_e2e(cur, last):
+        ins, ready = cur
+        S.wait_event(ready)
+        nxt = import_on_copy_stream() if not last else None
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(S)
+        step_batched(ins[0::2], ins[1::2], C)
+        ev[1].record(S)
         pft.pft_ct_export_batch(ctx, C, host_out)
+        ev[2].record(S)
         for h in ins:
             pft.pft_ct_destroy(h)
+        marks.append(ev)
+        return nxt
 
-    step_e2e()
+    cur = import_on_copy_stream()
+    step_e2e(cur, True)
     barrier()
+    marks.clear()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_e2e()
+    cur = import_on_copy_stream()
+    for k in range(args.steps):
+        cur = step_e2e(cur, k == args.steps - 1)
     barrier()
     e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
     e2e = throughput(BATCH * args.steps, world, e2e_s)
+    # device-side split of the end-to-end step (events on the compute stream)
+    e2e_split = {k: round(sum(ev[i].elapsed_time(ev[i + 1]) for ev in marks) / len(marks), 2)
+                 for i, k in enumerate(("compute_ms", "export_ms"))}
+    e2e_split["wall_ms"] = round(1e3 * e2e_s / args.steps, 2)
 
     # roofline of the timed kernel family
     roof = None
     if k_ms > 0 and args.roofline_kernel.startswith("ntt"):
         achieved = k_work / (k_ms / 1e3) / 1e9  # Gbutterfly/s (one Shoup mulmod each)
         peak = SMS * IMAD_PER_CLK * SM_MHZ_MAX * 1e6 / IMAD_PER_MULMOD / 1e9
+        limb_passes = k_work / max(1, k_launches) / ((1 << LOGN) // 2 * 8)
         roof = {"bound": "alu", "kernel": args.roofline_kernel, "achieved": round(achieved, 2),
                 "peak": round(peak, 2), "unit": "Gmulmod/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "launches": k_launches, "kernel_ms": round(k_ms, 3),
+                "traffic": round(NTT_DRAM_BYTES_PER_LIMB_PASS * limb_passes),
+                "algorithmic_bytes": round(limb_passes * (1 << LOGN) * 16),
+                "traffic_source": "ncu DRAM bytes per limb-pass of the 16 x 30-limb transform case, "
+                                  "times the mean limb-passes per launch in the step",
+                "launches": k_launches, "kernel_ms": round(k_ms, 3),
                 "kernel_share_of_step": round(k_ms / ms, 4),
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 10 IMAD per Shoup mulmod"}
     elif k_ms > 0:
@@ -276,7 +314,7 @@ def run_gpu(args):
            "plain_value": round(plain, 3) if plain else None,
            "graph_value": round(graph_value, 3) if graph_value else None,
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": d2h},
+                   "d2h_bytes_per_step": d2h, "split": e2e_split},
            "gpu_launches": int(all_launches), "roofline": roof,
            "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
                         "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
