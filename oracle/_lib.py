@@ -56,6 +56,7 @@ def lib():
             L.orc_automorph.argtypes = [_u64p, _u64p, _c.c_int, _c.c_int, _c.c_uint64, _u64p]
             L.orc_bconv.argtypes = [_u64p, _u64p, _c.c_int, _u64p, _c.c_int, _c.c_int, _u64p]
             L.orc_eval_at.argtypes = [_u64p, _c.c_uint64, _c.c_uint64, _c.c_int, _i64p, _c.c_int, _u64p]
+            L.orc_interp_layout.argtypes = [_u64p, _c.c_uint64, _c.c_uint64, _c.c_int, _u64p]
             _lib = L
     return _lib
 
@@ -187,4 +188,11 @@ def eval_at(a, psi, q, logn, idx):
     idx = np.ascontiguousarray(idx, np.int64)
     out = np.empty(idx.size, np.uint64)
     lib().orc_eval_at(_u64(a), int(psi), int(q), logn, idx, idx.size, out)
+    return out
+
+
+def interp_layout(A, psi, q, logn):
+    """Coefficients of the polynomial whose library evaluation layout is A."""
+    out = np.empty(1 << logn, np.uint64)
+    lib().orc_interp_layout(_u64(A), int(psi), int(q), logn, out)
     return out

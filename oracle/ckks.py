@@ -35,6 +35,7 @@ from . import params as P
 # sampler stream domains (the first nonce word)
 DOM_SECRET, DOM_PK_A, DOM_PK_E, DOM_KSK_A, DOM_KSK_E = 1, 2, 3, 4, 5
 DOM_ENC_A, DOM_ENC_E, DOM_ENC_V, DOM_ENC_E0, DOM_ENC_E1 = 6, 7, 8, 9, 10
+DOM_KSK_A_EVAL = 11  # a_j of seeded compressed keys, drawn in the library's evaluation layout
 
 
 class Ciphertext:
@@ -92,7 +93,7 @@ def crt_centered(rows, primes):
 class Oracle:
     def __init__(self, logn, n_limbs, n_special, alpha, first_bits=60, mid_bits=40,
                  special_bits=60, scale=2.0 ** 40, seed=(1, 2, 3, 4), sigma="3.2",
-                 primes=None, special_primes=None):
+                 primes=None, special_primes=None, compressed_keys=False):
         self.logn, self.N = logn, 1 << logn
         if primes is None:
             self.q, self.p = P.prime_chain(logn, n_limbs, n_special, first_bits, mid_bits, special_bits)
@@ -104,6 +105,7 @@ class Oracle:
         self.cdt = np.array(P.gauss_cdt(sigma), np.uint32)
         self.Pprod = math.prod(self.p)
         self.keys = {}
+        self.compressed_keys = compressed_keys
 
     # ---- sampler (counter-based ChaCha20 streams) --------------------------------------
     def uniform_rows(self, dom, obj, subs, primes):
@@ -147,7 +149,15 @@ class Oracle:
         s_b = C.reduce_signed(self.s, basis)
         K = np.empty((beta, 2, nb, self.N), np.uint64)
         for j in range(beta):
-            a = self.uniform_rows(DOM_KSK_A, key_id, [j * 256 + m for m in range(nb)], basis)
+            if self.compressed_keys:
+                # seeded compressed keys: a_j drawn as evaluation-layout entries (entry i of
+                # row m = the uniform residue of word pair i of stream (key_id, 256 j + m)),
+                # i.e. a_j is the polynomial interpolating those values
+                ev = self.uniform_rows(DOM_KSK_A_EVAL, key_id, [j * 256 + m for m in range(nb)], basis)
+                a = np.stack([C.interp_layout(ev[m], P.root_2n(basis[m], self.logn), basis[m], self.logn)
+                              for m in range(nb)])
+            else:
+                a = self.uniform_rows(DOM_KSK_A, key_id, [j * 256 + m for m in range(nb)], basis)
             e = C.reduce_signed(self.gauss(DOM_KSK_E, key_id, j), basis)
             b = C.vsub(e, C.polymul(a, s_b, basis), basis)
             for i in range(j * alpha, min((j + 1) * alpha, L)):

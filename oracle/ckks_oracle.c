@@ -324,3 +324,20 @@ void orc_eval_at(const u64* a, u64 psi, u64 q, int logn, const i64* idx, int nid
     }
     free(pw);
 }
+
+/* The inverse of that layout: the coefficients of the polynomial whose value at
+ * psi^(2*brv(i)+1) is A[i].  With V_m = A[brv(m)] = sum_j (a_j psi^j) w^(m j),
+ * w = psi^2, the twisted coefficients are the inverse cyclic transform of V:
+ * a_j = n^-1 psi^-j sum_m V_m w^(-m j). */
+void orc_interp_layout(const u64* A, u64 psi, u64 q, int logn, u64* out) {
+    int n = 1 << logn;
+    u64* v = (u64*)malloc(sizeof(u64) * (size_t)n);
+    for (int m = 0; m < n; m++) v[m] = A[brv((u64)m, logn)] % q;
+    cyclic_ntt(v, n, invmod(mulmod(psi, psi, q), q), q);
+    u64 ninv = invmod((u64)n % q, q), psi_inv = invmod(psi, q), pj = ninv;
+    for (int j = 0; j < n; j++) {
+        out[j] = mulmod(v[j], pj, q);
+        pj = mulmod(pj, psi_inv, q);
+    }
+    free(v);
+}

@@ -78,6 +78,24 @@ def test_eval_layout_definition_brute_force():
         assert int(got[i]) == want
 
 
+@pytest.mark.parametrize("logn", [4, 6, 10])
+def test_layout_interpolation_inverts_the_evaluation(logn):
+    """interp_layout(A) evaluated at the layout points (the independent O(N^2) definition)
+    gives back A; closed forms: the all-ones layout is the constant 1, the layout of the
+    roots themselves is X."""
+    n = 1 << logn
+    q = P.primes_of_bits(50, logn, 1)[0]
+    psi = P.root_2n(q, logn)
+    A = _rand(q, n)
+    a = C.interp_layout(A, psi, q, logn)
+    assert np.array_equal(C.eval_at(a, psi, q, logn, np.arange(n)), A)
+    one = C.interp_layout(np.ones(n, np.uint64), psi, q, logn)
+    assert int(one[0]) == 1 and not np.any(one[1:])
+    roots = np.array([pow(psi, 2 * int(format(i, "0%db" % logn)[::-1], 2) + 1, q) for i in range(n)], np.uint64)
+    x = C.interp_layout(roots, psi, q, logn)
+    assert int(x[1]) == 1 and int(x[0]) == 0 and not np.any(x[2:])
+
+
 def test_automorphism_by_evaluation():
     # (a(X^g))(zeta) = a(zeta^g) at every root zeta = psi^e (e odd) of X^N + 1
     logn, n = 5, 32

@@ -146,11 +146,21 @@ def _ks_bound(orc, l):
     return orc.N * 19 * orc.alpha * sum(qj) / orc.Pprod + orc.N * orc.k + orc.k + 1
 
 
+@pytest.fixture(scope="module")
+def small_compressed():
+    orc = ckks.Oracle(logn=10, n_limbs=3, n_special=2, alpha=2, first_bits=60, mid_bits=40, special_bits=60,
+                      seed=(11, 22, 33, 44), compressed_keys=True)
+    orc.keygen(rot_steps=[1], relin=True)  # key id 5 = g of a rotation by 1
+    return orc
+
+
+@pytest.mark.parametrize("compressed", [False, True])
 @pytest.mark.parametrize("l", [1, 2, 3])
-def test_keyswitch_equation(small, l):
+def test_keyswitch_equation(small, small_compressed, l, compressed):
     """u0 + u1 s = d s' + small, for the relinearisation key (s' = s^2) and a
-    rotation key (s' = s(X^g)); the error obeys the analytic bound."""
-    orc = small
+    rotation key (s' = s(X^g)); the error obeys the analytic bound.  Also for seeded
+    compressed keys, whose a_j are drawn in the evaluation layout."""
+    orc = small_compressed if compressed else small
     q = orc.q[:l]
     s = C.reduce_signed(orc.s, q)
     d = np.stack([rng.integers(0, qi, orc.N, dtype=np.uint64) for qi in q])
@@ -249,3 +259,16 @@ def test_fasttext_diagonal_variant(small):
     S = fasttext.encrypted_scores_diag(orc, orc.encrypt_sk(orc.encode(v, level=l), 77), D_pts, P_pt)
     got = orc.decode(orc.decrypt(S)).real[fasttext.diag_score_slots(n, c)]
     assert np.max(np.abs(got - fasttext.plain_scores(v[:m], H, O))) < 2 ** -20
+
+
+def test_compressed_keys_draw_a_in_the_evaluation_layout(small_compressed):
+    """a_j of a compressed key evaluates, at the layout points, to the stream's uniform
+    residues (the values the inner product regenerates), and differs from the full key's."""
+    orc = small_compressed
+    K = orc.keys[0]
+    basis = orc.q + orc.p
+    for j in range(K.shape[0]):
+        for m in (0, len(basis) - 1):
+            want = C.sample_uniform(orc.seed, ckks.DOM_KSK_A_EVAL, 0, 256 * j + m, basis[m], orc.N)
+            got = C.eval_at(K[j, 1, m], P.root_2n(basis[m], orc.logn), basis[m], orc.logn, np.arange(orc.N))
+            assert np.array_equal(got, want)
