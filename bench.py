@@ -142,7 +142,8 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pft.build()
-    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED,
+                             flags=pft.PFT_COMPRESSED_KEYS if args.compressed_keys else 0)
     tuned, tune_us = pft.pft_autotune(ctx)
     pft.pft_keygen(ctx, STEPS_ROT, True)
     lv = levels()
@@ -781,7 +782,8 @@ def run_case_ks(args):
 
     torch.cuda.set_device(0)
     pft.build()
-    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED,
+                             flags=pft.PFT_COMPRESSED_KEYS if args.compressed_keys else 0)
     pft.pft_keygen(ctx, [], True)
     A, B = [], []
     for i in range(4):
@@ -793,7 +795,7 @@ def run_case_ks(args):
     for _ in range(args.warmup):
         pft.pft_mul_relin_batch(ctx, A, B, C)
     torch.cuda.synchronize()
-    res = {"case": "ks", "level": L, "batch": 4}
+    res = {"case": "ks", "level": L, "batch": 4, "compressed_keys": bool(args.compressed_keys)}
     for fam in ("bconv", "ks_inner", "ntt", "sub_scale"):
         pft.pft_prof_start(fam)
         for _ in range(args.steps):
@@ -874,6 +876,8 @@ def main():
     ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
     ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
     ap.add_argument("--graph", type=int, default=1, help="also measure the step as one CUDA-graph launch")
+    ap.add_argument("--compressed-keys", action="store_true",
+                    help="seeded compressed switching keys (the step and --case ks)")
     ap.add_argument("--train", type=int, default=64, help="documents per encrypted training step (0: skip)")
     ap.add_argument("--train-plain-docs", type=int, default=2, help="documents timed on the plain training path")
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving trace (0: skip)")

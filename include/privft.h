@@ -75,6 +75,12 @@ typedef struct {
 } pft_allocator;
 
 #define PFT_ALLOW_INSECURE 1 /* pft_params.flags: accept log2(QP) above the 128-bit table */
+/* pft_params.flags: seeded compressed switching keys.  Each key keeps only its b_j rows; a_j
+ * is drawn uniformly in the evaluation domain from the ChaCha20 stream (seed, domain 11,
+ * object = key id (0 relinearisation, g rotation), sub = 256 j + prime index), and the key
+ * inner product regenerates it: key memory halves, the inner product trades key reads for
+ * ChaCha20 blocks.  Keys differ from the uncompressed ones (a_j is another draw). */
+#define PFT_COMPRESSED_KEYS 2
 
 /* Encryption parameters (SETUP, Sec. 2.3 and Sec. 5.4).
  *   log_n        log2 N, 4..16
@@ -88,7 +94,7 @@ typedef struct {
  *   scale        default encoding scale Delta = 2^rho
  *   seed         256-bit sampler key
  *   sigma        Gaussian standard deviation (the paper uses 3.2); tail cut at floor(6 sigma)
- *   flags        PFT_ALLOW_INSECURE
+ *   flags        PFT_ALLOW_INSECURE | PFT_COMPRESSED_KEYS
  * Security table (max log2(QP), uniform ternary secret, 128-bit): N=2^10: 27,
  * 2^11: 54, 2^12: 109, 2^13: 218, 2^14: 438, 2^15: 881, 2^16: 1772. */
 typedef struct {

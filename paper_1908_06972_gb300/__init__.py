@@ -21,6 +21,7 @@ _LIB = None
 PFT_OK, PFT_ERR_ARG, PFT_ERR_LEVEL_MISMATCH, PFT_ERR_SCALE_MISMATCH, PFT_ERR_NO_KEY = 0, 1, 2, 3, 4
 PFT_ERR_OOM, PFT_ERR_CUDA, PFT_ERR_TIMEOUT, PFT_ERR_SECURITY, PFT_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
 PFT_ALLOW_INSECURE = 1
+PFT_COMPRESSED_KEYS = 2
 PFT_ENC_PK, PFT_ENC_SK = 0, 1
 
 

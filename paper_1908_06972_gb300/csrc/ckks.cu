@@ -205,17 +205,25 @@ static void sample_signed_ntt(pft_ctx* c, u32 dom, u32 obj, u32 sub, int kind, c
 }
 
 // switching key from s' (evaluation form over the full basis, rows [L+k]) to s
+// Digit j of the key from s' to s: a_j uniform, b_j = -a_j s + e_j (+ P s' on the digit's
+// primes).  Full keys keep (b_j, a_j) with a_j drawn in coefficient form; compressed keys
+// (PFT_COMPRESSED_KEYS) keep b_j only, a_j being drawn directly in evaluation form from
+// its own stream so that the inner product can regenerate it.
 static u64* make_switch_key(pft_ctx* c, const u64* sp, u32 key_id) {
     const int n = c->n, L = c->L, k = c->k, R = L + k;
-    u64* K = (u64*)dalloc(c, (size_t)c->beta_max * 2 * R * n * 8);
+    const bool comp = c->compressed_keys;
+    u64* K = (u64*)dalloc(c, (size_t)c->beta_max * (comp ? 1 : 2) * R * n * 8);
+    std::unique_ptr<Scratch> abuf(comp ? new Scratch(c, (size_t)R * n * 8) : nullptr);
     for (int j = 0; j < c->beta_max; j++) {
-        u64* b = K + (size_t)(2 * j) * R * n;
-        u64* a = K + (size_t)(2 * j + 1) * R * n;
+        u64* b = K + (size_t)(comp ? j : 2 * j) * R * n;
+        u64* a = comp ? abuf->u() : K + (size_t)(2 * j + 1) * R * n;
         std::vector<PolyRef> ra{ref(a, R, 0, L, L)}, rb{ref(b, R, 0, L, L)};
-        chunks(1, [&](size_t x, size_t y) {
-            sample_uniform(c->tabs, c->prm.seed, DOM_KSK_A, key_id, 256u * j, mkset(ra, x, y), c->stream);
-        });
-        ntt_fwd(c, ra, ra);
+        if (comp) {
+            sample_uniform(c->tabs, c->prm.seed, kDomKskAEval, key_id, 256u * j, mkset(ra, 0, 1), c->stream);
+        } else {
+            sample_uniform(c->tabs, c->prm.seed, DOM_KSK_A, key_id, 256u * j, mkset(ra, 0, 1), c->stream);
+            ntt_fwd(c, ra, ra);
+        }
         sample_signed_ntt(c, DOM_KSK_E, key_id, (u32)j, 1, rb);  // b = e
         Scratch as(c, (size_t)R * n * 8);
         std::vector<PolyRef> ras{ref(as.u(), R, 0, L, L)}, rs{ref((u64*)c->s_ntt, R, 0, L, L)};
@@ -251,7 +259,21 @@ static void add_rot_keys(pft_ctx* c, const int32_t* steps, int n_steps) {
 // For each input d (any level): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
 // Every stage is one launch (or a few, by descriptor capacity) over all inputs, whatever
 // their levels; the key is read once per stage.
-void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>& io) {
+KeyRef keyref(pft_ctx* c, u32 key_id) {
+    NEED(c->keys.count(key_id), PFT_ERR_NO_KEY, "no such key");
+    KeyRef r;
+    r.ptr = c->keys[key_id];
+    r.id = key_id;
+    r.compressed = c->compressed_keys ? 1 : 0;
+    for (int i = 0; i < 4; i++) {
+        r.seedw[2 * i] = (u32)(c->prm.seed[i] & 0xffffffffu);
+        r.seedw[2 * i + 1] = (u32)(c->prm.seed[i] >> 32);
+    }
+    return r;
+}
+
+void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
+    const KeyRef key = keyref(c, key_id);
     const int L = c->L, k = c->k, alpha = c->alpha;
     const size_t B = io.size();
     if (B == 0) return;
@@ -516,7 +538,7 @@ static void mul_relin_group(pft_ctx* c, const pft_ct* const* a, const pft_ct* co
         u64* d = D.u() + off[i] * limb;
         io.push_back(KsIO{d + 2 * l * limb, d, d + l * limb, out[i]->data, out[i]->data + l * limb, l});
     }
-    keyswitch_batch(c, c->keys[0], io);
+    keyswitch_batch(c, 0u, io);
 }
 
 static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out) {
@@ -566,7 +588,7 @@ static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t s
         u64* r = R.u() + off[i] * limb;
         io.push_back(KsIO{r + l * limb, r, nullptr, out[i]->data, out[i]->data + l * limb, l});
     }
-    keyswitch_batch(c, c->keys[g], io);
+    keyswitch_batch(c, g, io);
 }
 
 // Rotations of one ciphertext by several steps sharing one ModUp of c1 (hoisting): the
@@ -639,7 +661,7 @@ static void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps,
             automorph(c->tabs, mkset(ein, x, y), mkset(eout, x, y), gs[i], c->stream);
         });
         KsDesc d{ExtG.u(), U.u(), l, 0};
-        ks_inner_multi(c->tabs, &d, 1, c->keys[gs[i]], L, k, alpha, c->stream);
+        ks_inner_multi(c->tabs, &d, 1, keyref(c, gs[i]), L, k, alpha, c->stream);
         // ModDown
         std::vector<PolyRef> sp, cvr;
         std::vector<BconvJob> jobs;
@@ -828,7 +850,7 @@ void relin_batch(pft_ctx* c, const std::vector<RelinIO>& io) {
             ks.push_back(KsIO{r.d + 2 * (size_t)r.l * limb, r.d, r.d + (size_t)r.l * limb, r.out->data,
                               r.out->data + (size_t)r.l * limb, r.l});
         }
-        keyswitch_batch(c, c->keys[0], ks);
+        keyswitch_batch(c, 0u, ks);
         i0 = i1;
     }
 }
@@ -910,7 +932,7 @@ void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g) {
             automorph(c->tabs, mkset(rin, x, y), mkset(rout, x, y), g, c->stream);
         });
         ew(c, EwOp::Add, tin0, rc0, tin0);
-        keyswitch_batch(c, c->keys[g], io);
+        keyswitch_batch(c, g, io);
         i0 = i1;
     }
 }
@@ -1288,6 +1310,7 @@ int pft_ctx_create(const pft_params* prm, const pft_allocator* alloc, pft_ctx** 
     std::unique_ptr<pft_ctx> c(new pft_ctx());
     int rc = guard(c.get(), [&] {
         c->prm = *prm;
+        c->compressed_keys = (prm->flags & PFT_COMPRESSED_KEYS) != 0;
         c->logn = prm->log_n;
         NEED(prm->log_n >= 4 && prm->log_n <= 16, PFT_ERR_ARG, "log_n must be in 4..16");
         NEED(prm->n_limbs >= 1 && prm->n_limbs <= kMaxLimbs, PFT_ERR_ARG, "n_limbs must be in 1..60");
@@ -1428,7 +1451,18 @@ int pft_key_export(pft_ctx* c, uint32_t key_id, uint64_t* out, size_t nw) {
         Scratch t(c, words * 8);
         std::vector<PolyRef> in, o;
         for (int i = 0; i < 2 * c->beta_max; i++) {
-            in.push_back(ref(c->keys[key_id] + (size_t)i * R * c->n, R, 0, c->L, c->L));
+            u64* src = c->keys[key_id] + (size_t)i * R * c->n;
+            if (c->compressed_keys) {
+                const int j = i / 2;
+                if (i % 2 == 0) {
+                    src = c->keys[key_id] + (size_t)j * R * c->n;
+                } else {  // regenerate a_j (evaluation form) in the output slot, then transform it there
+                    src = t.u() + (size_t)i * R * c->n;
+                    std::vector<PolyRef> ra{ref(src, R, 0, c->L, c->L)};
+                    sample_uniform(c->tabs, c->prm.seed, kDomKskAEval, key_id, 256u * j, mkset(ra, 0, 1), c->stream);
+                }
+            }
+            in.push_back(ref(src, R, 0, c->L, c->L));
             o.push_back(ref(t.u() + (size_t)i * R * c->n, R, 0, c->L, c->L));
         }
         ntt_inv(c, in, o);

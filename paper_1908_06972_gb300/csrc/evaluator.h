@@ -33,7 +33,8 @@ struct pft_ctx {
     u64* s_ntt = nullptr;  // [L+k][N]
     std::vector<i64> s_coeff;
     u64* pk = nullptr;  // [2][L][N]  (b, a)
-    std::map<u32, u64*> keys;
+    std::map<u32, u64*> keys;  // [beta][2][L+k][N], or [beta][L+k][N] (b only) when compressed
+    bool compressed_keys = false;
 };
 
 struct pft_ct {
@@ -201,7 +202,9 @@ struct KsIO {
     int l;  // level of this input
 };
 // For each input d (any level): (out0, out1) = (acc0, acc1) + ModDown(sum_j ModUp_j(d) * key_j).
-void keyswitch_batch(pft_ctx* c, const u64* key, const std::vector<KsIO>& io);
+void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io);
+// The key as the inner product reads it (full or compressed).
+KeyRef keyref(pft_ctx* c, u32 key_id);
 void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out, EwOp op);
 void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B, pft_ct* const* out);
 void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out);

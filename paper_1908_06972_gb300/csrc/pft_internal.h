@@ -138,7 +138,18 @@ struct KsDesc {
     int pad;
 };
 constexpr int kMaxKs = 128;  // inputs per launch (by-value parameters)
-void ks_inner_multi(const DevTables& t, const KsDesc* descs_host, int B, const u64* key, int L, int k, int alpha,
+// A switching key as the inner product reads it: [beta][2 (b, a)][L+k][N] in evaluation form,
+// or, compressed, only the b rows [beta][L+k][N] with a regenerated from the ChaCha20 stream
+// (seed words, domain DOM_KSK_A_EVAL, object = key id, sub = 256 j + row), entry i of row r
+// = the uniform residue of word pair i, already in evaluation form.
+constexpr u32 kDomKskAEval = 11;
+struct KeyRef {
+    const u64* ptr;
+    u32 id;
+    int compressed;
+    u32 seedw[8];
+};
+void ks_inner_multi(const DevTables& t, const KsDesc* descs_host, int B, const KeyRef& key, int L, int k, int alpha,
                     cudaStream_t st);
 // r = (last + h) mod p, h = floor(p/2), p = prime nlimbs(out); limb k of out = (r - h) mod q_k.
 void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st);

@@ -376,148 +376,6 @@ void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st
     }
 }
 
-// ---- key inner product over inputs at different levels -----------------------------------
-// Row `row` of the key (q rows 0..L-1, special rows L..L+k-1) is used by every input whose
-// level l exceeds it (q rows) or by every input (special rows); for input b its extended row
-// is m = row (q rows) or l + row - L.  The key slice of two coefficients (digits up to the
-// largest the participating inputs need) stays in registers across all inputs.
-template <int BMAX>
-__global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt, int B, const u64* key, int L, int k,
-                                                        int alpha) {
-    const int row = blockIdx.y;
-    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (2 * x2 >= t.n) return;
-    const int logn = t.logn;
-    const int rows_total = L + k;
-    const int need = bt.need[row];
-    if (need == 0) return;
-    const DPrime P = load_prime(t.primes, row);
-    const size_t xo = 2 * (size_t)x2;
-    ulonglong2 kb[BMAX], ka[BMAX];
-#pragma unroll
-    for (int j = 0; j < BMAX; j++) {
-        if (j < need) {
-            kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + xo));
-            ka[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + xo));
-        }
-    }
-    for (int b = 0; b < B; b++) {
-        const KsDesc D = bt.d[b];
-        const int l = D.l;
-        if (row < L && row >= l) continue;
-        const int m = row < L ? row : l + row - L;
-        const int E = l + k;
-        const int beta = (l + alpha - 1) / alpha;
-        ulonglong2 v[BMAX];
-#pragma unroll
-        for (int j = 0; j < BMAX; j++)
-            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(D.ext + (((size_t)j * E + m) << logn) + xo));
-        U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
-#pragma unroll
-        for (int j = 0; j < BMAX; j++) {
-            if (j < beta) {  // beta <= 8: 128-bit sums of at most 8 products
-                mac_wide(s0x, v[j].x, kb[j].x);
-                mac_wide(s0y, v[j].y, kb[j].y);
-                mac_wide(s1x, v[j].x, ka[j].x);
-                mac_wide(s1y, v[j].y, ka[j].y);
-            }
-        }
-        ulonglong2 r0, r1;
-        r0.x = barrett_reduce(s0x.hi, s0x.lo, P);
-        r0.y = barrett_reduce(s0y.hi, s0y.lo, P);
-        r1.x = barrett_reduce(s1x.hi, s1x.lo, P);
-        r1.y = barrett_reduce(s1y.hi, s1y.lo, P);
-        *reinterpret_cast<ulonglong2*>(D.u + ((size_t)m << logn) + xo) = r0;
-        *reinterpret_cast<ulonglong2*>(D.u + (((size_t)E + m) << logn) + xo) = r1;
-    }
-}
-
-// Any number of digits: the key is re-read for every input.
-__global__ void k_ks_inner_multi_generic(DevTables t, KsBatch bt, int B, const u64* key, int L, int k, int alpha) {
-    const int row = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= t.n) return;
-    const int logn = t.logn;
-    const int rows_total = L + k;
-    const DPrime P = load_prime(t.primes, row);
-    for (int b = 0; b < B; b++) {
-        const KsDesc D = bt.d[b];
-        const int l = D.l;
-        if (row < L && row >= l) continue;
-        const int m = row < L ? row : l + row - L;
-        const int E = l + k;
-        const int beta = (l + alpha - 1) / alpha;
-        U128 s0 = {0, 0}, s1 = {0, 0};
-        for (int j = 0; j < beta; j++) {
-            const u64 v = __ldg(D.ext + (((size_t)j * E + m) << logn) + x);
-            mac_wide(s0, v, __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x));
-            mac_wide(s1, v, __ldg(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + x));
-            if ((j & 7) == 7) {
-                s0.lo = barrett_reduce(s0.hi, s0.lo, P);
-                s0.hi = 0;
-                s1.lo = barrett_reduce(s1.hi, s1.lo, P);
-                s1.hi = 0;
-            }
-        }
-        D.u[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
-        D.u[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
-    }
-}
-
-void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const u64* key, int L, int k, int alpha,
-                    cudaStream_t st) {
-    const int beta_max = (L + alpha - 1) / alpha;
-    for (int a = 0; a < B; a += kMaxKs) {
-        const int cnt = B - a < kMaxKs ? B - a : kMaxKs;
-        KsBatch bt;
-        double bytes = 0;
-        int lmax = 0;
-        for (int r = 0; r < kMaxPrimes; r++) bt.need[r] = 0;
-        for (int i = 0; i < cnt; i++) {
-            bt.d[i] = descs[a + i];
-            const int l = descs[a + i].l, E = l + k, beta = (l + alpha - 1) / alpha;
-            bytes += (double)(beta + 2) * E * t.n * 8.0;
-            lmax = max(lmax, l);
-            for (int r = 0; r < L + k; r++)
-                if ((r >= L || r < l) && bt.need[r] < beta) bt.need[r] = (uint8_t)beta;
-        }
-        bytes += 2.0 * ((lmax + alpha - 1) / alpha) * (lmax + k) * t.n * 8.0;  // key rows and digits read
-        dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(L + k));
-        dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(L + k));
-        PFT_PROF("ks_inner", st, bytes);
-        if (beta_max <= 4) k_ks_inner_multi<4><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
-        else if (beta_max <= 8) k_ks_inner_multi<8><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
-        else k_ks_inner_multi_generic<<<grid1, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
-        PFT_LAUNCH_CHECK("ks_inner_multi");
-    }
-}
-
-// ---- rescale broadcast: r = (c_{l-1} + h) mod p, h = floor(p/2), per coefficient; every
-// lower limb k receives (r - h) mod q_k (coefficient form), so that after the transform
-// c'_k = (c_k - out_k) p^-1 = (c_k + h - r) / p coefficient by coefficient.
-// last: coefficient-form last limb of each polynomial; out: [l-1][N] per polynomial.
-__global__ void k_rescale_bcast(DevTables t, PolySet last, PolySet out) {
-    const int poly = blockIdx.z, limb = blockIdx.y;
-    const PolyRef& Ro = out.p[poly];
-    if (limb >= Ro.nlimbs) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= t.n) return;
-    const int lp = Ro.nlimbs;  // index of the dropped prime
-    const u64 p = __ldg(&t.primes[lp].q);
-    u64 r = __ldg(last.p[poly].ptr + x) + (p >> 1);
-    if (r >= p) r -= p;
-    const DPrime P = load_prime(t.primes, limb);
-    Ro.ptr[((size_t)limb << t.logn) + x] = submod(reduce64(r, P), reduce64(p >> 1, P), P.q);
-}
-
-void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st) {
-    if (out.count == 0) return;
-    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
-    PFT_PROF("rescale_bcast", st, set_limbs(out) * t.n * 8.0);
-    k_rescale_bcast<<<grid, 256, 0, st>>>(t, last, out);
-    PFT_LAUNCH_CHECK("rescale_bcast");
-}
-
 // ---- ChaCha20 sampler (RFC 8439 block function, counter mode) -----------------------------
 __device__ __forceinline__ u32 rotl(u32 x, int n) { return __funnelshift_l(x, x, n); }
 #define PFT_QR(a, b, c, d)                \
@@ -561,6 +419,182 @@ static SeedKey seed_key(const u64 seed[4]) {
     return k;
 }
 
+// (hi 2^64 + lo) mod q = ((hi mod q) (2^64 mod q) + lo) mod q; the sum is below
+// q^2 + 2^64 < 2^(63 + bitlen(q)), inside the Barrett bound.
+__device__ __forceinline__ u64 uniform_mod(u64 lo, u64 hi, const DPrime& P) {
+    const u64 hr = reduce64(hi, P);
+    U128 acc = mul_wide(hr, P.r64);
+    acc.lo += lo;
+    acc.hi += (acc.lo < lo) ? 1 : 0;
+    return barrett_reduce(acc.hi, acc.lo, P);
+}
+
+// ---- key inner product over inputs at different levels -----------------------------------
+// Row `row` of the key (q rows 0..L-1, special rows L..L+k-1) is used by every input whose
+// level l exceeds it (q rows) or by every input (special rows); for input b its extended row
+// is m = row (q rows) or l + row - L.  The key slice of two coefficients (digits up to the
+// largest the participating inputs need) stays in registers across all inputs.
+template <int BMAX, bool COMP>
+__global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt, int B, KeyRef kr, int L, int k,
+                                                        int alpha) {
+    const u64* key = kr.ptr;
+    const int row = blockIdx.y;
+    const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * x2 >= t.n) return;
+    const int logn = t.logn;
+    const int rows_total = L + k;
+    const int need = bt.need[row];
+    if (need == 0) return;
+    const DPrime P = load_prime(t.primes, row);
+    const size_t xo = 2 * (size_t)x2;
+    ulonglong2 kb[BMAX], ka[BMAX];
+#pragma unroll
+    for (int j = 0; j < BMAX; j++) {
+        if (j < need) {
+            if (!COMP) {
+                kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + xo));
+                ka[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + xo));
+            } else {
+                kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + (((size_t)j * rows_total + row) << logn) + xo));
+                // block xo/4 holds coefficients 4(xo/4) .. +3; this thread's two are at xo & 3
+                u64 w[8];
+                chacha_block(kr.seedw, (u32)(xo >> 2), kDomKskAEval, kr.id, 256u * j + (u32)row, w);
+                const int c0 = (int)(xo & 3);
+                ka[j].x = uniform_mod(w[2 * c0], w[2 * c0 + 1], P);
+                ka[j].y = uniform_mod(w[2 * c0 + 2], w[2 * c0 + 3], P);
+            }
+        }
+    }
+    for (int b = 0; b < B; b++) {
+        const KsDesc D = bt.d[b];
+        const int l = D.l;
+        if (row < L && row >= l) continue;
+        const int m = row < L ? row : l + row - L;
+        const int E = l + k;
+        const int beta = (l + alpha - 1) / alpha;
+        ulonglong2 v[BMAX];
+#pragma unroll
+        for (int j = 0; j < BMAX; j++)
+            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(D.ext + (((size_t)j * E + m) << logn) + xo));
+        U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
+#pragma unroll
+        for (int j = 0; j < BMAX; j++) {
+            if (j < beta) {  // beta <= 8: 128-bit sums of at most 8 products
+                mac_wide(s0x, v[j].x, kb[j].x);
+                mac_wide(s0y, v[j].y, kb[j].y);
+                mac_wide(s1x, v[j].x, ka[j].x);
+                mac_wide(s1y, v[j].y, ka[j].y);
+            }
+        }
+        ulonglong2 r0, r1;
+        r0.x = barrett_reduce(s0x.hi, s0x.lo, P);
+        r0.y = barrett_reduce(s0y.hi, s0y.lo, P);
+        r1.x = barrett_reduce(s1x.hi, s1x.lo, P);
+        r1.y = barrett_reduce(s1y.hi, s1y.lo, P);
+        *reinterpret_cast<ulonglong2*>(D.u + ((size_t)m << logn) + xo) = r0;
+        *reinterpret_cast<ulonglong2*>(D.u + (((size_t)E + m) << logn) + xo) = r1;
+    }
+}
+
+// Any number of digits: the key is re-read (or regenerated) for every input.
+__global__ void k_ks_inner_multi_generic(DevTables t, KsBatch bt, int B, KeyRef kr, int L, int k, int alpha) {
+    const u64* key = kr.ptr;
+    const int row = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= t.n) return;
+    const int logn = t.logn;
+    const int rows_total = L + k;
+    const DPrime P = load_prime(t.primes, row);
+    for (int b = 0; b < B; b++) {
+        const KsDesc D = bt.d[b];
+        const int l = D.l;
+        if (row < L && row >= l) continue;
+        const int m = row < L ? row : l + row - L;
+        const int E = l + k;
+        const int beta = (l + alpha - 1) / alpha;
+        U128 s0 = {0, 0}, s1 = {0, 0};
+        for (int j = 0; j < beta; j++) {
+            const u64 v = __ldg(D.ext + (((size_t)j * E + m) << logn) + x);
+            u64 kb, ka;
+            if (!kr.compressed) {
+                kb = __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x);
+                ka = __ldg(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + x);
+            } else {
+                kb = __ldg(key + (((size_t)j * rows_total + row) << logn) + x);
+                u64 w[8];
+                chacha_block(kr.seedw, (u32)(x >> 2), kDomKskAEval, kr.id, 256u * j + (u32)row, w);
+                ka = uniform_mod(w[2 * (x & 3)], w[2 * (x & 3) + 1], P);
+            }
+            mac_wide(s0, v, kb);
+            mac_wide(s1, v, ka);
+            if ((j & 7) == 7) {
+                s0.lo = barrett_reduce(s0.hi, s0.lo, P);
+                s0.hi = 0;
+                s1.lo = barrett_reduce(s1.hi, s1.lo, P);
+                s1.hi = 0;
+            }
+        }
+        D.u[((size_t)m << logn) + x] = barrett_reduce(s0.hi, s0.lo, P);
+        D.u[(((size_t)E + m) << logn) + x] = barrett_reduce(s1.hi, s1.lo, P);
+    }
+}
+
+void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const KeyRef& key, int L, int k, int alpha,
+                    cudaStream_t st) {
+    const int beta_max = (L + alpha - 1) / alpha;
+    for (int a = 0; a < B; a += kMaxKs) {
+        const int cnt = B - a < kMaxKs ? B - a : kMaxKs;
+        KsBatch bt;
+        double bytes = 0;
+        int lmax = 0;
+        for (int r = 0; r < kMaxPrimes; r++) bt.need[r] = 0;
+        for (int i = 0; i < cnt; i++) {
+            bt.d[i] = descs[a + i];
+            const int l = descs[a + i].l, E = l + k, beta = (l + alpha - 1) / alpha;
+            bytes += (double)(beta + 2) * E * t.n * 8.0;
+            lmax = max(lmax, l);
+            for (int r = 0; r < L + k; r++)
+                if ((r >= L || r < l) && bt.need[r] < beta) bt.need[r] = (uint8_t)beta;
+        }
+        bytes += (key.compressed ? 1.0 : 2.0) * ((lmax + alpha - 1) / alpha) * (lmax + k) * t.n * 8.0;  // key rows read
+        dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(L + k));
+        dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(L + k));
+        PFT_PROF("ks_inner", st, bytes);
+        if (beta_max <= 4 && !key.compressed) k_ks_inner_multi<4, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        else if (beta_max <= 8 && !key.compressed) k_ks_inner_multi<8, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        else if (beta_max <= 4) k_ks_inner_multi<4, true><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        else if (beta_max <= 8) k_ks_inner_multi<8, true><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        else k_ks_inner_multi_generic<<<grid1, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        PFT_LAUNCH_CHECK("ks_inner_multi");
+    }
+}
+
+// ---- rescale broadcast: r = (c_{l-1} + h) mod p, h = floor(p/2), per coefficient; every
+// lower limb k receives (r - h) mod q_k (coefficient form), so that after the transform
+// c'_k = (c_k - out_k) p^-1 = (c_k + h - r) / p coefficient by coefficient.
+// last: coefficient-form last limb of each polynomial; out: [l-1][N] per polynomial.
+__global__ void k_rescale_bcast(DevTables t, PolySet last, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= t.n) return;
+    const int lp = Ro.nlimbs;  // index of the dropped prime
+    const u64 p = __ldg(&t.primes[lp].q);
+    u64 r = __ldg(last.p[poly].ptr + x) + (p >> 1);
+    if (r >= p) r -= p;
+    const DPrime P = load_prime(t.primes, limb);
+    Ro.ptr[((size_t)limb << t.logn) + x] = submod(reduce64(r, P), reduce64(p >> 1, P), P.q);
+}
+
+void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("rescale_bcast", st, set_limbs(out) * t.n * 8.0);
+    k_rescale_bcast<<<grid, 256, 0, st>>>(t, last, out);
+    PFT_LAUNCH_CHECK("rescale_bcast");
+}
+
 // uniform mod q: block b (counter b) gives coefficients 4b..4b+3 from word pairs.
 __global__ void k_sample_uniform(DevTables t, SeedKey key, u32 dom, u32 obj, u32 sub_base, PolySet out) {
     const int poly = blockIdx.z, limb = blockIdx.y;
@@ -574,15 +608,7 @@ __global__ void k_sample_uniform(DevTables t, SeedKey key, u32 dom, u32 obj, u32
     chacha_block(key.w, (u32)b, dom, obj, sub_base + (u32)pi, w);
     u64* dst = Ro.ptr + ((size_t)limb << t.logn) + 4 * (size_t)b;
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-        // (hi 2^64 + lo) mod q = ((hi mod q) (2^64 mod q) + lo) mod q; the sum is below
-        // q^2 + 2^64 < 2^(63 + bitlen(q)), inside the Barrett bound.
-        const u64 hr = reduce64(w[2 * c + 1], P);
-        U128 acc = mul_wide(hr, P.r64);
-        acc.lo += w[2 * c];
-        acc.hi += (acc.lo < w[2 * c]) ? 1 : 0;
-        dst[c] = barrett_reduce(acc.hi, acc.lo, P);
-    }
+    for (int c = 0; c < 4; c++) dst[c] = uniform_mod(w[2 * c], w[2 * c + 1], P);
 }
 
 void sample_uniform(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 sub_base, const PolySet& out,

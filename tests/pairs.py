@@ -6,11 +6,13 @@ from oracle import ckks
 
 class Pair:
     def __init__(self, pft, logn, L, k, alpha, first_bits=60, mid_bits=40, special_bits=60, scale=2.0 ** 40,
-                 seed=(0x5EED, 11, 22, 33), rot_steps=(), relin=True, insecure=True, gpu_keys=True):
+                 seed=(0x5EED, 11, 22, 33), rot_steps=(), relin=True, insecure=True, gpu_keys=True, compressed=False):
         self.pft = pft
-        self.orc = ckks.Oracle(logn, L, k, alpha, first_bits, mid_bits, special_bits, scale, seed)
+        self.orc = ckks.Oracle(logn, L, k, alpha, first_bits, mid_bits, special_bits, scale, seed,
+                               compressed_keys=compressed)
+        flags = (pft.PFT_ALLOW_INSECURE if insecure else 0) | (pft.PFT_COMPRESSED_KEYS if compressed else 0)
         self.ctx = pft.pft_ctx_create(logn, L, k, alpha, first_bits, mid_bits, special_bits, scale, seed,
-                                      flags=pft.PFT_ALLOW_INSECURE if insecure else 0)
+                                      flags=flags)
         self.N = 1 << logn
         self.rot_steps = tuple(rot_steps)
         if gpu_keys:

@@ -384,3 +384,38 @@ def test_fasttext_diagonal_bit_exact_n12(p1):
         assert np.max(np.abs(got - OF.plain_scores(v[:m], H, O))) < 2.0 ** -20
     finally:
         pf.pft_ft_model_destroy(model)
+
+
+# ---- seeded compressed switching keys -----------------------------------------------------------
+@pytest.mark.parametrize("logn,L,k,alpha,mid", [(12, 3, 1, 1, 40), (12, 10, 1, 1, 40), (16, 6, 2, 4, 50)])
+def test_compressed_keys_bit_exact(gpu, logn, L, k, alpha, mid):
+    """Keys keep only b_j; the key inner product regenerates a_j from the seed.  Keys (with a_j
+    regenerated for export), HMUL + relinearisation, rotations (plain and hoisted) and a
+    mixed-level batch against the oracle's compressed keys.  L = 10 with one prime per digit
+    takes the inner-product kernel for more than 8 digits."""
+    p = Pair(gpu, logn, L, k, alpha, mid_bits=mid, rot_steps=[1, 3], compressed=True)
+    try:
+        o, pf, ctx = p.orc, p.pft, p.ctx
+        assert np.array_equal(pf.pft_key_export(ctx, 0), o.keys[0])
+        g = OK.galois_element(3, p.N)
+        assert np.array_equal(pf.pft_key_export(ctx, g), o.keys[g])
+        n_slots = min(p.N // 2, 512)
+        lv = [L, max(1, L - 2), max(1, L // 2)]
+        A = [o.encrypt_sk(o.encode(synth.slots(60 + i, n_slots), level=l), 70 + i) for i, l in enumerate(lv)]
+        B = [o.encrypt_pk(o.encode(synth.slots(80 + i, n_slots), level=l), 90 + i) for i, l in enumerate(lv)]
+        gA, gB = [p.ct(x) for x in A], [p.ct(x) for x in B]
+        C = [p.empty() for _ in lv]
+        pf.pft_mul_relin_batch(ctx, gA, gB, C)
+        M = [o.mul_relin(a, b) for a, b in zip(A, B)]
+        for i in range(len(lv)):
+            p.assert_equal(C[i], M[i], "compressed mul_relin l=%d" % lv[i])
+        pf.pft_rotate_batch(ctx, C, 1, C)
+        for i in range(len(lv)):
+            p.assert_equal(C[i], o.rotate(M[i], 1), "compressed rotate l=%d" % lv[i])
+        outs = [p.empty(), p.empty()]
+        pf.pft_rotate_hoisted(ctx, gA[0], [1, 3], outs)
+        want = o.rotate_hoisted(A[0], [1, 3])
+        for i in range(2):
+            p.assert_equal(outs[i], want[i], "compressed hoisted %d" % i)
+    finally:
+        p.close()
