@@ -206,6 +206,11 @@ int pft_ct_export(pft_ctx* ctx, const pft_ct* ct, uint64_t* coeffs, size_t n);
 int pft_ct_import_batch(pft_ctx* ctx, const uint64_t* const* coeffs, const int* levels, const double* scales, int B,
                         pft_ct** out);
 int pft_ct_export_batch(pft_ctx* ctx, const pft_ct* const* cts, int B, uint64_t* const* coeffs);
+/* The same without the final synchronisation: the copies are queued on the context's stream
+ * and coeffs[i] (page-locked host memory) holds the result once that stream has reached
+ * this point (an event or a stream synchronisation by the caller); cts must not be modified
+ * before then. */
+int pft_ct_export_batch_async(pft_ctx* ctx, const pft_ct* const* cts, int B, uint64_t* const* coeffs);
 
 /* ---- homomorphic operations (Sec. 2.3) ------------------------------------
  * `out` must be a handle from pft_ct_create / an op; it is resized as needed. */

@@ -90,7 +90,7 @@ def lib():
             "pft_encrypt": [vp, vp, i, u32, pp], "pft_decrypt": [vp, vp, pp],
             "pft_ct_import": [vp, u64, i, d, pp], "pft_ct_export": [vp, vp, u64, c_size_t],
             "pft_ct_import_batch": [vp, pp, ip, POINTER(c_double), i, pp],
-            "pft_ct_export_batch": [vp, pp, i, pp],
+            "pft_ct_export_batch": [vp, pp, i, pp], "pft_ct_export_batch_async": [vp, pp, i, pp],
             "pft_add": [vp, vp, vp, vp], "pft_sub": [vp, vp, vp, vp], "pft_add_plain": [vp, vp, vp, vp],
             "pft_mul_plain": [vp, vp, vp, vp], "pft_mul_relin": [vp, vp, vp, vp],
             "pft_rescale": [vp, vp, vp], "pft_rotate": [vp, vp, c_int32, vp],
@@ -160,7 +160,8 @@ def exported_symbols():
             "pft_server_get_stats", "pft_server_footprint", "pft_drop_level", "pft_add_const", "pft_mul_const",
             "pft_ct_set_scale", "pft_ft_enc_model_create", "pft_ft_enc_model_get", "pft_ft_enc_model_levels",
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
-            "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update"]
+            "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
+            "pft_ct_export_batch_async"]
 
 
 def _check(rc, ctx=None):
@@ -398,6 +399,14 @@ def pft_ct_export_batch(ctx, cts, arrays):
     """Exports cts[i] into the uint64 [2][l][N] host array arrays[i] (one synchronisation)."""
     ptrs = (c_void_p * max(1, len(arrays)))(*[a.ctypes.data for a in arrays])
     _check(lib().pft_ct_export_batch(ctx, _arr(cts), len(cts), ptrs), ctx)
+    return arrays
+
+
+def pft_ct_export_batch_async(ctx, cts, arrays):
+    """Queues the export of cts[i] into arrays[i] (page-locked) on the context's stream without
+    waiting; the arrays hold the results once that stream has reached this point."""
+    ptrs = (c_void_p * max(1, len(arrays)))(*[a.ctypes.data for a in arrays])
+    _check(lib().pft_ct_export_batch_async(ctx, _arr(cts), len(cts), ptrs), ctx)
     return arrays
 
 

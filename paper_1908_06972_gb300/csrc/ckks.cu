@@ -1600,32 +1600,54 @@ int pft_ct_import_batch(pft_ctx* c, const uint64_t* const* coeffs, const int* le
     });
 }
 
+static void export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs, bool sync);
+
 int pft_ct_export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs) {
-    return guard(c, [&] {
+    return guard(c, [&] { export_batch(c, cts, B, coeffs, true); });
+}
+
+int pft_ct_export_batch_async(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs) {
+    return guard(c, [&] { export_batch(c, cts, B, coeffs, false); });
+}
+
+static void export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs, bool sync) {
+    {
         NEED(c && cts && coeffs && B >= 0, PFT_ERR_ARG, "bad arguments");
-        size_t tot = 0;
-        std::vector<size_t> off(B);
+        size_t maxw = 0;
         for (int i = 0; i < B; i++) {
             check_ct(cts[i]);
             NEED(coeffs[i], PFT_ERR_ARG, "null output buffer");
-            off[i] = tot;
-            tot += (size_t)2 * cts[i]->level * c->n;
+            maxw = std::max(maxw, (size_t)2 * cts[i]->level * c->n);
         }
-        Scratch t(c, tot * 8);
-        std::vector<PolyRef> in, o;
-        for (int i = 0; i < B; i++) {
-            const int l = cts[i]->level;
-            for (int pol = 0; pol < 2; pol++) {
-                in.push_back(cpoly(cts[i]->data, l, c->n, pol));
-                o.push_back(cpoly(t.u() + off[i], l, c->n, pol));
+        if (B == 0) return;
+        // groups of ciphertexts through one staging buffer of at most 256 MiB (or one
+        // ciphertext), reused in stream order: transform, copy out, next group
+        const size_t cap = std::max(maxw, ((size_t)256 << 20) / 8);
+        Scratch t(c, cap * 8);
+        int i0 = 0;
+        while (i0 < B) {
+            int i1 = i0;
+            size_t used = 0;
+            std::vector<size_t> off;
+            std::vector<PolyRef> in, o;
+            while (i1 < B && used + (size_t)2 * cts[i1]->level * c->n <= cap) {
+                const int l = cts[i1]->level;
+                off.push_back(used);
+                for (int pol = 0; pol < 2; pol++) {
+                    in.push_back(cpoly(cts[i1]->data, l, c->n, pol));
+                    o.push_back(cpoly(t.u() + used, l, c->n, pol));
+                }
+                used += (size_t)2 * l * c->n;
+                i1++;
             }
+            ntt_inv(c, in, o);
+            for (int i = i0; i < i1; i++)
+                PFT_CUDA(cudaMemcpyAsync(coeffs[i], t.u() + off[i - i0], (size_t)2 * cts[i]->level * c->n * 8,
+                                         cudaMemcpyDeviceToHost, c->stream));
+            i0 = i1;
         }
-        ntt_inv(c, in, o);
-        for (int i = 0; i < B; i++)
-            PFT_CUDA(cudaMemcpyAsync(coeffs[i], t.u() + off[i], (size_t)2 * cts[i]->level * c->n * 8,
-                                     cudaMemcpyDeviceToHost, c->stream));
-        PFT_CUDA(cudaStreamSynchronize(c->stream));
-    });
+        if (sync) PFT_CUDA(cudaStreamSynchronize(c->stream));
+    }
 }
 
 int pft_encode(pft_ctx* c, const double* re_im, int n_slots, double scale, int level, pft_pt** out) {

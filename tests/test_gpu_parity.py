@@ -288,6 +288,13 @@ def test_batched_import_export_round_trip(p1):
     pf.pft_ct_export_batch(p1.ctx, hs, outs)
     for c, arr in zip(cts, outs):
         assert np.array_equal(arr, c.c)
+    # asynchronous form into page-locked buffers, read after the stream has caught up
+    import torch
+    pinned = [torch.zeros(c.c.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64) for c in cts]
+    pf.pft_ct_export_batch_async(p1.ctx, hs, pinned)
+    torch.cuda.synchronize()
+    for c, arr in zip(cts, pinned):
+        assert np.array_equal(arr, c.c)
 
 
 def test_graph_replay_matches_oracle(gpu):
