@@ -246,24 +246,32 @@ def run_gpu(args):
                                                               [sc for _, sc in host_in]))
 
     pending = []
+    host = {"import": 0.0, "compute": 0.0, "export": 0.0, "wait": 0.0}
 
     def step_e2e(k, cur, last):
         ins, ready = cur
         S.wait_event(ready)
+        h0 = time.perf_counter()
         nxt = import_next() if not last else None
+        h1 = time.perf_counter()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(S)
         out_cts, out_host = C2[k % 2], outs2[k % 2]
         step_batched(ins[0::2], ins[1::2], out_cts)
         ev[1].record(S)
+        h2 = time.perf_counter()
         Cs.wait_event(ev[1])
         _, done = on_copy_stream(lambda: pft.pft_ct_export_batch_async(ctx, out_cts, out_host))
         pending.append((done, ins))
+        h3 = time.perf_counter()
         while len(pending) > 1:  # the previous step's results have landed: release its inputs
             d, old = pending.pop(0)
             d.synchronize()
             for h in old:
                 pft.pft_ct_destroy(h)
+        h4 = time.perf_counter()
+        for key, dt in (("import", h1 - h0), ("compute", h2 - h1), ("export", h3 - h2), ("wait", h4 - h3)):
+            host[key] += dt
         marks.append(ev)
         return nxt
 
@@ -278,6 +286,8 @@ def run_gpu(args):
     drain()
     barrier()
     marks.clear()
+    for key in host:
+        host[key] = 0.0
     t0 = time.perf_counter()
     cur = import_next()
     for k in range(args.steps):
@@ -287,7 +297,8 @@ def run_gpu(args):
     e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
     e2e = throughput(BATCH * args.steps, world, e2e_s)
     e2e_split = {"compute_ms": round(sum(ev[0].elapsed_time(ev[1]) for ev in marks) / len(marks), 2),
-                 "wall_ms": round(1e3 * e2e_s / args.steps, 2)}
+                 "wall_ms": round(1e3 * e2e_s / args.steps, 2),
+                 "host_ms": {key: round(1e3 * v / args.steps, 2) for key, v in host.items()}}
     for h in C2[1]:
         pft.pft_ct_destroy(h)
 

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cstdlib>
+
 #include "modarith.cuh"
 
 namespace pft {
@@ -287,9 +289,28 @@ void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g,
 // halves: low word = c mod 2^30, high word = c >> 30).  NS (the number of source primes) is a
 // compile-time constant; each thread converts two adjacent coefficients for two targets at
 // a time (four independent accumulation chains).
-template <int NS>
+template <int NS, int TP>
 __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
+    extern __shared__ u64 bsm[];
     const BconvJob J = jobs.j[blockIdx.y];
+    const int gap = J.skip_hi - J.skip_lo;
+    const int nt = J.nrows - gap;
+    // the job's constants and, per target, its output row, prime and Montgomery constant,
+    // staged once per CTA so that the accumulation loop reads only shared memory
+    uint2* sT = reinterpret_cast<uint2*>(bsm);          // [nt][NS] (30-bit split)
+    u64* sQ = bsm + (size_t)nt * NS;                    // [nt] target prime
+    u64* sM = sQ + nt;                                  // [nt] -q^-1 mod 2^64
+    u32* sRow = reinterpret_cast<u32*>(sM + nt);        // [nt] output row
+    const uint2* T = reinterpret_cast<const uint2*>(J.table + 2 * NS);
+    for (int i = threadIdx.x; i < nt * NS; i += blockDim.x) sT[i] = __ldg(&T[i]);
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const int m = i < J.skip_lo ? i : i + gap;
+        const int tp = m < J.split ? m : J.base2 + m - J.split;
+        sQ[i] = __ldg(&t.primes[tp].q);
+        sM[i] = __ldg(&t.primes[tp].mneg);
+        sRow[i] = (u32)m;
+    }
+    __syncthreads();
     const int x2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * x2 >= t.n) return;
     const int logn = t.logn;
@@ -308,43 +329,38 @@ __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
         split30(ya[i], ya0[i], ya1[i]);
         split30(yb[i], yb0[i], yb1[i]);
     }
-    // constants stored pre-split: low word = c mod 2^30, high word = c >> 30
-    const uint2* T = reinterpret_cast<const uint2*>(J.table + 2 * NS);
-    const int gap = J.skip_hi - J.skip_lo;
-    const int nt = J.nrows - gap;
-    for (int m0 = 0; m0 < nt; m0 += 2) {
-        const int m1i = m0 + 1 < nt ? m0 + 1 : m0;
-        Acc3 a0 = {0, 0, 0}, b0 = {0, 0, 0}, a1 = {0, 0, 0}, b1 = {0, 0, 0};
+    u64* dst = J.dst + 2 * (size_t)x2;
+    // TP targets per iteration (the last group may repeat a target; its result is not stored)
+    for (int m0 = 0; m0 < nt; m0 += TP) {
+        Acc3 a[TP], b[TP];
+        const uint2* cp[TP];
+#pragma unroll
+        for (int u = 0; u < TP; u++) {
+            a[u] = {0, 0, 0};
+            b[u] = {0, 0, 0};
+            cp[u] = sT + (m0 + u < nt ? m0 + u : m0) * NS;
+        }
 #pragma unroll
         for (int i = 0; i < NS; i++) {
-            const uint2 c0 = __ldg(&T[(size_t)m0 * NS + i]);
-            const uint2 c1 = __ldg(&T[(size_t)m1i * NS + i]);
-            acc3_mac(a0, ya0[i], ya1[i], c0.x, c0.y);
-            acc3_mac(b0, yb0[i], yb1[i], c0.x, c0.y);
-            acc3_mac(a1, ya0[i], ya1[i], c1.x, c1.y);
-            acc3_mac(b1, yb0[i], yb1[i], c1.x, c1.y);
+#pragma unroll
+            for (int u = 0; u < TP; u++) {
+                const uint2 c = cp[u][i];
+                acc3_mac(a[u], ya0[i], ya1[i], c.x, c.y);
+                acc3_mac(b[u], yb0[i], yb1[i], c.x, c.y);
+            }
         }
         // constants are c 2^64 mod t, so a Montgomery reduction of the sum (< t 2^63) gives
         // sum y_i c_i mod t
-        {
-            const int m = m0 < J.skip_lo ? m0 : m0 + gap;
-            const int tp = m < J.split ? m : J.base2 + m - J.split;
-            const u64 q = __ldg(&t.primes[tp].q), mneg = __ldg(&t.primes[tp].mneg);
-            const U128 va = acc3_value(a0), vb = acc3_value(b0);
-            ulonglong2 r;
-            r.x = mont_reduce(va.hi, va.lo, q, mneg);
-            r.y = mont_reduce(vb.hi, vb.lo, q, mneg);
-            *reinterpret_cast<ulonglong2*>(J.dst + ((size_t)m << logn) + 2 * (size_t)x2) = r;
-        }
-        if (m0 + 1 < nt) {
-            const int m = m1i < J.skip_lo ? m1i : m1i + gap;
-            const int tp = m < J.split ? m : J.base2 + m - J.split;
-            const u64 q = __ldg(&t.primes[tp].q), mneg = __ldg(&t.primes[tp].mneg);
-            const U128 va = acc3_value(a1), vb = acc3_value(b1);
-            ulonglong2 r;
-            r.x = mont_reduce(va.hi, va.lo, q, mneg);
-            r.y = mont_reduce(vb.hi, vb.lo, q, mneg);
-            *reinterpret_cast<ulonglong2*>(J.dst + ((size_t)m << logn) + 2 * (size_t)x2) = r;
+#pragma unroll
+        for (int u = 0; u < TP; u++) {
+            if (m0 + u < nt) {
+                const u64 q = sQ[m0 + u], mneg = sM[m0 + u];
+                const U128 va = acc3_value(a[u]), vb = acc3_value(b[u]);
+                ulonglong2 r;
+                r.x = mont_reduce(va.hi, va.lo, q, mneg);
+                r.y = mont_reduce(vb.hi, vb.lo, q, mneg);
+                *reinterpret_cast<ulonglong2*>(dst + ((size_t)sRow[m0 + u] << logn)) = r;
+            }
         }
     }
 }
@@ -358,18 +374,23 @@ void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st
         for (size_t a = 0; a < sel.size(); a += kMaxBconv) {
             const int cnt = (int)std::min(sel.size() - a, (size_t)kMaxBconv);
             BconvBatch b;
-            for (int i = 0; i < cnt; i++) b.j[i] = sel[a + i];
+            int ntmax = 1;
+            for (int i = 0; i < cnt; i++) {
+                b.j[i] = sel[a + i];
+                ntmax = max(ntmax, b.j[i].nrows - (b.j[i].skip_hi - b.j[i].skip_lo));
+            }
+            const size_t smem = (size_t)ntmax * ns * 8 + (size_t)ntmax * 20;
             dim3 grid((unsigned)((t.n / 2 + 255) / 256), (unsigned)cnt);
             PFT_PROF("bconv", st, 0.0);
             switch (ns) {
-                case 1: k_bconv<1><<<grid, 256, 0, st>>>(t, b); break;
-                case 2: k_bconv<2><<<grid, 256, 0, st>>>(t, b); break;
-                case 3: k_bconv<3><<<grid, 256, 0, st>>>(t, b); break;
-                case 4: k_bconv<4><<<grid, 256, 0, st>>>(t, b); break;
-                case 5: k_bconv<5><<<grid, 256, 0, st>>>(t, b); break;
-                case 6: k_bconv<6><<<grid, 256, 0, st>>>(t, b); break;
-                case 7: k_bconv<7><<<grid, 256, 0, st>>>(t, b); break;
-                default: k_bconv<8><<<grid, 256, 0, st>>>(t, b); break;
+                case 1: k_bconv<1, 2><<<grid, 256, smem, st>>>(t, b); break;
+                case 2: k_bconv<2, 2><<<grid, 256, smem, st>>>(t, b); break;
+                case 3: k_bconv<3, 2><<<grid, 256, smem, st>>>(t, b); break;
+                case 4: k_bconv<4, 2><<<grid, 256, smem, st>>>(t, b); break;
+                case 5: k_bconv<5, 2><<<grid, 256, smem, st>>>(t, b); break;
+                case 6: k_bconv<6, 2><<<grid, 256, smem, st>>>(t, b); break;
+                case 7: k_bconv<7, 2><<<grid, 256, smem, st>>>(t, b); break;
+                default: k_bconv<8, 2><<<grid, 256, smem, st>>>(t, b); break;
             }
             PFT_LAUNCH_CHECK("bconv");
         }
