@@ -336,7 +336,8 @@ def run_gpu(args):
 
     sv = None
     if args.serve > 0:
-        sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_low_load)
+        sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_low_load,
+                           args.serve_diag > 0)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -529,7 +530,7 @@ SV_WORKLOAD = ("Poisson arrivals of encrypted fastText inferences (vocab 32768, 
                "vocabulary in 2 ciphertexts); keys and models resident; inputs and scores in host memory")
 
 
-def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, seed=31):
+def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, seed=31):
     from paper_1908_06972_gb300 import serving, synth
 
     H, O = synth.fasttext_weights(77, FT_M, FT_N, FT_C)
@@ -542,6 +543,8 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, seed=31):
         streams.append(st)
         ctxs.append(ctx)
     torch.cuda.synchronize()
+
+    scales = [2.0 ** 40] * len(SV_RINGS)
 
     def trace(count, rate_, tseed):
         rng = np.random.default_rng(tseed)
@@ -556,13 +559,13 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, seed=31):
             chunks = -(-FT_M // t)
             coeffs = np.zeros((chunks, 2, level, n), np.uint64)
             for c in range(chunks):
-                pt = pft.pft_encode(ctxs[r], docs[i][c * t:(c + 1) * t], 2.0 ** 40, level)
+                pt = pft.pft_encode(ctxs[r], docs[i][c * t:(c + 1) * t], scales[r], level)
                 ct = pft.pft_encrypt(ctxs[r], pt, pft.PFT_ENC_SK, 40000 + 4 * i + c)
                 pft.pft_ct_export(ctxs[r], ct, coeffs[c])
                 pft.pft_ct_destroy(ct)
                 pft.pft_pt_destroy(pt)
             out = np.zeros((2, level - 2, n), np.uint64)
-            reqs.append(serving.Request(t=float(times[i]), ring=r, level=level, scale=2.0 ** 40, coeffs=coeffs,
+            reqs.append(serving.Request(t=float(times[i]), ring=r, level=level, scale=scales[r], coeffs=coeffs,
                                         out=out, tag=i))
         return reqs, docs
 
@@ -581,30 +584,51 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, seed=31):
                 "requests_per_ring": [sum(1 for q in reqs if q.ring == r) for r in range(len(SV_RINGS))],
                 "mean_level": round(float(np.mean([q.level for q in reqs])), 2)}
 
+    fig3_model0 = models[0]
     warm, _ = trace(2, 1000.0, seed + 100)  # kernels loaded, allocator pools grown
     run(warm)
     reqs, docs = trace(n_req, rate, seed)
     res = run(reqs)
     out = {"workload": SV_WORKLOAD, "unit": "inferences/s", "budget_gib": budget_gib,
            "saturated": summary(res, reqs, rate)}
-    # accuracy: decrypt the first request of each ring against FP64 Algorithm 1
-    err = 0.0
-    for r in range(len(SV_RINGS)):
-        q = next((q for q in reqs if q.ring == r), None)
-        if q is None:
-            continue
-        sc = res.done[q.tag]["scale"]
-        h = pft.pft_ct_import(ctxs[r], q.out, sc)
-        dec = pft.pft_decrypt(ctxs[r], h)
-        got = pft.pft_decode(ctxs[r], dec, FT_C)[:FT_C].real
-        pft.pft_pt_destroy(dec)
-        pft.pft_ct_destroy(h)
-        err = max(err, float(np.max(np.abs(got - fp64_scores(docs[q.tag], H, O)))))
-    out["max_abs_err_vs_fp64"] = err
+    def accuracy(res, reqs, docs, slots):
+        """Decrypt the first request of each ring against FP64 Algorithm 1."""
+        err = 0.0
+        for r in range(len(SV_RINGS)):
+            q = next((q for q in reqs if q.ring == r), None)
+            if q is None:
+                continue
+            h = pft.pft_ct_import(ctxs[r], q.out, res.done[q.tag]["scale"])
+            dec = pft.pft_decrypt(ctxs[r], h)
+            got = pft.pft_decode(ctxs[r], dec, 1 << (SV_RINGS[r][0] - 1)).real[slots[r]]
+            pft.pft_pt_destroy(dec)
+            pft.pft_ct_destroy(h)
+            err = max(err, float(np.max(np.abs(got - fp64_scores(docs[q.tag], H, O)))))
+        return err
+
+    fig3_slots = [list(range(FT_C))] * len(SV_RINGS)
+    out["max_abs_err_vs_fp64"] = accuracy(res, reqs, docs, fig3_slots)
     if low_load > 0:
         rate_low = low_load * res.throughput()
         reqs_low, _ = trace(n_req, rate_low, seed + 7)
         out["under_capacity"] = summary(run(reqs_low), reqs_low, rate_low)
+    if diag_leg:
+        # the same saturated trace with the rotation-light sequence on the N = 2^16 ring (its
+        # vocabulary fits one ciphertext there; inputs at 2^50, scores in slots 64 c)
+        logn0 = SV_RINGS[0][0]
+        pft.pft_add_rotation_keys(ctxs[0], list(range(1, FT_N)) + [FT_N << k for k in range(logn0 - 1 - 6)])
+        dmodel = pft.pft_ft_model_create_diag(ctxs[0], H, O, SV_RINGS[0][1])
+        models[0] = dmodel  # the server of run() now serves ring 0 with the diagonal model
+        scales[0] = 2.0 ** 50
+        warm_d, _ = trace(2, 1000.0, seed + 101)
+        run(warm_d)
+        reqs_d, docs_d = trace(n_req, rate, seed)
+        res_d = run(reqs_d)
+        out["rotation_light_ring16"] = summary(res_d, reqs_d, rate)
+        out["rotation_light_ring16"]["max_abs_err_vs_fp64"] = accuracy(
+            res_d, reqs_d, docs_d, [[FT_N * c for c in range(FT_C)]] + fig3_slots[1:])
+        models[0] = fig3_model0
+        pft.pft_ft_model_destroy(dmodel)
     for m in models:
         pft.pft_ft_model_destroy(m)
     for c in ctxs:
@@ -920,6 +944,8 @@ def main():
     ap.add_argument("--serve", type=int, default=24, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
     ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")
+    ap.add_argument("--serve-diag", type=int, default=1,
+                    help="also serve with the rotation-light sequence on the N=2^16 ring")
     ap.add_argument("--serve-low-load", type=float, default=0.7,
                     help="second trace offered at this fraction of the measured throughput (0: skip)")
     args = ap.parse_args()
