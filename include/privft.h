@@ -231,6 +231,17 @@ int pft_rescale(pft_ctx* ctx, const pft_ct* a, pft_ct* out);
  * key switching with the rotation key of g.  Steps with no key -> PFT_ERR_NO_KEY. */
 int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
 
+/* ---- device status ---------------------------------------------------------
+ * Kernels that wait on asynchronous copies (the key inner product streams the digit rows
+ * through an mbarrier-counted shared-memory ring) bound every wait; if one expires the
+ * kernel records it in a device flag and returns early, and its results are invalid.
+ * pft_device_status synchronises the context's stream and returns PFT_ERR_TIMEOUT (clearing
+ * the flag) if that happened since the last check; pft_ct_export_batch checks it too.
+ * pft_wait_selftest queues a wait that can never complete, bounded by `polls` (1..2^20)
+ * polls, which raises the flag: a diagnostic of the mechanism (no copy is in flight). */
+int pft_device_status(pft_ctx* ctx);
+int pft_wait_selftest(pft_ctx* ctx, long long polls);
+
 /* ---- level and scale management (used by the training step of Sec. 4.2) ---
  * The paper keeps every operand of a step at one level and scale; training mixes
  * operands of different depths, which these exact operations reconcile. */

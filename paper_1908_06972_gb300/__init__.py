@@ -100,6 +100,7 @@ def lib():
             "pft_rotate_hoisted": [vp, vp, POINTER(c_int32), i, pp],
             "pft_dot_plain_batch": [vp, pp, pp, i, i, i, pp],
             "pft_drop_level": [vp, vp, i, vp], "pft_add_const": [vp, vp, d, vp],
+            "pft_device_status": [vp], "pft_wait_selftest": [vp, ctypes.c_longlong],
             "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
@@ -161,7 +162,7 @@ def exported_symbols():
             "pft_ct_set_scale", "pft_ft_enc_model_create", "pft_ft_enc_model_get", "pft_ft_enc_model_levels",
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
-            "pft_ct_export_batch_async"]
+            "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest"]
 
 
 def _check(rc, ctx=None):
@@ -461,6 +462,15 @@ def pft_rescale_batch(ctx, a, out):
 
 def pft_rotate_batch(ctx, a, step, out):
     _op("pft_rotate_batch", ctx, _arr(a), len(a), c_int32(step), _arr(out))
+
+
+def pft_device_status(ctx):
+    """Raises PftError(PFT_ERR_TIMEOUT) if a bounded device wait expired since the last check."""
+    _check(lib().pft_device_status(ctx), ctx)
+
+
+def pft_wait_selftest(ctx, polls):
+    _check(lib().pft_wait_selftest(ctx, int(polls)), ctx)
 
 
 def pft_drop_level(ctx, a, level, out):

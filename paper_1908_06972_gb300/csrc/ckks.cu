@@ -1646,7 +1646,10 @@ static void export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* 
                                          cudaMemcpyDeviceToHost, c->stream));
             i0 = i1;
         }
-        if (sync) PFT_CUDA(cudaStreamSynchronize(c->stream));
+        if (sync) {
+            PFT_CUDA(cudaStreamSynchronize(c->stream));
+            NEED(!wait_timeout_flag(true, c->stream), PFT_ERR_TIMEOUT, "a bounded device wait expired; results are invalid");
+        }
     }
 }
 
@@ -1761,6 +1764,21 @@ int pft_add_const(pft_ctx* c, const pft_ct* a, double value, pft_ct* out) {
 int pft_mul_const(pft_ctx* c, const pft_ct* a, double value, double const_scale, pft_ct* out) {
     return guard(c, [&] { op_const_batch(c, &a, 1, value, const_scale, true, &out); });
 }
+int pft_device_status(pft_ctx* c) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "bad arguments");
+        PFT_CUDA(cudaStreamSynchronize(c->stream));
+        NEED(!wait_timeout_flag(true, c->stream), PFT_ERR_TIMEOUT, "a bounded device wait expired");
+    });
+}
+
+int pft_wait_selftest(pft_ctx* c, long long polls) {
+    return guard(c, [&] {
+        NEED(c && polls >= 1 && polls <= (1ll << 20), PFT_ERR_ARG, "polls must lie in 1..2^20");
+        wait_selftest(polls, c->stream);
+    });
+}
+
 int pft_ct_set_scale(pft_ct* ct, double scale) {
     if (!ct || !(scale > 0) || !std::isfinite(scale)) return PFT_ERR_ARG;
     ct->scale = scale;

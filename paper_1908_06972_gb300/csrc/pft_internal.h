@@ -151,6 +151,10 @@ struct KeyRef {
 };
 void ks_inner_multi(const DevTables& t, const KsDesc* descs_host, int B, const KeyRef& key, int L, int k, int alpha,
                     cudaStream_t st);
+// Whether a kernel's bounded wait has expired since the last reset (reads a device flag).
+int wait_timeout_flag(bool reset, cudaStream_t st);
+// Launches a wait that cannot complete, bounded by `polls` polls (it raises the flag).
+void wait_selftest(long long polls, cudaStream_t st);
 // r = (last + h) mod p, h = floor(p/2), p = prime nlimbs(out); limb k of out = (r - h) mod q_k.
 void rescale_bcast(const DevTables& t, const PolySet& last, const PolySet& out, cudaStream_t st);
 

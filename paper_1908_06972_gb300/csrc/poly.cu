@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cstdlib>
+#include <cstring>
 
 #include "modarith.cuh"
 
@@ -517,6 +518,178 @@ __global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt,
     }
 }
 
+// ---- the same with bulk copies (cp.async.bulk + mbarrier) ---------------------------------
+// CTA = one key row x 256 coefficients, 128 threads with two coefficients each and the key
+// slice in registers.  The digit rows of the inputs that use the row stream through a ring
+// of kKsStages shared-memory stages (one input's digits, 2 KiB each) filled by one thread
+// with 1-D bulk copies whose bytes an mbarrier per stage counts: the CTA computes input u
+// while the copies of the next inputs are in flight.  Every wait is bounded; on expiry the
+// kernel records the failure in g_wait_timeout, waits (bounded) for its own copies in
+// flight and returns.
+constexpr int kKsStages = 3;
+constexpr int kKsChunk = 256;                // coefficients per CTA (2 KiB per digit row)
+constexpr long long kWaitPolls = 1ll << 22;  // polls of a bounded wait (seconds at most)
+
+__device__ int g_wait_timeout;
+
+__device__ __forceinline__ u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, u64* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(u64* bar, u32 parity) {
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity) {
+    for (long long i = 0; i < kWaitPolls; i++)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, int B, KeyRef kr, int L, int k,
+                                                       int alpha, int stage_digits) {
+    extern __shared__ __align__(128) u64 ring[];  // [kKsStages][stage_digits][kKsChunk]
+    __shared__ __align__(8) u64 bars[kKsStages];
+    const int row = blockIdx.y;
+    const int logn = t.logn;
+    const int rows_total = L + k;
+    const int need = bt.need[row];
+    if (need == 0) return;  // uniform over the CTA
+    const size_t chunk0 = (size_t)blockIdx.x * kKsChunk;
+    const int xl = 2 * threadIdx.x;
+    const size_t xo = chunk0 + xl;
+    const DPrime P = load_prime(t.primes, row);
+    const u64* key = kr.ptr;
+    ulonglong2 kb[BMAX], ka[BMAX];
+#pragma unroll
+    for (int j = 0; j < BMAX; j++) {
+        if (j < need) {
+            kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + xo));
+            ka[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + xo));
+        }
+    }
+    auto used = [&](int b) { return !(row < L && row >= bt.d[b].l); };
+    auto next = [&](int b) {
+        while (b < B && !used(b)) b++;
+        return b;
+    };
+    // thread 0 fills stage s with the digit rows of input b
+    auto issue = [&](int b, int s) {
+        const KsDesc& D = bt.d[b];
+        const int l = D.l, E = l + k, beta = (l + alpha - 1) / alpha;
+        const int m = row < L ? row : l + row - L;
+        mbar_expect_tx(&bars[s], (u32)(beta * kKsChunk * 8));
+        for (int j = 0; j < beta; j++)
+            bulk_g2s(ring + ((size_t)s * stage_digits + j) * kKsChunk, D.ext + (((size_t)j * E + m) << logn) + chunk0,
+                     (u32)(kKsChunk * 8), &bars[s]);
+    };
+    if (threadIdx.x == 0) {
+        for (int s2 = 0; s2 < kKsStages; s2++) mbar_init(&bars[s2], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // prologue: the first kKsStages used inputs
+    int ib = next(0);
+    if (threadIdx.x == 0) {
+        int bb = ib;
+        for (int s2 = 0; s2 < kKsStages && bb < B; s2++, bb = next(bb + 1)) issue(bb, s2);
+    }
+    for (int s2 = 0; s2 < kKsStages && ib < B; s2++) ib = next(ib + 1);  // ib: next input to issue
+    int u = 0;
+    for (int b = next(0); b < B; b = next(b + 1), u++) {
+        const int s = u % kKsStages;
+        const u32 parity = (u32)((u / kKsStages) & 1);
+        const bool ok = __syncthreads_and(mbar_wait(&bars[s], parity));
+        if (!ok) {
+            // record, then wait (bounded) for the copies still in flight on the other stages
+            if (threadIdx.x == 0) {
+                atomicExch(&g_wait_timeout, 1);
+                mbar_wait(&bars[s], parity);
+                int uu = u + 1;
+                for (int bb = next(b + 1); bb < ib; bb = next(bb + 1), uu++)
+                    mbar_wait(&bars[uu % kKsStages], (u32)((uu / kKsStages) & 1));
+            }
+            return;
+        }
+        const KsDesc& D = bt.d[b];
+        const int l = D.l, E = l + k, beta = (l + alpha - 1) / alpha;
+        const int m = row < L ? row : l + row - L;
+        const u64* st = ring + (size_t)s * stage_digits * kKsChunk + xl;
+        U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
+#pragma unroll
+        for (int j = 0; j < BMAX; j++) {
+            if (j < beta) {  // beta <= 8: 128-bit sums of at most 8 products
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(st + (size_t)j * kKsChunk);
+                mac_wide(s0x, v.x, kb[j].x);
+                mac_wide(s0y, v.y, kb[j].y);
+                mac_wide(s1x, v.x, ka[j].x);
+                mac_wide(s1y, v.y, ka[j].y);
+            }
+        }
+        ulonglong2 r0, r1;
+        r0.x = barrett_reduce(s0x.hi, s0x.lo, P);
+        r0.y = barrett_reduce(s0y.hi, s0y.lo, P);
+        r1.x = barrett_reduce(s1x.hi, s1x.lo, P);
+        r1.y = barrett_reduce(s1y.hi, s1y.lo, P);
+        *reinterpret_cast<ulonglong2*>(D.u + ((size_t)m << logn) + xo) = r0;
+        *reinterpret_cast<ulonglong2*>(D.u + (((size_t)E + m) << logn) + xo) = r1;
+        __syncthreads();  // every thread has read stage s
+        if (ib < B) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(ib, s);
+            }
+            ib = next(ib + 1);
+        }
+    }
+}
+
+// Self-test of the bounded wait: an mbarrier that expects bytes no copy delivers (no copy is
+// issued, so nothing is in flight) must give up after `polls` polls and raise the flag.
+__global__ void k_wait_selftest(long long polls) {
+    __shared__ __align__(8) u64 bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, 16);
+    bool ok = false;
+    for (long long i = 0; i < polls && !ok; i++) ok = mbar_test(&bar, 0);
+    if (!ok) atomicExch(&g_wait_timeout, 1);
+}
+
+void wait_selftest(long long polls, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(polls);
+    PFT_LAUNCH_CHECK("wait self-test");
+}
+
+int wait_timeout_flag(bool reset, cudaStream_t st) {
+    int v = 0;
+    PFT_CUDA(cudaMemcpyFromSymbolAsync(&v, g_wait_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    PFT_CUDA(cudaStreamSynchronize(st));
+    if (reset && v) {
+        static const int z = 0;
+        PFT_CUDA(cudaMemcpyToSymbolAsync(g_wait_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+        PFT_CUDA(cudaStreamSynchronize(st));
+    }
+    return v;
+}
+
 // Any number of digits: the key is re-read (or regenerated) for every input.
 __global__ void k_ks_inner_multi_generic(DevTables t, KsBatch bt, int B, KeyRef kr, int L, int k, int alpha) {
     const u64* key = kr.ptr;
@@ -581,7 +754,21 @@ void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const KeyRef
         dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(L + k));
         dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(L + k));
         PFT_PROF("ks_inner", st, bytes);
-        if (beta_max <= 4 && !key.compressed) k_ks_inner_multi<4, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
+        if (beta_max <= 8 && !key.compressed && t.n % kKsChunk == 0) {
+            const int sd = beta_max <= 4 ? 4 : 8;
+            dim3 gb((unsigned)(t.n / kKsChunk), (unsigned)(L + k));
+            const size_t smem = (size_t)kKsStages * sd * kKsChunk * 8;
+            static bool attr = false;  // the 8-digit ring needs 48 KiB of dynamic shared memory
+            if (!attr) {
+                PFT_CUDA(cudaFuncSetAttribute(k_ks_inner_bulk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)((size_t)kKsStages * 8 * kKsChunk * 8)));
+                PFT_CUDA(cudaFuncSetAttribute(k_ks_inner_bulk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)((size_t)kKsStages * 8 * kKsChunk * 8)));
+                attr = true;
+            }
+            if (sd == 4) k_ks_inner_bulk<4><<<gb, 128, smem, st>>>(t, bt, cnt, key, L, k, alpha, sd);
+            else k_ks_inner_bulk<8><<<gb, 128, smem, st>>>(t, bt, cnt, key, L, k, alpha, sd);
+        } else if (beta_max <= 4 && !key.compressed) k_ks_inner_multi<4, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
         else if (beta_max <= 8 && !key.compressed) k_ks_inner_multi<8, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
         else if (beta_max <= 4) k_ks_inner_multi<4, true><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
         else if (beta_max <= 8) k_ks_inner_multi<8, true><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);

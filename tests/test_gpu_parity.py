@@ -426,3 +426,20 @@ def test_compressed_keys_bit_exact(gpu, logn, L, k, alpha, mid):
             p.assert_equal(outs[i], want[i], "compressed hoisted %d" % i)
     finally:
         p.close()
+
+
+def test_bounded_wait_reports_timeout(p1):
+    """A wait that cannot complete gives up after its poll limit and the host reads
+    PFT_ERR_TIMEOUT; the flag is cleared and the context stays usable."""
+    pf, ctx = p1.pft, p1.ctx
+    pf.pft_device_status(ctx)  # clean before
+    pf.pft_wait_selftest(ctx, 1000)
+    with pytest.raises(pf.PftError) as e:
+        pf.pft_device_status(ctx)
+    assert e.value.code == pf.PFT_ERR_TIMEOUT
+    pf.pft_device_status(ctx)  # cleared
+    a = p1.orc.encrypt_sk(p1.orc.encode(synth.slots(5, 64), level=3), 5)
+    g, out = p1.ct(a), p1.empty()
+    pf.pft_mul_relin(ctx, g, g, out)
+    p1.assert_equal(out, p1.orc.mul_relin(a, a), "after the self-test")
+    pf.pft_device_status(ctx)
