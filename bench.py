@@ -878,27 +878,47 @@ def run_case_ks(args):
 
 
 # ---- CPU oracle -------------------------------------------------------------------------------------
-def cpu_baseline(level):
-    """The oracle on a bounded sample: one ciphertext at `level` through mul_relin and one
-    rotation (keys generated for a chain truncated at `level`, which is the slice of the full
-    keys a level-`level` ciphertext touches); a unit = mul_relin + 16 rotations."""
-    from oracle import ckks
-    from paper_1908_06972_gb300 import synth
+_ORACLES = {}
 
-    orc = ckks.Oracle(LOGN, level, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
-    orc.keygen([1], True)
-    a = orc.encrypt_sk(orc.encode(synth.slots(1, 256), level=level), 1)
-    b = orc.encrypt_sk(orc.encode(synth.slots(2, 256), level=level), 2)
-    t0 = time.perf_counter()
-    c = orc.mul_relin(a, b)
-    t1 = time.perf_counter()
-    orc.rotate(c, 1)
-    t2 = time.perf_counter()
-    unit_s = (t1 - t0) + 16 * (t2 - t1)
+
+def _oracle_at(level):
+    """Oracle on the chain truncated at `level` (the slice of the full keys a level-`level`
+    ciphertext touches), with its keys and two input ciphertexts; built once per level."""
+    if level not in _ORACLES:
+        from oracle import ckks
+        from paper_1908_06972_gb300 import synth
+
+        orc = ckks.Oracle(LOGN, level, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED)
+        orc.keygen([1], True)
+        a = orc.encrypt_sk(orc.encode(synth.slots(1, 256), level=level), 1)
+        b = orc.encrypt_sk(orc.encode(synth.slots(2, 256), level=level), 2)
+        _ORACLES[level] = (orc, a, b)
+    return _ORACLES[level]
+
+
+def cpu_baseline(levels_spec):
+    """The oracle on a bounded sample of the workload: one ciphertext pair at each sampled
+    level through mul_relin and one rotation; the time of a unit (mul_relin + 16 rotations) is
+    interpolated linearly in the level between the samples and averaged over the workload's
+    64 levels."""
+    pts = sorted(int(x) for x in str(levels_spec).split(","))
+    unit, measured = [], 0.0
+    for lv in pts:
+        orc, a, b = _oracle_at(lv)
+        t0 = time.perf_counter()
+        c = orc.mul_relin(a, b)
+        t1 = time.perf_counter()
+        orc.rotate(c, 1)
+        t2 = time.perf_counter()
+        unit.append((t1 - t0) + 16 * (t2 - t1))
+        measured += t2 - t0
+    wl = levels()
+    unit_s = float(np.mean(np.interp(wl, pts, unit)))
     cores = len(os.sched_getaffinity(0))
     return {"value": round(1.0 / unit_s, 6), "unit": "mult+relin/s", "cores": cores, "kind": "oracle",
-            "sample": "1 ciphertext at level %d (workload mean 17.5): mul_relin + 1 rotation timed, "
-                      "unit = mul_relin + 16 rotations (%.1f s measured)" % (level, t2 - t0)}
+            "sample": "one ciphertext pair at each of levels %s through mul_relin + 1 rotation (%.1f s measured); "
+                      "unit time (mul_relin + 16 rotations) interpolated in the level and averaged over the "
+                      "workload's 64 levels (mean %.2f)" % (", ".join(map(str, pts)), measured, float(np.mean(wl)))}
 
 
 def run_reference(args):
@@ -932,7 +952,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--roofline-kernel", default="ntt")
-    ap.add_argument("--cpu-level", type=int, default=5)
+    ap.add_argument("--cpu-level", default="5,19,30", help="levels the CPU oracle is timed at")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
     ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
