@@ -470,20 +470,39 @@ __global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt,
     const DPrime P = load_prime(t.primes, row);
     const size_t xo = 2 * (size_t)x2;
     ulonglong2 kb[BMAX], ka[BMAX];
+    if (!COMP) {
 #pragma unroll
-    for (int j = 0; j < BMAX; j++) {
-        if (j < need) {
-            if (!COMP) {
+        for (int j = 0; j < BMAX; j++) {
+            if (j < need) {
                 kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + xo));
                 ka[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + ((((size_t)j * 2 + 1) * rows_total + row) << logn) + xo));
-            } else {
-                kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + (((size_t)j * rows_total + row) << logn) + xo));
-                // block xo/4 holds coefficients 4(xo/4) .. +3; this thread's two are at xo & 3
+            }
+        }
+    } else {
+        // ChaCha20 block xo/4 holds the word pairs of coefficients 4(xo/4) .. +3: lanes 2i and
+        // 2i+1 (coefficients +0,+1 and +2,+3 of one block) each draw the block of one digit of
+        // a pair and swap the halves the other lane needs.
+        const int par = (int)(threadIdx.x & 1);
+#pragma unroll
+        for (int j = 0; j < BMAX; j += 2) {
+            if (j < need) {  // uniform over the CTA (one key row)
                 u64 w[8];
-                chacha_block(kr.seedw, (u32)(xo >> 2), kDomKskAEval, kr.id, 256u * j + (u32)row, w);
-                const int c0 = (int)(xo & 3);
-                ka[j].x = uniform_mod(w[2 * c0], w[2 * c0 + 1], P);
-                ka[j].y = uniform_mod(w[2 * c0 + 2], w[2 * c0 + 3], P);
+                chacha_block(kr.seedw, (u32)(xo >> 2), kDomKskAEval, kr.id, 256u * (j + par) + (u32)row, w);
+                // this lane's coefficients are word pairs 2 par, 2 par + 1 of the block
+                const u64 own0 = uniform_mod(par ? w[4] : w[0], par ? w[5] : w[1], P);
+                const u64 own1 = uniform_mod(par ? w[6] : w[2], par ? w[7] : w[3], P);
+                const u64 give0 = uniform_mod(par ? w[0] : w[4], par ? w[1] : w[5], P);
+                const u64 give1 = uniform_mod(par ? w[2] : w[6], par ? w[3] : w[7], P);
+                const u64 got0 = __shfl_xor_sync(0xffffffffu, give0, 1);
+                const u64 got1 = __shfl_xor_sync(0xffffffffu, give1, 1);
+                // lane parity 0 drew digit j, parity 1 drew digit j + 1
+                const ulonglong2 a_own = make_ulonglong2(own0, own1), a_got = make_ulonglong2(got0, got1);
+                ka[j] = par ? a_got : a_own;
+                if (j + 1 < BMAX) ka[j + 1] = par ? a_own : a_got;
+                kb[j] = __ldg(reinterpret_cast<const ulonglong2*>(key + (((size_t)j * rows_total + row) << logn) + xo));
+                if (j + 1 < need)
+                    kb[j + 1] =
+                        __ldg(reinterpret_cast<const ulonglong2*>(key + (((size_t)(j + 1) * rows_total + row) << logn) + xo));
             }
         }
     }
@@ -768,6 +787,8 @@ void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const KeyRef
             }
             if (sd == 4) k_ks_inner_bulk<4><<<gb, 128, smem, st>>>(t, bt, cnt, key, L, k, alpha, sd);
             else k_ks_inner_bulk<8><<<gb, 128, smem, st>>>(t, bt, cnt, key, L, k, alpha, sd);
+        } else if (key.compressed && t.n < 256) {  // lane pairs need full warps
+            k_ks_inner_multi_generic<<<grid1, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
         } else if (beta_max <= 4 && !key.compressed) k_ks_inner_multi<4, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
         else if (beta_max <= 8 && !key.compressed) k_ks_inner_multi<8, false><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
         else if (beta_max <= 4) k_ks_inner_multi<4, true><<<grid2, 128, 0, st>>>(t, bt, cnt, key, L, k, alpha);
