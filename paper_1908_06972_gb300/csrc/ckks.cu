@@ -309,7 +309,6 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
     // 2. ModUp: fast basis conversion of every digit to the other rows; digit rows copied
     {
         std::vector<BconvJob> jobs;
-        std::vector<PolyRef> cin, cout;
         for (size_t b = 0; b < B; b++) {
             const int l = io[b].l, E = l + k, beta = (l + alpha - 1) / alpha;
             for (int j = 0; j < beta; j++) {
@@ -327,12 +326,10 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
                 J.base2 = L;
                 J.pad = 0;
                 jobs.push_back(J);
-                cin.push_back(ref((u64*)io[b].d + (size_t)lo * limb, hi - lo, lo));
-                cout.push_back(ref(ext(b, j) + (size_t)lo * limb, hi - lo, lo));
             }
         }
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
-        ew(c, EwOp::Copy, cin, {}, cout);
+        // the digit's own rows are d itself: the inner product reads them there
     }
     // 3. evaluation form of the converted rows
     {
@@ -353,6 +350,7 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
         for (size_t b = 0; b < B; b++) {
             d[b].ext = ext(b, 0);
             d[b].u = uu(b, 0);
+            d[b].d = io[b].d;
             d[b].l = io[b].l;
             d[b].pad = 0;
         }
@@ -660,7 +658,7 @@ static void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps,
         chunks(eout.size(), [&](size_t x, size_t y) {
             automorph(c->tabs, mkset(ein, x, y), mkset(eout, x, y), gs[i], c->stream);
         });
-        KsDesc d{ExtG.u(), U.u(), l, 0};
+        KsDesc d{ExtG.u(), U.u(), nullptr, l, 0};
         ks_inner_multi(c->tabs, &d, 1, keyref(c, gs[i]), L, k, alpha, c->stream);
         // ModDown
         std::vector<PolyRef> sp, cvr;

@@ -134,6 +134,8 @@ void bconv(const DevTables& t, const BconvJob* jobs_host, int n_jobs, cudaStream
 struct KsDesc {
     const u64* ext;
     u64* u;
+    const u64* d;  // the input in evaluation form: rows of digit j are read here (ext's copies
+                   // of them are not written); null: ext holds them
     int l;
     int pad;
 };

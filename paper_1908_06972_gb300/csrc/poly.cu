@@ -258,26 +258,63 @@ void sub_scale(const DevTables& t, const PolySet& x, const PolySet* y, const Pol
 // ---- Galois automorphism X -> X^g in the evaluation layout ---------------------------------
 // Entry i holds a(psi^(2 brv(i) + 1)); a(X^g) there equals a(psi^((2 brv(i) + 1) g)),
 // i.e. entry brv(((2 brv(i) + 1) g mod 2N - 1) / 2) of the input.
+__device__ __forceinline__ u32 automorph_src(u32 i, int logn, u64 g) {
+    const u32 mask2n = (2u << logn) - 1;
+    const u32 bi = __brev(i) >> (32 - logn);
+    const u32 e = (u32)(((u64)(2 * bi + 1) * g) & mask2n);
+    return __brev((e - 1) >> 1) >> (32 - logn);
+}
+
+// Multiplication by an odd g modulo 2N fixes the low bits of an exponent given its low bits,
+// so in the bit-reversed layout the top bits of a source index depend only on the top bits of
+// its destination: every block of kAutBlock consecutive outputs reads one block of
+// kAutBlock consecutive inputs.  A CTA stages kAutBlocks such input blocks in shared memory
+// with coalesced loads, permutes there and writes its outputs coalesced.
+constexpr int kAutBlock = 256, kAutBlocks = 4;
+
+__global__ void __launch_bounds__(256) k_automorph_blocked(DevTables t, PolySet in, PolySet out, u64 g) {
+    __shared__ u64 sm[kAutBlocks * kAutBlock];
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int logn = t.logn;
+    const size_t base = (size_t)limb << logn;
+    const u64* src = in.p[poly].ptr + base;
+    const u32 o0 = blockIdx.x * (kAutBlocks * kAutBlock);
+#pragma unroll
+    for (int k = 0; k < kAutBlocks; k++) {
+        const u32 ib = automorph_src(o0 + k * kAutBlock, logn, g) & ~(u32)(kAutBlock - 1);
+        sm[k * kAutBlock + threadIdx.x] = __ldg(src + ib + threadIdx.x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kAutBlocks; k++) {
+        const u32 i = o0 + k * kAutBlock + threadIdx.x;
+        Ro.ptr[base + i] = sm[k * kAutBlock + (automorph_src(i, logn, g) & (kAutBlock - 1))];
+    }
+}
+
+// small rings (N < kAutBlocks * kAutBlock): one gather per output
 __global__ void k_automorph(DevTables t, PolySet in, PolySet out, u64 g) {
     const int poly = blockIdx.z, limb = blockIdx.y;
     const PolyRef& Ro = out.p[poly];
     if (limb >= Ro.nlimbs) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= t.n) return;
-    const int logn = t.logn;
-    const u32 mask2n = (2u << logn) - 1;
-    const u32 bi = __brev((u32)i) >> (32 - logn);
-    const u32 e = (u32)(((u64)(2 * bi + 1) * g) & mask2n);
-    const u32 src = __brev((e - 1) >> 1) >> (32 - logn);
-    const size_t base = (size_t)limb << logn;
-    Ro.ptr[base + i] = __ldg(in.p[poly].ptr + base + src);
+    const size_t base = (size_t)limb << t.logn;
+    Ro.ptr[base + i] = __ldg(in.p[poly].ptr + base + automorph_src((u32)i, t.logn, g));
 }
 
 void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g, cudaStream_t st) {
     if (out.count == 0) return;
-    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
     PFT_PROF("automorph", st, set_limbs(out) * t.n * 16.0);
-    k_automorph<<<grid, 256, 0, st>>>(t, in, out, g);
+    if (t.n >= kAutBlocks * kAutBlock) {
+        dim3 grid((unsigned)(t.n / (kAutBlocks * kAutBlock)), (unsigned)out.max_limbs, (unsigned)out.count);
+        k_automorph_blocked<<<grid, 256, 0, st>>>(t, in, out, g);
+    } else {
+        dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+        k_automorph<<<grid, 256, 0, st>>>(t, in, out, g);
+    }
     PFT_LAUNCH_CHECK("automorph");
 }
 
@@ -451,6 +488,14 @@ __device__ __forceinline__ u64 uniform_mod(u64 lo, u64 hi, const DPrime& P) {
     return barrett_reduce(acc.hi, acc.lo, P);
 }
 
+// Row m of extended digit j of an input: the input itself for the digit's own rows (when it
+// is given), the basis-conversion output otherwise.
+__device__ __forceinline__ const u64* ks_row(const KsDesc& D, int j, int E, int m, int alpha, int logn) {
+    const int lo = j * alpha;
+    if (D.d && m >= lo && m < lo + alpha && m < D.l) return D.d + ((size_t)m << logn);
+    return D.ext + (((size_t)j * E + m) << logn);
+}
+
 // ---- key inner product over inputs at different levels -----------------------------------
 // Row `row` of the key (q rows 0..L-1, special rows L..L+k-1) is used by every input whose
 // level l exceeds it (q rows) or by every input (special rows); for input b its extended row
@@ -516,7 +561,7 @@ __global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt,
         ulonglong2 v[BMAX];
 #pragma unroll
         for (int j = 0; j < BMAX; j++)
-            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(D.ext + (((size_t)j * E + m) << logn) + xo));
+            if (j < beta) v[j] = __ldg(reinterpret_cast<const ulonglong2*>(ks_row(D, j, E, m, alpha, logn) + xo));
         U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
 #pragma unroll
         for (int j = 0; j < BMAX; j++) {
@@ -615,7 +660,7 @@ __global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, 
         const int m = row < L ? row : l + row - L;
         mbar_expect_tx(&bars[s], (u32)(beta * kKsChunk * 8));
         for (int j = 0; j < beta; j++)
-            bulk_g2s(ring + ((size_t)s * stage_digits + j) * kKsChunk, D.ext + (((size_t)j * E + m) << logn) + chunk0,
+            bulk_g2s(ring + ((size_t)s * stage_digits + j) * kKsChunk, ks_row(D, j, E, m, alpha, logn) + chunk0,
                      (u32)(kKsChunk * 8), &bars[s]);
     };
     if (threadIdx.x == 0) {
@@ -727,7 +772,7 @@ __global__ void k_ks_inner_multi_generic(DevTables t, KsBatch bt, int B, KeyRef 
         const int beta = (l + alpha - 1) / alpha;
         U128 s0 = {0, 0}, s1 = {0, 0};
         for (int j = 0; j < beta; j++) {
-            const u64 v = __ldg(D.ext + (((size_t)j * E + m) << logn) + x);
+            const u64 v = __ldg(ks_row(D, j, E, m, alpha, logn) + x);
             u64 kb, ka;
             if (!kr.compressed) {
                 kb = __ldg(key + ((((size_t)j * 2 + 0) * rows_total + row) << logn) + x);
