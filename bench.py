@@ -961,7 +961,7 @@ def main():
                     help="seeded compressed switching keys (the step and --case ks)")
     ap.add_argument("--train", type=int, default=64, help="documents per encrypted training step (0: skip)")
     ap.add_argument("--train-plain-docs", type=int, default=2, help="documents timed on the plain training path")
-    ap.add_argument("--serve", type=int, default=24, help="requests in the serving trace (0: skip)")
+    ap.add_argument("--serve", type=int, default=48, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
     ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")
     ap.add_argument("--serve-diag", type=int, default=1,
