@@ -14,6 +14,8 @@ per column; the output product, then one final rescale.
 """
 import numpy as np
 
+from .ckks import Plaintext
+
 
 def plain_scores(v, H, O):
     """Algorithm 1, steps 2-3 on the normalised count vector v (= (1/w) sum x_i)."""
@@ -212,3 +214,95 @@ def encrypted_train_step(orc, v_cts, w_cts, H_cts, O_cts, eta):
         a = _align(orc, dH[j], eta, H_cts[j].scale)
         H_new.append(orc.sub(orc.drop_level(H_cts[j], a.level), a))
     return dH, dO, H_new, O_new
+
+
+# ---- rotation-light training (diagonal packing; not in the paper) ------------------------------
+# Model: D_k[i] = H[(i + k) mod t, i mod n] (k < n, the diagonals of the inference variant) at
+# level l0 and P[n c + j] = O[j, c] (one ciphertext) at level l0 - 1; a plaintext mask M with
+# 1 in the score slots n c.  The client sends v_b (m <= t) and w_b = y_b - 1/4 in slots n c.
+#   forward  R_bk = rot(v_b, k) (hoisted), Q_b = Relin(sum_k R_bk x D_k),
+#            Hb = Rescale(Q_b + rot(Q_b, n 2^s) ...)             h_b[i mod n] in slot i, l0-1
+#            Sb = Rescale(S + rot(S, 2^s) ..., S = Relin(Hb x P)) s_b[c] in slot n c,  l0-2
+#            Sm = Rescale(Sb * M)                                 zero off the score slots, l0-3
+#            g_b = [Rescale(Relin(u x u)), u = Sm + 2] at 8x its scale - 1/2 - w_b,    l0-4
+#   backward Gb = g_b + rot(g_b, -2^s) ...                        g_b[c] in block c
+#            dP = Rescale(Relin(sum_b Hb x Gb))                   dO[j, c] in slot n c + j, l0-5
+#            Eb = Rescale(X + rot(X, n 2^s) ..., X = Relin(Gb x P)) e_b[i mod n] in slot i, l0-5
+#            dD_k = Rescale(Relin(sum_b R_bk x Eb))              the diagonals of dH, l0-6
+#   update   D_k <- D_k - Align(dD_k) (l0-7), P <- drop(P - Align(dP), l0-8): one level below D.
+
+def train_pack_diag(H, O, t):
+    """Slot vectors of the diagonal training layout: D [n][t], P [t], mask M [t]."""
+    D, P = pack_diag(H, O, t)
+    n, c = O.shape
+    M = np.zeros(t)
+    M[[n * cc for cc in range(c)]] = 1.0
+    return D, P, M
+
+
+def train_label_spec_diag(orc, level, sc_v, sc_D, sc_P, sc_M):
+    q = orc.q
+    sh = sc_v * sc_D / float(q[level - 1])
+    ss = sh * sc_P / float(q[level - 2])
+    sm = ss * sc_M / float(q[level - 3])
+    su = sm * sm / float(q[level - 4])
+    return level - 4, 8.0 * su
+
+
+def encrypted_train_step_diag(orc, v_cts, w_cts, D_cts, P_ct, M_pt, eta):
+    """One minibatch step of the diagonal layout on the oracle.  Returns (dD [n], dP, D' [n], P')."""
+    B, n = len(v_cts), len(D_cts)
+    t = orc.N // 2
+    l0 = D_cts[0].level
+    assert all(x.level == l0 for x in v_cts + D_cts) and P_ct.level == l0 - 1
+    R, Hs, G = [], [], []
+    for b in range(B):
+        Rb = [v_cts[b]] + orc.rotate_hoisted(v_cts[b], list(range(1, n)))
+        R.append(Rb)
+        Q = orc.relin(*orc.tensor_sum([(Rb[k], D_cts[k]) for k in range(n)]))
+        st = n
+        while st < t:
+            Q = orc.add(Q, orc.rotate(Q, st))
+            st *= 2
+        Hb = orc.rescale(Q)
+        Hs.append(Hb)
+        S = orc.relin(*orc.tensor_sum([(Hb, P_ct)]))
+        st = 1
+        while st < n:
+            S = orc.add(S, orc.rotate(S, st))
+            st *= 2
+        Sb = orc.rescale(S)
+        Mq = Plaintext(M_pt.m[:Sb.level], M_pt.scale)
+        Sm = orc.rescale(orc.mul_plain(Sb, Mq))
+        u = orc.add_const(Sm, 2.0)
+        U = orc.rescale(orc.relin(*orc.tensor_sum([(u, u)])))
+        U = orc.add_const(orc.set_scale(U, 8.0 * U.scale), -0.5)
+        g = orc.sub(U, w_cts[b])
+        st = 1
+        while st < n:
+            g = orc.add(g, orc.rotate(g, -st))
+            st *= 2
+        G.append(g)
+    lg = G[0].level
+    dP = orc.rescale(orc.relin(*orc.tensor_sum([(orc.drop_level(Hs[b], lg), G[b]) for b in range(B)])))
+    Pg = orc.drop_level(P_ct, lg)
+    E = []
+    for b in range(B):
+        X = orc.relin(*orc.tensor_sum([(G[b], Pg)]))
+        st = n
+        while st < t:
+            X = orc.add(X, orc.rotate(X, st))
+            st *= 2
+        E.append(orc.rescale(X))
+    le = E[0].level
+    dD = [orc.rescale(orc.relin(*orc.tensor_sum([(orc.drop_level(R[b][k], le), E[b]) for b in range(B)])))
+          for k in range(n)]
+    if eta == 0:
+        return dD, dP, list(D_cts), P_ct
+    D_new = []
+    for k in range(n):
+        a = _align(orc, dD[k], eta, D_cts[k].scale)
+        D_new.append(orc.sub(orc.drop_level(D_cts[k], a.level), a))
+    a = _align(orc, dP, eta, P_ct.scale)
+    P_new = orc.drop_level(orc.sub(orc.drop_level(P_ct, a.level), a), D_new[0].level - 1)
+    return dD, dP, D_new, P_new

@@ -123,3 +123,54 @@ def test_encrypted_train_step_matches_fp64(small):
         assert np.max(np.abs(dec(o, O1[j], c) - (O[j] - eta * gO[j]))) < tol
     # a gradient step lowers the loss
     assert OF.train_loss_plain(V, Y, H - eta * gH, O - eta * gO) < OF.train_loss_plain(V, Y, H, O)
+
+
+@pytest.fixture(scope="module")
+def small_diag():
+    o = OK.Oracle(10, 10, 2, 2, 60, 40, 60, 2.0 ** 40, (0x7C, 1, 2, 3))
+    n, t = 4, 512
+    steps = list(range(1, n)) + [n << s for s in range(7)] + [-1, -2]
+    o.keygen(steps, True)
+    return o
+
+
+def test_encrypted_train_step_diag_matches_fp64(small_diag):
+    """The rotation-light training step (diagonal layout) decrypts to the diagonals of the FP64
+    dH, to dO in the output layout, and to the SGD update."""
+    o = small_diag
+    t = o.N // 2
+    rng = np.random.default_rng(13)
+    B, m, n, c, eta = 2, 400, 4, 2, 0.5
+    V = np.zeros((B, m))
+    for b in range(B):
+        np.add.at(V[b], rng.integers(0, m, 25), 1.0)
+        V[b] /= V[b].sum()
+    Y = np.eye(c)[[1, 0]]
+    H = rng.normal(0, 0.1, (m, n))
+    O = rng.normal(0, 0.1, (n, c))
+    D, P, M = OF.train_pack_diag(H, O, t)
+    l0 = 10
+    pad = lambda x: np.concatenate([x, np.zeros(t - x.size)])  # noqa: E731
+    v_ct = [o.encrypt_sk(o.encode(pad(V[b]), level=l0), 100 + b) for b in range(B)]
+    D_ct = [o.encrypt_sk(o.encode(D[k], level=l0), 200 + k) for k in range(n)]
+    P_ct = o.encrypt_sk(o.encode(P, level=l0 - 1), 300)
+    M_pt = o.encode(M, scale=2.0 ** 40, level=l0)
+    lw, sw = OF.train_label_spec_diag(o, l0, v_ct[0].scale, D_ct[0].scale, P_ct.scale, M_pt.scale)
+    assert lw == l0 - 4
+    wv = np.zeros(t)
+    w_ct = []
+    for b in range(B):
+        wv[:] = 0
+        wv[[n * cc for cc in range(c)]] = Y[b] - 0.25
+        w_ct.append(o.encrypt_sk(o.encode(wv, scale=sw, level=lw), 400 + b))
+    dD, dP, D1, P1 = OF.encrypted_train_step_diag(o, v_ct, w_ct, D_ct, P_ct, M_pt, eta)
+    gH, gO = OF.train_grads_plain(V, Y, H, O)
+    gD, gP, _ = OF.train_pack_diag(np.vstack([gH, np.zeros((t - m, n))])[:t], gO, t)
+    tol = 2.0 ** -20
+    for k in range(n):
+        assert dD[k].level == l0 - 6 and D1[k].level == l0 - 7 and D1[k].scale == D_ct[k].scale
+        assert np.max(np.abs(dec(o, dD[k], t) - gD[k])) < tol
+        assert np.max(np.abs(dec(o, D1[k], t) - (D[k] - eta * gD[k]))) < tol
+    assert dP.level == l0 - 5 and P1.level == l0 - 8 and P1.scale == P_ct.scale
+    assert np.max(np.abs(dec(o, dP, t)[: n * c] - gP[: n * c])) < tol
+    assert np.max(np.abs(dec(o, P1, t)[: n * c] - (P - eta * gP)[: n * c])) < tol
