@@ -442,7 +442,23 @@ typedef struct pft_ft_tape pft_ft_tape; /* forward state kept for the backward p
 /* Copies H[0..n-1] and O[0..n-1] into a new encrypted model. */
 int pft_ft_enc_model_create(pft_ctx* ctx, const pft_ct* const* H, const pft_ct* const* O, int m, int n, int c,
                             pft_ft_enc_model** out);
-/* Copy of H_j (which = 0) or O_j (which = 1) into out. */
+/* Rotation-light layout (not in the paper): D[k] = the diagonals D_k[i] = H[(i+k) mod t, i mod n]
+ * (k < n, level l0), P = O packed as P[n c' + j] = O[j, c'] (one ciphertext, level l0-1) and a
+ * plaintext mask with 1 in the score slots n c' (level >= l0-2; its leading limbs serve lower
+ * levels).  Labels w_b = y_b - 1/4 spread over the class blocks: w_b[c'] in slots n c' .. n c' + n - 1.
+ * Per document n-1 hoisted rotations of v_b and rotate-and-sums by n 2^s, 2^s and -2^s replace
+ * the n log2(t) rotations of each TotalSum: h_b comes out replicated with period n, the scores
+ * spread over their blocks, and the backward reuses the rotated documents (dD_k = sum_b
+ * rot(v_b, k) E_b).  lift_bits K (0..30): the documents are multiplied by the integer 2^K before
+ * their rotations, which divides the key-switching noise those rotations add (the only key
+ * switches at the input scale, summed over the vocabulary) by 2^K; a mask encoded at 2^-K times
+ * the usual scale returns the scores to it.  Gradients: grad_H receives the n diagonals of dH
+ * (level l0-6), grad_O[0] receives dO in the layout of P (level l0-5).  Seven levels per step:
+ * the update leaves D_k at l0-7 and P at l0-8.  Needs m <= t, n a power of two dividing t,
+ * n c <= t, and rotation keys for 1..n-1, n 2^s (< t) and -2^s (< n).  The handles are copied. */
+int pft_ft_enc_model_create_diag(pft_ctx* ctx, const pft_ct* const* D, const pft_ct* P, const pft_pt* mask, int m,
+                                 int n, int c, int lift_bits, pft_ft_enc_model** out);
+/* Copy of H_j (which = 0) or O_j (which = 1) into out (diagonal layout: D_j, and P for j = 0). */
 int pft_ft_enc_model_get(pft_ctx* ctx, const pft_ft_enc_model* model, int which, int j, pft_ct* out);
 int pft_ft_enc_model_levels(const pft_ft_enc_model* model, int* level_H, int* level_O);
 int pft_ft_enc_model_destroy(pft_ft_enc_model* model);

@@ -219,17 +219,23 @@ def encrypted_train_step(orc, v_cts, w_cts, H_cts, O_cts, eta):
 # ---- rotation-light training (diagonal packing; not in the paper) ------------------------------
 # Model: D_k[i] = H[(i + k) mod t, i mod n] (k < n, the diagonals of the inference variant) at
 # level l0 and P[n c + j] = O[j, c] (one ciphertext) at level l0 - 1; a plaintext mask M with
-# 1 in the score slots n c.  The client sends v_b (m <= t) and w_b = y_b - 1/4 in slots n c.
-#   forward  R_bk = rot(v_b, k) (hoisted), Q_b = Relin(sum_k R_bk x D_k),
+# 1 in the score slots n c.  The client sends v_b (m <= t) and w_b = y_b - 1/4 spread over the
+# class blocks (w_b[c] in slots n c .. n c + n - 1).
+#   lift     v'_b = 2^K v_b (an exact integer product: the scale grows by 2^K)
+#   forward  R_bk = rot(v'_b, k) (hoisted), Q_b = Relin(sum_k R_bk x D_k),
 #            Hb = Rescale(Q_b + rot(Q_b, n 2^s) ...)             h_b[i mod n] in slot i, l0-1
 #            Sb = Rescale(S + rot(S, 2^s) ..., S = Relin(Hb x P)) s_b[c] in slot n c,  l0-2
-#            Sm = Rescale(Sb * M)                                 zero off the score slots, l0-3
-#            g_b = [Rescale(Relin(u x u)), u = Sm + 2] at 8x its scale - 1/2 - w_b,    l0-4
-#   backward Gb = g_b + rot(g_b, -2^s) ...                        g_b[c] in block c
-#            dP = Rescale(Relin(sum_b Hb x Gb))                   dO[j, c] in slot n c + j, l0-5
+#            Sm = Rescale(Z + rot(Z, -2^s) ..., Z = Sb * M)       s_b[c] over block c, l0-3
+#            Gb = [Rescale(Relin(u x u)), u = Sm + 2] at 8x its scale - 1/2 - w_b,     l0-4
+#   backward dP = Rescale(Relin(sum_b Hb x Gb))                   dO[j, c] in slot n c + j, l0-5
 #            Eb = Rescale(X + rot(X, n 2^s) ..., X = Relin(Gb x P)) e_b[i mod n] in slot i, l0-5
 #            dD_k = Rescale(Relin(sum_b R_bk x Eb))              the diagonals of dH, l0-6
 #   update   D_k <- D_k - Align(dD_k) (l0-7), P <- drop(P - Align(dP), l0-8): one level below D.
+# Noise: the document rotations are the only key switches applied at the input scale; their
+# rounding noise is summed over the vocabulary in Hb, and the lift by 2^K divides it by 2^K
+# (a mask encoded at 2^-K times the usual scale brings the scores back).  The scores are spread
+# over their blocks before the rescale that follows the mask, so that the rescale noise of the
+# slots around a score is not summed into it.
 
 def train_pack_diag(H, O, t):
     """Slot vectors of the diagonal training layout: D [n][t], P [t], mask M [t]."""
@@ -240,16 +246,23 @@ def train_pack_diag(H, O, t):
     return D, P, M
 
 
-def train_label_spec_diag(orc, level, sc_v, sc_D, sc_P, sc_M):
+def train_label_diag(y, n, t):
+    """Label slot vector of the diagonal layout: y[c] - 1/4 over block c."""
+    w = np.zeros(t)
+    w[: n * len(y)] = np.repeat(np.asarray(y, np.float64) - 0.25, n)
+    return w
+
+
+def train_label_spec_diag(orc, level, sc_v, sc_D, sc_P, sc_M, lift_bits=0):
     q = orc.q
-    sh = sc_v * sc_D / float(q[level - 1])
+    sh = sc_v * 2.0 ** lift_bits * sc_D / float(q[level - 1])
     ss = sh * sc_P / float(q[level - 2])
     sm = ss * sc_M / float(q[level - 3])
     su = sm * sm / float(q[level - 4])
     return level - 4, 8.0 * su
 
 
-def encrypted_train_step_diag(orc, v_cts, w_cts, D_cts, P_ct, M_pt, eta):
+def encrypted_train_step_diag(orc, v_cts, w_cts, D_cts, P_ct, M_pt, eta, lift_bits=0):
     """One minibatch step of the diagonal layout on the oracle.  Returns (dD [n], dP, D' [n], P')."""
     B, n = len(v_cts), len(D_cts)
     t = orc.N // 2
@@ -257,7 +270,8 @@ def encrypted_train_step_diag(orc, v_cts, w_cts, D_cts, P_ct, M_pt, eta):
     assert all(x.level == l0 for x in v_cts + D_cts) and P_ct.level == l0 - 1
     R, Hs, G = [], [], []
     for b in range(B):
-        Rb = [v_cts[b]] + orc.rotate_hoisted(v_cts[b], list(range(1, n)))
+        v = orc.mul_const(v_cts[b], 1.0, 2.0 ** lift_bits) if lift_bits else v_cts[b]
+        Rb = [v] + orc.rotate_hoisted(v, list(range(1, n)))
         R.append(Rb)
         Q = orc.relin(*orc.tensor_sum([(Rb[k], D_cts[k]) for k in range(n)]))
         st = n
@@ -272,17 +286,15 @@ def encrypted_train_step_diag(orc, v_cts, w_cts, D_cts, P_ct, M_pt, eta):
             S = orc.add(S, orc.rotate(S, st))
             st *= 2
         Sb = orc.rescale(S)
-        Mq = Plaintext(M_pt.m[:Sb.level], M_pt.scale)
-        Sm = orc.rescale(orc.mul_plain(Sb, Mq))
-        u = orc.add_const(Sm, 2.0)
-        U = orc.rescale(orc.relin(*orc.tensor_sum([(u, u)])))
-        U = orc.add_const(orc.set_scale(U, 8.0 * U.scale), -0.5)
-        g = orc.sub(U, w_cts[b])
+        Z = orc.mul_plain(Sb, Plaintext(M_pt.m[:Sb.level], M_pt.scale))
         st = 1
         while st < n:
-            g = orc.add(g, orc.rotate(g, -st))
+            Z = orc.add(Z, orc.rotate(Z, -st))
             st *= 2
-        G.append(g)
+        u = orc.add_const(orc.rescale(Z), 2.0)
+        U = orc.rescale(orc.relin(*orc.tensor_sum([(u, u)])))
+        U = orc.add_const(orc.set_scale(U, 8.0 * U.scale), -0.5)
+        G.append(orc.sub(U, w_cts[b]))
     lg = G[0].level
     dP = orc.rescale(orc.relin(*orc.tensor_sum([(orc.drop_level(Hs[b], lg), G[b]) for b in range(B)])))
     Pg = orc.drop_level(P_ct, lg)

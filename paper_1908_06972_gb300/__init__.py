@@ -114,6 +114,7 @@ def lib():
             "pft_fasttext_infer": [vp, vp, pp, i, vp], "pft_fasttext_infer_batch": [vp, vp, pp, i, i, pp],
             "pft_ft_enc_model_create": [vp, pp, pp, i, i, i, pp], "pft_ft_enc_model_get": [vp, vp, i, i, vp],
             "pft_ft_enc_model_levels": [vp, ip, ip], "pft_ft_enc_model_destroy": [vp],
+            "pft_ft_enc_model_create_diag": [vp, pp, vp, vp, i, i, i, i, pp],
             "pft_fasttext_train_spec": [vp, vp, d, ip, ip, POINTER(c_double)],
             "pft_fasttext_train_forward": [vp, vp, pp, pp, i, pp], "pft_ft_tape_score": [vp, vp, i, vp],
             "pft_fasttext_train_backward": [vp, vp, pp, pp], "pft_ft_tape_destroy": [vp],
@@ -162,7 +163,7 @@ def exported_symbols():
             "pft_ct_set_scale", "pft_ft_enc_model_create", "pft_ft_enc_model_get", "pft_ft_enc_model_levels",
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
-            "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest"]
+            "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag"]
 
 
 def _check(rc, ctx=None):
@@ -587,6 +588,12 @@ def pft_fasttext_infer_batch(ctx, model, v, n_chunks, scores):
 def pft_ft_enc_model_create(ctx, H, O, m, n, c):
     out = c_void_p()
     _check(lib().pft_ft_enc_model_create(ctx, _arr(H), _arr(O), m, n, c, ctypes.byref(out)), ctx)
+    return out
+
+
+def pft_ft_enc_model_create_diag(ctx, D, P, mask, m, n, c, lift_bits=0):
+    out = c_void_p()
+    _check(lib().pft_ft_enc_model_create_diag(ctx, _arr(D), P, mask, m, n, c, lift_bits, ctypes.byref(out)), ctx)
     return out
 
 

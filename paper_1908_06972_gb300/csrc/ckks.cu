@@ -592,7 +592,7 @@ static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t s
 // Rotations of one ciphertext by several steps sharing one ModUp of c1 (hoisting): the
 // extended digits (evaluation form) are permuted by each step's automorphism, then go through
 // the inner product with that step's key and ModDown; out_i = (aut(c0) + u0', u1').
-static void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs) {
+void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs) {
     check_ct(a);
     NEED(n >= 0 && (n == 0 || (steps && outs)), PFT_ERR_ARG, "bad arguments");
     const int l = a->level, k = c->k, L = c->L, alpha = c->alpha, E = l + k, beta = (l + alpha - 1) / alpha;

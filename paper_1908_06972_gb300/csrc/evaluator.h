@@ -209,6 +209,8 @@ void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, in
 void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B, pft_ct* const* out);
 void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out);
 void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out);
+// Rotations of one ciphertext by several steps sharing one ModUp (hoisting).
+void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs);
 // T[i] += rotate(T[i], g) for every ciphertext of T (any levels), tiled to bound scratch memory.
 void rot_accumulate(pft_ctx* c, const std::vector<pft_ct*>& T, u32 g);
 // out[i] = the first `level` limbs of a[i] (the same message at a lower level).

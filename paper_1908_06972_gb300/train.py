@@ -13,20 +13,31 @@ import torch
 
 from . import (pft_add_batch, pft_ct_create, pft_ct_destroy, pft_fasttext_train_backward,
                pft_fasttext_train_forward, pft_fasttext_train_spec, pft_fasttext_train_update,
-               pft_ft_enc_model_create, pft_ft_enc_model_destroy, pft_ft_enc_model_get, pft_ft_enc_model_levels,
-               pft_ft_tape_destroy)
+               pft_ft_enc_model_create, pft_ft_enc_model_create_diag, pft_ft_enc_model_destroy,
+               pft_ft_enc_model_get, pft_ft_enc_model_levels, pft_ft_tape_destroy)
 
 
 class EncryptedFastText:
     """H (m x n) and O (n x c) as ciphertexts: H[j] = column j over the vocabulary slots,
-    O[j] = row j in slots 0..c-1 one level below H (the handles are copied)."""
+    O[j] = row j in slots 0..c-1 one level below H (the handles are copied).  `diag` builds
+    the rotation-light layout instead: H_cts = the n diagonals, O_cts = [P], plus the mask
+    and the documents' lift (bits)."""
 
-    def __init__(self, ctx, H_cts, O_cts, m, n, c):
+    def __init__(self, ctx, H_cts, O_cts, m, n, c, mask=None, lift_bits=0):
         self.ctx, self.n = ctx, n
-        self.model = pft_ft_enc_model_create(ctx, H_cts, O_cts, m, n, c)
+        if mask is None:
+            self.model = pft_ft_enc_model_create(ctx, H_cts, O_cts, m, n, c)
+            self.n_o = n
+        else:
+            self.model = pft_ft_enc_model_create_diag(ctx, H_cts, O_cts[0], mask, m, n, c, lift_bits)
+            self.n_o = 1
         self.anchor_H = torch.zeros((), dtype=torch.float64, requires_grad=True)
         self.anchor_O = torch.zeros((), dtype=torch.float64, requires_grad=True)
         self.grad_H = self.grad_O = None
+
+    @classmethod
+    def diag(cls, ctx, D_cts, P_ct, mask, m, n, c, lift_bits=0):
+        return cls(ctx, D_cts, [P_ct], m, n, c, mask=mask, lift_bits=lift_bits)
 
     def parameters(self):
         return [self.anchor_H, self.anchor_O]
@@ -86,7 +97,7 @@ class _FastTextLoss(torch.autograd.Function):
             raise ValueError("the encrypted loss can only be differentiated with an upstream gradient of 1")
         m = fctx.model
         gH = [pft_ct_create(m.ctx) for _ in range(m.n)]
-        gO = [pft_ct_create(m.ctx) for _ in range(m.n)]
+        gO = [pft_ct_create(m.ctx) for _ in range(m.n_o)]
         try:
             pft_fasttext_train_backward(m.ctx, fctx.tape, gH, gO)
         except Exception:

@@ -231,3 +231,152 @@ def test_training_errors(pair, data):
         assert e.value.code == pf.PFT_ERR_LEVEL_MISMATCH
     finally:
         pf.pft_ft_enc_model_destroy(model)
+
+
+# ---- rotation-light training (diagonal layout) ------------------------------------------------
+# N = 2^12 (t = 2048 slots), 10 primes so the seven levels of the step fit; n = 4 diagonals.
+# Keys: 1..n-1 (hoisted document rotations), n 2^s (the replication sums over t/n blocks),
+# -2^s (the spreading of the scores over their blocks) and relinearisation.  Each model is run
+# unlifted (mask at 2^40) and with the documents lifted by 2^10 (mask at 2^30).
+
+DL0, DN, DM, DC, DB = 10, 4, 400, 2, 3
+
+
+@pytest.fixture(scope="module")
+def pair_diag(gpu):
+    t = 2048
+    steps = list(range(1, DN)) + [DN << s for s in range(20) if (DN << s) < t] + [-(1 << s) for s in range(2)]
+    p = Pair(gpu, 12, DL0, 2, 2, seed=(0x7C, 9, 9, 1), rot_steps=steps)
+    yield p
+    p.close()
+
+
+@pytest.fixture(scope="module", params=[0, 10])
+def data_diag(pair_diag, request):
+    lift = request.param
+    o, t = pair_diag.orc, pair_diag.N // 2
+    rng = np.random.default_rng(31)
+    V = np.zeros((DB, DM))
+    for b in range(DB):
+        np.add.at(V[b], rng.integers(0, DM, 25), 1.0)
+        V[b] /= V[b].sum()
+    Y = np.eye(DC)[[1, 0, 1]]
+    H = rng.normal(0, 0.1, (DM, DN))
+    O = rng.normal(0, 0.1, (DN, DC))
+    D, P, Mv = OF.train_pack_diag(H, O, t)
+    pad = lambda x: np.concatenate([x, np.zeros(t - x.size)])  # noqa: E731
+    v = [o.encrypt_sk(o.encode(pad(V[b]), level=DL0), 100 + b) for b in range(DB)]
+    Dc = [o.encrypt_sk(o.encode(D[k], level=DL0), 200 + k) for k in range(DN)]
+    Pc = o.encrypt_pk(o.encode(P, level=DL0 - 1), 300)
+    Mp = o.encode(Mv, scale=2.0 ** (40 - lift), level=DL0)
+    lw, sw = OF.train_label_spec_diag(o, DL0, v[0].scale, Dc[0].scale, Pc.scale, Mp.scale, lift)
+    w = [o.encrypt_sk(o.encode(OF.train_label_diag(Y[b], DN, t), scale=sw, level=lw), 400 + b) for b in range(DB)]
+    want = OF.encrypted_train_step_diag(o, v, w, Dc, Pc, Mp, ETA, lift)
+    return dict(V=V, Y=Y, H=H, O=O, v=v, w=w, Dc=Dc, Pc=Pc, Mp=Mp, spec=(lw, sw), want=want, lift=lift)
+
+
+def gpu_model_diag(p, d):
+    return p.pft.pft_ft_enc_model_create_diag(p.ctx, [p.ct(x) for x in d["Dc"]], p.ct(d["Pc"]), p.pt(d["Mp"]),
+                                              DM, DN, DC, d["lift"])
+
+
+def check_model_diag(p, model, want_D, want_P, what):
+    pf = p.pft
+    for k in range(DN):
+        h = p.empty()
+        pf.pft_ft_enc_model_get(p.ctx, model, 0, k, h)
+        p.assert_equal(h, want_D[k], "%s D_%d" % (what, k))
+    h = p.empty()
+    pf.pft_ft_enc_model_get(p.ctx, model, 1, 0, h)
+    p.assert_equal(h, want_P, "%s P" % what)
+
+
+def run_fused_diag(p, d):
+    model = gpu_model_diag(p, d)
+    gD = [p.empty() for _ in range(DN)]
+    gP = [p.empty()]
+    p.pft.pft_fasttext_train_step(p.ctx, model, [p.ct(x) for x in d["v"]], [p.ct(x) for x in d["w"]], ETA, gD, gP)
+    return model, gD, gP
+
+
+def test_diag_spec_and_levels(pair_diag, data_diag):
+    pf = pair_diag.pft
+    model = gpu_model_diag(pair_diag, data_diag)
+    try:
+        assert pf.pft_fasttext_train_spec(pair_diag.ctx, model, data_diag["v"][0].scale) == \
+            (DL0, data_diag["spec"][0], data_diag["spec"][1])
+        assert pf.pft_ft_enc_model_levels(model) == (DL0, DL0 - 1)
+    finally:
+        pf.pft_ft_enc_model_destroy(model)
+
+
+@pytest.mark.parametrize("tile", [None, "1"])
+def test_diag_fused_step_bit_exact(pair_diag, data_diag, tile):
+    pf = pair_diag.pft
+    dD, dP, D1, P1 = data_diag["want"]
+    if tile:
+        os.environ["PFT_TRAIN_TILE"] = tile
+    try:
+        model, gD, gP = run_fused_diag(pair_diag, data_diag)
+    finally:
+        os.environ.pop("PFT_TRAIN_TILE", None)
+    try:
+        for k in range(DN):
+            pair_diag.assert_equal(gD[k], dD[k], "dD_%d" % k)
+        pair_diag.assert_equal(gP[0], dP, "dP")
+        assert pf.pft_ft_enc_model_levels(model) == (DL0 - 7, DL0 - 8)
+        check_model_diag(pair_diag, model, D1, P1, "updated")
+    finally:
+        pf.pft_ft_enc_model_destroy(model)
+
+
+def test_diag_autograd_path_bit_exact(pair_diag, data_diag):
+    from paper_1908_06972_gb300 import train as T
+
+    p, d = pair_diag, data_diag
+    dD, dP, D1, P1 = d["want"]
+    m = T.EncryptedFastText.diag(p.ctx, [p.ct(x) for x in d["Dc"]], p.ct(d["Pc"]), p.pt(d["Mp"]), DM, DN, DC,
+                                 d["lift"])
+    try:
+        opt = T.EncryptedSGD(m, ETA)
+        m.loss([p.ct(x) for x in d["v"]], [p.ct(x) for x in d["w"]]).backward()
+        assert len(m.grad_O) == 1
+        for k in range(DN):
+            p.assert_equal(m.grad_H[k], dD[k], "autograd dD_%d" % k)
+        p.assert_equal(m.grad_O[0], dP, "autograd dP")
+        opt.step()
+        check_model_diag(p, m.model, D1, P1, "autograd updated")
+    finally:
+        m.close()
+
+
+def test_diag_decrypted_gradients_vs_fp64(pair_diag, data_diag):
+    p, d, o = pair_diag, data_diag, pair_diag.orc
+    t = p.N // 2
+    model, gD, gP = run_fused_diag(p, d)
+    try:
+        dec = lambda h: o.decode(o.decrypt(OK.Ciphertext(p.export(h), p.pft.pft_ct_scale(h)))).real  # noqa: E731
+        got_D = [dec(gD[k]) for k in range(DN)]
+        got_P = dec(gP[0])
+    finally:
+        p.pft.pft_ft_enc_model_destroy(model)
+    gH, gO = OF.train_grads_plain(d["V"], d["Y"], d["H"], d["O"])
+    ref_D, ref_P, _ = OF.train_pack_diag(np.vstack([gH, np.zeros((t - DM, DN))]), gO, t)
+    for k in range(DN):
+        assert np.max(np.abs(got_D[k] - ref_D[k])) < 2.0 ** -20, k
+    assert np.max(np.abs(got_P[:DN * DC] - ref_P[:DN * DC])) < 2.0 ** -20
+
+
+def test_diag_model_errors(pair_diag, data_diag):
+    p, d = pair_diag, data_diag
+    pf = p.pft
+    D = [p.ct(x) for x in d["Dc"]]
+    with pytest.raises(pf.PftError) as e:  # n not a power of two
+        pf.pft_ft_enc_model_create_diag(p.ctx, D[:3], p.ct(d["Pc"]), p.pt(d["Mp"]), DM, 3, DC)
+    assert e.value.code == pf.PFT_ERR_ARG
+    with pytest.raises(pf.PftError) as e:  # lift out of range
+        pf.pft_ft_enc_model_create_diag(p.ctx, D, p.ct(d["Pc"]), p.pt(d["Mp"]), DM, DN, DC, 31)
+    assert e.value.code == pf.PFT_ERR_ARG
+    with pytest.raises(pf.PftError) as e:  # P not one level below the diagonals
+        pf.pft_ft_enc_model_create_diag(p.ctx, D, D[0], p.pt(d["Mp"]), DM, DN, DC)
+    assert e.value.code == pf.PFT_ERR_LEVEL_MISMATCH

@@ -134,9 +134,11 @@ def small_diag():
     return o
 
 
-def test_encrypted_train_step_diag_matches_fp64(small_diag):
+@pytest.mark.parametrize("lift", [0, 10])
+def test_encrypted_train_step_diag_matches_fp64(small_diag, lift):
     """The rotation-light training step (diagonal layout) decrypts to the diagonals of the FP64
-    dH, to dO in the output layout, and to the SGD update."""
+    dH, to dO in the output layout, and to the SGD update; with the documents lifted by 2^10
+    and the mask at 2^30 the scales come back to those of the unlifted step."""
     o = small_diag
     t = o.N // 2
     rng = np.random.default_rng(13)
@@ -154,16 +156,13 @@ def test_encrypted_train_step_diag_matches_fp64(small_diag):
     v_ct = [o.encrypt_sk(o.encode(pad(V[b]), level=l0), 100 + b) for b in range(B)]
     D_ct = [o.encrypt_sk(o.encode(D[k], level=l0), 200 + k) for k in range(n)]
     P_ct = o.encrypt_sk(o.encode(P, level=l0 - 1), 300)
-    M_pt = o.encode(M, scale=2.0 ** 40, level=l0)
-    lw, sw = OF.train_label_spec_diag(o, l0, v_ct[0].scale, D_ct[0].scale, P_ct.scale, M_pt.scale)
+    M_pt = o.encode(M, scale=2.0 ** (40 - lift), level=l0)
+    lw, sw = OF.train_label_spec_diag(o, l0, v_ct[0].scale, D_ct[0].scale, P_ct.scale, M_pt.scale, lift)
     assert lw == l0 - 4
-    wv = np.zeros(t)
-    w_ct = []
-    for b in range(B):
-        wv[:] = 0
-        wv[[n * cc for cc in range(c)]] = Y[b] - 0.25
-        w_ct.append(o.encrypt_sk(o.encode(wv, scale=sw, level=lw), 400 + b))
-    dD, dP, D1, P1 = OF.encrypted_train_step_diag(o, v_ct, w_ct, D_ct, P_ct, M_pt, eta)
+    if lift:  # the lift and the mask cancel: the labels sit at the unlifted step's scale
+        assert sw == OF.train_label_spec_diag(o, l0, v_ct[0].scale, D_ct[0].scale, P_ct.scale, 2.0 ** 40)[1]
+    w_ct = [o.encrypt_sk(o.encode(OF.train_label_diag(Y[b], n, t), scale=sw, level=lw), 400 + b) for b in range(B)]
+    dD, dP, D1, P1 = OF.encrypted_train_step_diag(o, v_ct, w_ct, D_ct, P_ct, M_pt, eta, lift)
     gH, gO = OF.train_grads_plain(V, Y, H, O)
     gD, gP, _ = OF.train_pack_diag(np.vstack([gH, np.zeros((t - m, n))])[:t], gO, t)
     tol = 2.0 ** -20
@@ -174,3 +173,8 @@ def test_encrypted_train_step_diag_matches_fp64(small_diag):
     assert dP.level == l0 - 5 and P1.level == l0 - 8 and P1.scale == P_ct.scale
     assert np.max(np.abs(dec(o, dP, t)[: n * c] - gP[: n * c])) < tol
     assert np.max(np.abs(dec(o, P1, t)[: n * c] - (P - eta * gP)[: n * c])) < tol
+
+
+def test_train_label_diag_layout():
+    w = OF.train_label_diag([1.0, 0.0, 0.5], 4, 16)
+    assert np.array_equal(w, [0.75] * 4 + [-0.25] * 4 + [0.25] * 4 + [0.0] * 4)
