@@ -30,12 +30,29 @@ namespace pft {
 // Shoup product x W mod q in [0, 2q), formed as x w + hq (-q) (mod 2^64) so that the
 // subtraction folds into the multiply-adds; nq = -q mod 2^64.
 __device__ __forceinline__ u64 shoup_nq(u64 x, ulonglong2 W, u64 nq) { return x * W.x + mulhi(x, W.y) * nq; }
+// Quotient estimate of the Shoup product without the low x low partial product:
+// floor(x w' / 2^64) - {0, 1, 2}.  Writing x = xh 2^32 + xl and w' = wh 2^32 + wl, the exact
+// value is xh wh + floor((xh wl + xl wh + floor(xl wl / 2^32)) / 2^32); the three dropped
+// low halves sum to less than 3 * 2^32, so at most 2 carries are lost.  With it the Shoup
+// product x w - h q lies in [0, 4q) instead of [0, 2q).
+__device__ __forceinline__ u64 mulhi_est(u64 x, u64 w) {
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    const uint32_t wl = (uint32_t)w, wh = (uint32_t)(w >> 32);
+    return (u64)xh * wh + __umulhi(xh, wl) + __umulhi(xl, wh);
+}
 // Cooley-Tukey (Harvey): X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q).  LAZY (primes below
-// 2^58): no correction of X, values grow by less than 2q per stage, so the 16 stages of an
-// N = 2^16 forward transform from [0, 2q) stay below 34q < 2^64.
+// 2^57): no correction of X and the estimated quotient, so WY lies in [0, 4q) and values grow
+// by less than 4q per stage: the 16 stages of an N = 2^16 forward transform from [0, 2q) stay
+// below 66q < 2^63.1.
 template <bool LAZY = false>
 __device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
-    if (!LAZY && X >= q2) X -= q2;
+    if (LAZY) {
+        const u64 T = Y * W.x - mulhi_est(Y, W.y) * q;
+        Y = X - T + 2 * q2;
+        X = X + T;
+        return;
+    }
+    if (X >= q2) X -= q2;
     const u64 T = shoup_nq(Y, W, 0 - q);
     Y = X - T + q2;
     X = X + T;
@@ -209,7 +226,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(512, MINB)
 // exchange (odd strides 17 / 273: conflict-free); pass B stages its final store (forward)
 // or first load (inverse) through shared memory to keep the global side coalesced.
 constexpr int kRowStride = 273;  // 256 + 16 padding + 1
-constexpr u64 kLazyBound = 1ull << 58;  // forward butterflies skip the correction below this prime
+constexpr u64 kLazyBound = 1ull << 57;  // forward butterflies skip the correction below this prime
 
 template <bool INV, int LOGT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet in, PolySet out, int is_final) {
@@ -291,7 +308,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
         for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
         if (lazy) {
             ntt16_round<false, 0, 8, true>(x, w << 4, u, tw, q, q2, NI, NI1);
-            // values below 34q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
+            // values below 66q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
             // (mu = floor(2^(64+s) / q)), then one correction
             const u64 one_p = __ldg(&t.primes[pi].mu) >> __ldg(&t.primes[pi].s);
 #pragma unroll

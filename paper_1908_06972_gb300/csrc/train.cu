@@ -509,15 +509,16 @@ void bwd_tile_diag(pft_ctx* c, pft_ft_tape& T, int b0, int b1, Accum& acc, bool 
 }
 
 // levels a call needs: forward and backward / with the update
-int min_level(const pft_ft_enc_model* M, bool update) {
+int levels_needed(const pft_ft_enc_model* M, bool update) {
     return M->variant == 0 ? (update ? 7 : 6) : (update ? 9 : 7);
 }
 
 void check_batch(pft_ctx* c, const pft_ft_enc_model* M, const pft_ct* const* docs, const pft_ct* const* labels,
-                 int B, int min_level) {
+                 int B, bool with_update) {
     check_model(M, c);
     NEED(B >= 1 && docs && labels, PFT_ERR_ARG, "bad arguments");
     const int l0 = M->H[0].level;
+    const int min_level = levels_needed(M, with_update);
     NEED(l0 >= min_level, PFT_ERR_LEVEL_MISMATCH,
          "the model has " + std::to_string(l0) + " levels left, this call needs " + std::to_string(min_level));
     NEED(c->keys.count(0), PFT_ERR_NO_KEY, "no relinearisation key");
@@ -699,7 +700,7 @@ int pft_fasttext_train_forward(pft_ctx* c, const pft_ft_enc_model* M, const pft_
                                const pft_ct* const* labels, int B, pft_ft_tape** out) {
     return guard(c, [&] {
         NEED(out, PFT_ERR_ARG, "bad arguments");
-        check_batch(c, M, docs, labels, B, min_level(M, false));
+        check_batch(c, M, docs, labels, B, false);
         std::unique_ptr<pft_ft_tape> T(new pft_ft_tape());
         init_tape(c, M, docs, B, *T);
         const int tile = tile_docs(c, M, T->l0);
@@ -755,7 +756,7 @@ int pft_fasttext_train_step(pft_ctx* c, pft_ft_enc_model* M, const pft_ct* const
                             int B, double eta, pft_ct* const* grad_H, pft_ct* const* grad_O) {
     return guard(c, [&] {
         NEED(std::isfinite(eta), PFT_ERR_ARG, "bad learning rate");
-        check_batch(c, M, docs, labels, B, min_level(M, eta != 0));
+        check_batch(c, M, docs, labels, B, eta != 0);
         const int n = M->n, no = n_grad_O(M);
         std::vector<pft_ct> own;  // gradients the caller does not keep
         std::vector<pft_ct*> gH(n), gO(no);

@@ -1,9 +1,10 @@
 """Edge cases of the GPU path against the oracle and the layout definition.
 
 * Transforms at every supported shape class (one pass N <= 2^14, 8 + 7 stages at 2^15, the
-  two-pass kernels at 2^16) with primes on both sides of the lazy-butterfly bound 2^58 and of
-  small size, on extreme inputs (every coefficient q - 1, alternating 0 / q - 1) and random
-  ones: forward equal to the evaluation definition, inverse restoring the input exactly.
+  two-pass kernels at 2^16) with primes on both sides of the lazy-butterfly bound 2^57 (57-bit
+  primes are the largest on the lazy path), the benchmark's 50-bit primes and small ones, on
+  extreme inputs (every coefficient q - 1, alternating 0 / q - 1) and random ones: forward
+  equal to the evaluation definition, inverse restoring the input exactly.
 * Degenerate operations: empty batches, identity and wrap-around rotations, level-1
   ciphertexts (one prime: one digit), rescale refused at level 1."""
 import numpy as np
@@ -19,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("logn", [4, 8, 11, 15, 16])
-@pytest.mark.parametrize("bits", [(59, 58, 60), (30, 30, 31)])
+@pytest.mark.parametrize("bits", [(59, 58, 60), (57, 57, 60), (58, 57, 58), (50, 50, 60), (30, 30, 31)])
 def test_transform_extreme_inputs(gpu, logn, bits):
     import torch
 
