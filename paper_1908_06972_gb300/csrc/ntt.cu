@@ -12,7 +12,8 @@
 // N points split into independent sub-transforms of 2^S points at stride T =
 // N >> (s0 + S); a CTA loads C of them into shared memory with coalesced loads,
 // each thread keeps 16 points in registers and applies up to 4 stages per round
-// (Harvey lazy butterflies: forward values in [0, 4q), inverse in [0, 2q)), and
+// (Harvey lazy butterflies: forward values in [0, 4q), inverse in [0, 2q), [0, 4q) in the
+// N = 2^16 kernels), and
 // rounds exchange through shared memory.  N <= 2^14: one pass, one CTA per limb.
 // N = 2^15, 2^16: two passes (8 + 7 or 8 + 8 stages).
 #include <cooperative_groups.h>
@@ -40,35 +41,36 @@ __device__ __forceinline__ u64 mulhi_est(u64 x, u64 w) {
     const uint32_t wl = (uint32_t)w, wh = (uint32_t)(w >> 32);
     return (u64)xh * wh + __umulhi(xh, wl) + __umulhi(xl, wh);
 }
-// Cooley-Tukey (Harvey): X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q).  LAZY (primes below
-// 2^57): no correction of X and the estimated quotient, so WY lies in [0, 4q) and values grow
-// by less than 4q per stage: the 16 stages of an N = 2^16 forward transform from [0, 2q) stay
-// below 66q < 2^63.1.
+// Cooley-Tukey (Harvey) with the estimated quotient, so WY lies in [0, 4q):
+// X, Y in [0, 8q) -> X + WY, X - WY in [0, 8q) (X corrected below 4q; primes below 2^61).
+// LAZY (primes below 2^57): no correction of X, values grow by less than 4q per stage: the
+// 16 stages of an N = 2^16 forward transform from [0, 2q) stay below 66q < 2^63.1.
 template <bool LAZY = false>
 __device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
-    if (LAZY) {
-        const u64 T = Y * W.x - mulhi_est(Y, W.y) * q;
-        Y = X - T + 2 * q2;
-        X = X + T;
-        return;
-    }
-    if (X >= q2) X -= q2;
-    const u64 T = shoup_nq(Y, W, 0 - q);
-    Y = X - T + q2;
+    const u64 q4 = 2 * q2;
+    if (!LAZY && X >= q4) X -= q4;
+    const u64 T = Y * W.x - mulhi_est(Y, W.y) * q;
+    Y = X - T + q4;
     X = X + T;
 }
-// Gentleman-Sande: X, Y in [0, 2q) -> X + Y, (X - Y) W in [0, 2q)
+// Gentleman-Sande: X, Y in [0, 4q) -> X + Y, (X - Y) W in [0, 4q) (primes below 2^61: sums
+// and differences below 8q; the product with the estimated quotient lies in [0, 4q))
 __device__ __forceinline__ void gs_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
+    const u64 q4 = 2 * q2;
     u64 S = X + Y;
-    if (S >= q2) S -= q2;
-    const u64 D = X - Y + q2;
+    if (S >= q4) S -= q4;
+    const u64 D = X - Y + q4;
     X = S;
-    Y = shoup_nq(D, W, 0 - q);
+    Y = D * W.x - mulhi_est(D, W.y) * q;
 }
 __device__ __forceinline__ u64 canon4(u64 v, u64 q, u64 q2) {
     if (v >= q2) v -= q2;
     if (v >= q) v -= q;
     return v;
+}
+__device__ __forceinline__ u64 canon8(u64 v, u64 q, u64 q2) {
+    if (v >= 2 * q2) v -= 2 * q2;
+    return canon4(v, q, q2);
 }
 
 // ---- N = 2^16 in one launch: an 8-CTA cluster per limb ------------------------------------
@@ -101,8 +103,8 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
                 ct_bfly<LAZY>(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
             } else if (s == 0) {  // last inverse stage: N^-1 folded into both outputs
                 u64 S = x[e] + x[e | (1 << lb)];
-                if (S >= q2) S -= q2;
-                const u64 D = x[e] - x[e | (1 << lb)] + q2;
+                if (S >= 2 * q2) S -= 2 * q2;
+                const u64 D = x[e] - x[e | (1 << lb)] + 2 * q2;
                 x[e] = mul_shoup_lazy(S, NI.x, NI.y, q);
                 x[e | (1 << lb)] = mul_shoup_lazy(D, NI1.x, NI1.y, q);
             } else {
@@ -167,7 +169,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(512, MINB)
         for (int e = 0; e < 16; e++) x[e] = sm[((w << 4) | e) * ST + lane];
         ntt16_round<false, 0, 8>(x, w << 4, r, tw, q, q2, NI, NI1);
 #pragma unroll
-        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * ST + lane] = canon4(x[e], q, q2);
+        for (int e = 0; e < 16; e++) sm[((w << 4) | e) * ST + lane] = canon8(x[e], q, q2);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 16; k++) {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
         } else {
             ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
 #pragma unroll
-            for (int e = 0; e < 16; e++) my[w * 17 + e] = canon4(x[e], q, q2);
+            for (int e = 0; e < 16; e++) my[w * 17 + e] = canon8(x[e], q, q2);
         }
         __syncthreads();
 #pragma unroll

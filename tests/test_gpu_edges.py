@@ -34,17 +34,21 @@ def test_transform_extreme_inputs(gpu, logn, bits):
         for r, q in enumerate(primes):
             x[0, r, :] = q - 1                        # every coefficient at its maximum
             x[1, r, :] = np.where(np.arange(n) % 2 == 0, 0, q - 1)
-        t = torch.from_numpy(x.view(np.int64).copy()).cuda()
-        gpu.pft_ntt(p.ctx, t.data_ptr(), 3, len(primes), 0)
-        y = t.cpu().numpy().view(np.uint64)
         idx = np.arange(n) if logn <= 11 else np.r_[0:32, n // 2 - 16:n // 2 + 16, n - 32:n]
-        for poly in range(3):
-            for r, q in enumerate(primes):
-                assert np.all(y[poly, r] < q), (poly, r)
-                want = OC.eval_at(x[poly, r], OP.root_2n(q, logn), q, logn, idx)
-                assert np.array_equal(y[poly, r][idx], want), (logn, bits, poly, r)
-        gpu.pft_ntt(p.ctx, t.data_ptr(), 3, len(primes), 1)
-        assert np.array_equal(t.cpu().numpy().view(np.uint64), x)
+        want = [[OC.eval_at(x[poly, r], OP.root_2n(q, logn), q, logn, idx) for r, q in enumerate(primes)]
+                for poly in range(3)]
+        for variant in range(4) if logn == 16 else [None]:  # every N = 2^16 kernel variant
+            if variant is not None:
+                gpu.pft_set_transform_variant(p.ctx, variant)
+            t = torch.from_numpy(x.view(np.int64).copy()).cuda()
+            gpu.pft_ntt(p.ctx, t.data_ptr(), 3, len(primes), 0)
+            y = t.cpu().numpy().view(np.uint64)
+            for poly in range(3):
+                for r, q in enumerate(primes):
+                    assert np.all(y[poly, r] < q), (variant, poly, r)
+                    assert np.array_equal(y[poly, r][idx], want[poly][r]), (logn, bits, variant, poly, r)
+            gpu.pft_ntt(p.ctx, t.data_ptr(), 3, len(primes), 1)
+            assert np.array_equal(t.cpu().numpy().view(np.uint64), x), variant
     finally:
         p.close()
 
