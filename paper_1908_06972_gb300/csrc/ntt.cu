@@ -39,7 +39,7 @@ __device__ __forceinline__ u64 shoup_nq(u64 x, ulonglong2 W, u64 nq) { return x 
 __device__ __forceinline__ u64 mulhi_est(u64 x, u64 w) {
     const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
     const uint32_t wl = (uint32_t)w, wh = (uint32_t)(w >> 32);
-    return (u64)xh * wh + __umulhi(xh, wl) + __umulhi(xl, wh);
+    return (u64)xh * wh + ((u64)__umulhi(xh, wl) + __umulhi(xl, wh));
 }
 // Cooley-Tukey (Harvey) with the estimated quotient, so WY lies in [0, 4q):
 // X, Y in [0, 8q) -> X + WY, X - WY in [0, 8q) (X corrected below 4q; primes below 2^61).
@@ -49,7 +49,7 @@ template <bool LAZY = false>
 __device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
     const u64 q4 = 2 * q2;
     if (!LAZY && X >= q4) X -= q4;
-    const u64 T = Y * W.x - mulhi_est(Y, W.y) * q;
+    const u64 T = Y * W.x + mulhi_est(Y, W.y) * (0 - q);
     Y = X - T + q4;
     X = X + T;
 }
@@ -61,7 +61,7 @@ __device__ __forceinline__ void gs_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64
     if (S >= q4) S -= q4;
     const u64 D = X - Y + q4;
     X = S;
-    Y = D * W.x - mulhi_est(D, W.y) * q;
+    Y = D * W.x + mulhi_est(D, W.y) * (0 - q);
 }
 __device__ __forceinline__ u64 canon4(u64 v, u64 q, u64 q2) {
     if (v >= q2) v -= q2;
