@@ -60,6 +60,18 @@ __device__ __forceinline__ void acc3_mac(Acc3& A, u32 a0, u32 a1, u32 b0, u32 b1
     A.s01 += (u64)a1 * b0;
     A.s11 += (u64)a1 * b1;
 }
+// Karatsuba form for at most 4 terms: S00 = sum a0 b0, S11 = sum a1 b1 and
+// SM = sum (a0 + a1)(b0 + b1) (each factor below 2^31, so 4 terms stay below 2^64);
+// the middle sum is SM - S00 - S11.  Three products per term instead of four.
+struct Acc3K {
+    u64 s00, sm, s11;
+};
+__device__ __forceinline__ void acc3k_mac(Acc3K& A, u32 a0, u32 a1, u32 a01, u32 b0, u32 b1, u32 b01) {
+    A.s00 += (u64)a0 * b0;
+    A.s11 += (u64)a1 * b1;
+    A.sm += (u64)a01 * b01;
+}
+__device__ __forceinline__ Acc3 acc3k_fold(const Acc3K& A) { return Acc3{A.s00, A.sm - A.s00 - A.s11, A.s11}; }
 // the 128-bit value S00 + 2^30 S01 + 2^60 S11
 __device__ __forceinline__ U128 acc3_value(const Acc3& A) {
     U128 r;

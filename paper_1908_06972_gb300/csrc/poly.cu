@@ -373,18 +373,43 @@ __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
         Acc3 a[TP], b[TP];
         const uint2* cp[TP];
 #pragma unroll
-        for (int u = 0; u < TP; u++) {
-            a[u] = {0, 0, 0};
-            b[u] = {0, 0, 0};
-            cp[u] = sT + (m0 + u < nt ? m0 + u : m0) * NS;
-        }
-#pragma unroll
-        for (int i = 0; i < NS; i++) {
+        for (int u = 0; u < TP; u++) cp[u] = sT + (m0 + u < nt ? m0 + u : m0) * NS;
+        if constexpr (NS <= 4) {  // Karatsuba: three products per term
+            Acc3K ka[TP], kb[TP];
 #pragma unroll
             for (int u = 0; u < TP; u++) {
-                const uint2 c = cp[u][i];
-                acc3_mac(a[u], ya0[i], ya1[i], c.x, c.y);
-                acc3_mac(b[u], yb0[i], yb1[i], c.x, c.y);
+                ka[u] = {0, 0, 0};
+                kb[u] = {0, 0, 0};
+            }
+#pragma unroll
+            for (int i = 0; i < NS; i++) {
+#pragma unroll
+                for (int u = 0; u < TP; u++) {
+                    const uint2 c = cp[u][i];
+                    const u32 c01 = c.x + c.y;
+                    acc3k_mac(ka[u], ya0[i], ya1[i], ya0[i] + ya1[i], c.x, c.y, c01);
+                    acc3k_mac(kb[u], yb0[i], yb1[i], yb0[i] + yb1[i], c.x, c.y, c01);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TP; u++) {
+                a[u] = acc3k_fold(ka[u]);
+                b[u] = acc3k_fold(kb[u]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < TP; u++) {
+                a[u] = {0, 0, 0};
+                b[u] = {0, 0, 0};
+            }
+#pragma unroll
+            for (int i = 0; i < NS; i++) {
+#pragma unroll
+                for (int u = 0; u < TP; u++) {
+                    const uint2 c = cp[u][i];
+                    acc3_mac(a[u], ya0[i], ya1[i], c.x, c.y);
+                    acc3_mac(b[u], yb0[i], yb1[i], c.x, c.y);
+                }
             }
         }
         // constants are c 2^64 mod t, so a Montgomery reduction of the sum (< t 2^63) gives
