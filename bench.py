@@ -45,7 +45,7 @@ SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 10
 # DRAM bytes (read + written) per limb and pass of the N = 2^16 transform kernels: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum over the four two-pass launches of the
 # 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes.
-NTT_DRAM_BYTES_PER_LIMB_PASS = 1.0067e6
+NTT_DRAM_BYTES_PER_LIMB_PASS = 1.0121e6
 
 
 def levels():
