@@ -272,6 +272,42 @@ KeyRef keyref(pft_ctx* c, u32 key_id) {
     return r;
 }
 
+// conv <- NTT(conv), then out = (x + c - conv) s (+ acc; entries of acc with a null pointer, or
+// an empty acc: none), with per-limb constants {c, s, s'}: one fused pass where the transform
+// variant has it, else the transform and the elementwise epilogue.
+static void ntt_fwd_sub_scale(pft_ctx* c, const std::vector<PolyRef>& conv, const std::vector<PolyRef>& x,
+                              const std::vector<PolyRef>& acc, const std::vector<PolyRef>& out, const u64* consts) {
+    std::vector<PolyRef> a = acc;
+    if (a.empty())
+        for (const PolyRef& r : x) a.push_back(ref(nullptr, r.nlimbs));
+    bool fused = true;
+    chunks(conv.size(), [&](size_t lo, size_t hi) {
+        NttEpi e;
+        e.x = mkset(x, lo, hi);
+        e.acc = mkset(a, lo, hi);
+        e.out = mkset(out, lo, hi);
+        e.consts = consts;
+        if (fused) fused = ntt_forward_epilogue(c->tabs, mkset(conv, lo, hi), e, c->stream);
+    });
+    if (fused) return;
+    ntt_fwd(c, conv, conv);
+    std::vector<PolyRef> xw, yw, aw, ow, xn, yn, on;
+    for (size_t i = 0; i < conv.size(); i++) {
+        if (a[i].ptr) {
+            xw.push_back(x[i]);
+            yw.push_back(conv[i]);
+            aw.push_back(a[i]);
+            ow.push_back(out[i]);
+        } else {
+            xn.push_back(x[i]);
+            yn.push_back(conv[i]);
+            on.push_back(out[i]);
+        }
+    }
+    if (!ow.empty()) subscale(c, xw, &yw, &aw, ow, consts);
+    if (!on.empty()) subscale(c, xn, &yn, nullptr, on, consts);
+}
+
 void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
     const KeyRef key = keyref(c, key_id);
     const int L = c->L, k = c->k, alpha = c->alpha;
@@ -358,13 +394,12 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
     }
     // 5. ModDown: coefficient form of the special rows, conversion to q_0..q_{l-1}, evaluation form
     {
-        std::vector<PolyRef> sp, cvr;
+        std::vector<PolyRef> sp;
         std::vector<BconvJob> jobs;
         for (size_t b = 0; b < B; b++) {
             const int l = io[b].l;
             for (int pol = 0; pol < 2; pol++) {
                 sp.push_back(ref(uu(b, pol) + (size_t)l * limb, k, 0, 0, L));
-                cvr.push_back(ref(cv(b, pol), l));
                 BconvJob J;
                 J.src = uu(b, pol) + (size_t)l * limb;
                 J.dst = cv(b, pol);
@@ -382,32 +417,27 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
         }
         ntt_inv(c, sp, sp);
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
-        ntt_fwd(c, cvr, cvr);
     }
-    // 6. out = acc + (u_Q - conv) P^-1
-    {
-        std::vector<PolyRef> x, y, acc, out, x1, y1, out1, acc1;
-        bool all0 = true, all1 = true, none1 = true;
-        for (size_t b = 0; b < B; b++) {
-            all0 &= io[b].acc0 != nullptr;
-            all1 &= io[b].acc1 != nullptr;
-            none1 &= io[b].acc1 == nullptr;
-        }
-        NEED(all0 && (all1 || none1), PFT_ERR_ARG, "internal: mixed accumulators");
-        for (size_t b = 0; b < B; b++) {
-            const int l = io[b].l;
-            x.push_back(ref(uu(b, 0), l));
-            y.push_back(ref(cv(b, 0), l));
-            acc.push_back(ref((u64*)io[b].acc0, l));
-            out.push_back(ref(io[b].out0, l));
-            x1.push_back(ref(uu(b, 1), l));
-            y1.push_back(ref(cv(b, 1), l));
-            if (io[b].acc1) acc1.push_back(ref((u64*)io[b].acc1, l));
-            out1.push_back(ref(io[b].out1, l));
-        }
-        subscale(c, x, &y, &acc, out, c->moddown_consts);
-        subscale(c, x1, &y1, all1 ? &acc1 : nullptr, out1, c->moddown_consts);
+    // 6. out = acc + (u_Q - conv) P^-1, fused with the last forward pass of conv where the
+    // transform variant has that kernel
+    bool all0 = true, all1 = true, none1 = true;
+    for (size_t b = 0; b < B; b++) {
+        all0 &= io[b].acc0 != nullptr;
+        all1 &= io[b].acc1 != nullptr;
+        none1 &= io[b].acc1 == nullptr;
     }
+    NEED(all0 && (all1 || none1), PFT_ERR_ARG, "internal: mixed accumulators");
+    std::vector<PolyRef> cvr, ex, eacc, eout;
+    for (size_t b = 0; b < B; b++) {
+        const int l = io[b].l;
+        for (int pol = 0; pol < 2; pol++) {
+            cvr.push_back(ref(cv(b, pol), l));
+            ex.push_back(ref(uu(b, pol), l));
+            eacc.push_back(ref((u64*)(pol ? io[b].acc1 : io[b].acc0), l));
+            eout.push_back(ref(pol ? io[b].out1 : io[b].out0, l));
+        }
+    }
+    ntt_fwd_sub_scale(c, cvr, ex, eacc, eout, c->moddown_consts);
 }
 
 // ---- operations ---------------------------------------------------------------------------
@@ -683,12 +713,10 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
         }
         ntt_inv(c, sp, sp);
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
-        ntt_fwd(c, cvr, cvr);
-        std::vector<PolyRef> x0{ref(U.u(), l)}, y0{ref(Cv.u(), l)}, a0{ref(A0.u(), l)}, o0{ref(o->data, l)};
-        std::vector<PolyRef> x1{ref(U.u() + (size_t)E * limb, l)}, y1{ref(Cv.u() + (size_t)l * limb, l)},
-            o1{ref(o->data + (size_t)l * limb, l)};
-        subscale(c, x0, &y0, &a0, o0, c->moddown_consts);
-        subscale(c, x1, &y1, nullptr, o1, c->moddown_consts);
+        const std::vector<PolyRef> xs{ref(U.u(), l), ref(U.u() + (size_t)E * limb, l)};
+        const std::vector<PolyRef> as{ref(A0.u(), l), ref(nullptr, l)};
+        const std::vector<PolyRef> os{ref(o->data, l), ref(o->data + (size_t)l * limb, l)};
+        ntt_fwd_sub_scale(c, cvr, xs, as, os, c->moddown_consts);
     }
 }
 
@@ -720,8 +748,7 @@ void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* 
         }
         ntt_inv(c, lin, lout);
         chunks(rr.size(), [&](size_t p, size_t q) { rescale_bcast(c->tabs, mkset(lout, p, q), mkset(rr, p, q), c->stream); });
-        ntt_fwd(c, rr, rr);
-        subscale(c, x, &rr, nullptr, out_refs, c->rescale_consts[l - 1]);
+        ntt_fwd_sub_scale(c, rr, x, {}, out_refs, c->rescale_consts[l - 1]);
         for (size_t i = 0; i < G; i++) {
             pft_ct* o = out[idx[i]];
             const double sc = a[idx[i]]->scale / (double)c->primes[l - 1];

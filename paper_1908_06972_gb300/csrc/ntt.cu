@@ -278,6 +278,47 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet
     }
 }
 
+// Forward stages 8..15 of the 16 rows of this CTA (limb `limb` of prime pi, rows read from
+// src): canonical results are left in sm, row c2 point m at c2 * kRowStride + m + (m >> 4),
+// after a barrier.
+__device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* __restrict__ src, int pi, u64* sm) {
+    const int logn = t.logn;
+    const int w = threadIdx.x & 15, cc = threadIdx.x >> 4;
+    const int u = blockIdx.x * 16 + cc;
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 q2 = 2 * q;
+    const ulonglong2* tw = t.fwd + ((size_t)pi << logn);
+    const ulonglong2 NI = make_ulonglong2(0, 0);
+    u64* my = sm + cc * kRowStride;
+    u64 x[16];
+    const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
+#pragma unroll
+    for (int e = 0; e < 16; e++) x[e] = src[((size_t)u << 8) | (e << 4) | w];
+    if (lazy) ntt16_round<false, 4, 8, true>(x, w, u, tw, q, q2, NI, NI);
+    else ntt16_round<false, 4, 8>(x, w, u, tw, q, q2, NI, NI);
+#pragma unroll
+    for (int e = 0; e < 16; e++) my[e * 17 + w] = x[e];  // point e*16 + w
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
+    if (lazy) {
+        ntt16_round<false, 0, 8, true>(x, w << 4, u, tw, q, q2, NI, NI);
+        // values below 66q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
+        // (mu = floor(2^(64+s) / q)), then one correction
+        const u64 one_p = __ldg(&t.primes[pi].mu) >> __ldg(&t.primes[pi].s);
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            u64 r = x[e] - mulhi(x[e], one_p) * q;
+            my[w * 17 + e] = r >= q ? r - q : r;
+        }
+    } else {
+        ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI);
+#pragma unroll
+        for (int e = 0; e < 16; e++) my[w * 17 + e] = canon8(x[e], q, q2);
+    }
+    __syncthreads();
+}
+
 template <bool INV, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet in, PolySet out, int is_final) {
     __shared__ u64 sm[16 * kRowStride];
@@ -286,69 +327,73 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     if (limb >= Ro.nlimbs) return;
     const int logn = t.logn;
     const int pi = prime_of(Ro, limb);
-    const int w = threadIdx.x & 15, cc = threadIdx.x >> 4;
-    const int u = blockIdx.x * 16 + cc;
     const u64* src = in.p[poly].ptr + ((size_t)limb << logn);
     u64* dst = Ro.ptr + ((size_t)limb << logn);
-    const u64 q = __ldg(&t.primes[pi].q);
-    const u64 q2 = 2 * q;
-    const ulonglong2* tw = (INV ? t.inv : t.fwd) + ((size_t)pi << logn);
-    const ulonglong2 NI = INV ? __ldg(&t.ninv[pi]) : make_ulonglong2(0, 0);
-    const ulonglong2 NI1 = INV ? __ldg(&t.inv1ninv[pi]) : make_ulonglong2(0, 0);
-    u64* my = sm + cc * kRowStride;
-    u64 x[16];
     if (!INV) {
-        const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
-#pragma unroll
-        for (int e = 0; e < 16; e++) x[e] = src[((size_t)u << 8) | (e << 4) | w];
-        if (lazy) ntt16_round<false, 4, 8, true>(x, w, u, tw, q, q2, NI, NI1);
-        else ntt16_round<false, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
-#pragma unroll
-        for (int e = 0; e < 16; e++) my[e * 17 + w] = x[e];  // point e*16 + w
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
-        if (lazy) {
-            ntt16_round<false, 0, 8, true>(x, w << 4, u, tw, q, q2, NI, NI1);
-            // values below 66q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
-            // (mu = floor(2^(64+s) / q)), then one correction
-            const u64 one_p = __ldg(&t.primes[pi].mu) >> __ldg(&t.primes[pi].s);
-#pragma unroll
-            for (int e = 0; e < 16; e++) {
-                u64 r = x[e] - mulhi(x[e], one_p) * q;
-                my[w * 17 + e] = r >= q ? r - q : r;
-            }
-        } else {
-            ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
-#pragma unroll
-            for (int e = 0; e < 16; e++) my[w * 17 + e] = canon8(x[e], q, q2);
-        }
-        __syncthreads();
+        contig_fwd_rows(t, src, pi, sm);
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             const int f = threadIdx.x + 256 * k;
             const int c2 = f >> 8, m = f & 255;
             dst[((size_t)(blockIdx.x * 16 + c2) << 8) | m] = sm[c2 * kRowStride + m + (m >> 4)];
         }
-    } else {
+        return;
+    }
+    const int w = threadIdx.x & 15, cc = threadIdx.x >> 4;
+    const int u = blockIdx.x * 16 + cc;
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 q2 = 2 * q;
+    const ulonglong2* tw = t.inv + ((size_t)pi << logn);
+    const ulonglong2 NI = __ldg(&t.ninv[pi]);
+    const ulonglong2 NI1 = __ldg(&t.inv1ninv[pi]);
+    u64* my = sm + cc * kRowStride;
+    u64 x[16];
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-            const int f = threadIdx.x + 256 * k;
-            const int c2 = f >> 8, m = f & 255;
-            sm[c2 * kRowStride + m + (m >> 4)] = src[((size_t)(blockIdx.x * 16 + c2) << 8) | m];
-        }
-        __syncthreads();
+    for (int k = 0; k < 16; k++) {
+        const int f = threadIdx.x + 256 * k;
+        const int c2 = f >> 8, m = f & 255;
+        sm[c2 * kRowStride + m + (m >> 4)] = src[((size_t)(blockIdx.x * 16 + c2) << 8) | m];
+    }
+    __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
-        ntt16_round<true, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
+    for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
+    ntt16_round<true, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
 #pragma unroll
-        for (int e = 0; e < 16; e++) my[w * 17 + e] = x[e];
-        __syncthreads();
+    for (int e = 0; e < 16; e++) my[w * 17 + e] = x[e];
+    __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 16; e++) x[e] = my[e * 17 + w];  // point e*16 + w
-        ntt16_round<true, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
+    for (int e = 0; e < 16; e++) x[e] = my[e * 17 + w];  // point e*16 + w
+    ntt16_round<true, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
 #pragma unroll
-        for (int e = 0; e < 16; e++) dst[((size_t)u << 8) | (e << 4) | w] = is_final ? canon4(x[e], q, q2) : x[e];
+    for (int e = 0; e < 16; e++) dst[((size_t)u << 8) | (e << 4) | w] = is_final ? canon4(x[e], q, q2) : x[e];
+}
+
+// Forward stages 8..15 fused with the ModDown epilogue: for the canonical transform value v,
+// out = (x + c - v) s mod q (+ acc when the polynomial has one), with per-limb constants
+// {c, s, s'} (Shoup) at consts[3 limb].  The rows of `in` hold the output of stages 0..7.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, PolySet in, NttEpi e) {
+    __shared__ u64 sm[16 * kRowStride];
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ri = in.p[poly];
+    if (limb >= Ri.nlimbs) return;
+    const int logn = t.logn;
+    const int pi = prime_of(Ri, limb);
+    const size_t base = (size_t)limb << logn;
+    contig_fwd_rows(t, Ri.ptr + base, pi, sm);
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 c = __ldg(&e.consts[3 * limb]), s = __ldg(&e.consts[3 * limb + 1]), sp = __ldg(&e.consts[3 * limb + 2]);
+    const u64* __restrict__ xs = e.x.p[poly].ptr + base;
+    const u64* __restrict__ as = e.acc.p[poly].ptr;  // null: no accumulator for this polynomial
+    u64* __restrict__ os = e.out.p[poly].ptr + base;
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        const int f = threadIdx.x + 256 * k;
+        const int c2 = f >> 8, m = f & 255;
+        const size_t j = ((size_t)(blockIdx.x * 16 + c2) << 8) | m;
+        u64 r = mul_shoup(submod(addmod(xs[j], c, q), sm[c2 * kRowStride + m + (m >> 4)], q), s, sp, q);
+        if (as) r = addmod(r, as[base + j], q);
+        os[j] = r;
     }
 }
 
@@ -386,6 +431,22 @@ static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const Po
                                  cudaStream_t st) {
     if (minb == 4) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
     else launch_ntt16_twopass_v<3>(t, in, out, inverse, st);
+}
+
+template <int MINB>
+static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {
+    dim3 grid(16, (unsigned)io.max_limbs, (unsigned)io.count);
+    const double work = set_limbs(io) * (double)(t.n / 2) * 8;
+    {
+        PFT_PROF("ntt.fwd.strided", st, work);
+        k_ntt8_strided<false, 8, MINB><<<grid, 256, 0, st>>>(t, io, io, 0);
+    }
+    PFT_LAUNCH_CHECK("ntt pass A");
+    {
+        PFT_PROF("ntt.fwd.contig", st, work);
+        k_ntt8_contig_epi<MINB><<<grid, 256, 0, st>>>(t, io, e);
+    }
+    PFT_LAUNCH_CHECK("ntt pass B + ModDown epilogue");
 }
 
 template <bool INV, int MINB>
@@ -645,6 +706,15 @@ static void run(const DevTables& t, const PolySet& in, const PolySet& out, bool 
 
 void ntt_forward(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
     run(t, in, out, false, st);
+}
+bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {
+    if (io.count == 0) return true;
+    if (t.logn != 16) return false;
+    const int v16 = ntt16_variant(t);
+    if (v16 != 0 && v16 != 1) return false;
+    if (v16 == 1) launch_ntt16_epi_v<4>(t, io, e, st);
+    else launch_ntt16_epi_v<3>(t, io, e, st);
+    return true;
 }
 void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
     run(t, in, out, true, st);

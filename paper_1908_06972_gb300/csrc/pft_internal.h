@@ -98,6 +98,15 @@ inline double set_limbs(const PolySet& s) {
 // Negacyclic transform of every limb of every polynomial of `out` (input from `in`,
 // which may be the same set).
 void ntt_forward(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
+// The ModDown epilogue applied by the last forward pass: out = (x + c - NTT(io)) s (+ acc; a null
+// acc pointer: none), per-limb constants {c, s, s'} at consts[3 limb].
+struct NttEpi {
+    PolySet x, acc, out;
+    const u64* consts;
+};
+// Forward transform of io (in place) fused with the epilogue; false (nothing launched) where
+// the ring or the transform variant has no fused kernel.
+bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st);
 void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
 
 enum class EwOp { Add, Sub, Mul, Neg, Copy };
