@@ -443,7 +443,8 @@ static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttE
     }
     PFT_LAUNCH_CHECK("ntt pass A");
     {
-        PFT_PROF("ntt.fwd.contig", st, work);
+        // named apart from the plain transform launches: it also moves the epilogue's operands
+        PFT_PROF("epi.ntt_moddown", st, work);
         k_ntt8_contig_epi<MINB><<<grid, 256, 0, st>>>(t, io, e);
     }
     PFT_LAUNCH_CHECK("ntt pass B + ModDown epilogue");
