@@ -39,9 +39,10 @@ SEED = (0x5EED0001, 0x5EED0002, 0x5EED0003, 0x5EED0004)
 WORKLOAD = ("N=2^16, 30 limbs (60 + 29x50 bits) + 4 special (60 bits), digits of 4 primes; "
             "batch 64 ciphertexts at levels U{5..30}; per ciphertext mul_relin then 16 chained "
             "rotations (2^0..2^14, -1)")
-# ALU roofline (derivation in the design doc): 152 SMs x 64 32-bit IMAD per SM per clock x 2.07 GHz,
-# at 10 IMAD per 64-bit Shoup butterfly multiply.
-SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 10
+# ALU roofline: 152 SMs x 64 32-bit IMAD per SM per clock x 2.07 GHz, at 9 IMAD per 64-bit
+# Shoup butterfly multiply with an estimated quotient (3 for the quotient, 3 for each of the
+# two low halves).
+SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 9
 # DRAM bytes (read + written) per limb and pass of the N = 2^16 transform kernels: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum over the four two-pass launches of the
 # 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes.
@@ -316,7 +317,8 @@ def run_gpu(args):
                                   "times the mean limb-passes per launch in the step",
                 "launches": k_launches, "kernel_ms": round(k_ms, 3),
                 "kernel_share_of_step": round(k_ms / ms, 4),
-                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 10 IMAD per Shoup mulmod"}
+                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 9 IMAD per Shoup mulmod "
+                               "(estimated quotient)"}
     elif k_ms > 0:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
