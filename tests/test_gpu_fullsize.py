@@ -198,3 +198,70 @@ def test_training_step_full_size_vs_fp64(gpu):
         for h in handles:
             pf.pft_ct_destroy(h)
         pf.pft_ctx_destroy(ctx)
+
+
+def test_rotation_light_training_step_full_size_vs_fp64(gpu):
+    """The diagonal-layout step at the same sizes, documents lifted by 2^10 (mask at 2^30):
+    decrypted diagonals of dH, dO in the layout of P and the updated weights within 2^-20 of
+    FP64; the model ends at levels L - 7 (diagonals) and L - 8 (P)."""
+    from oracle import fasttext as OF
+
+    pf = gpu
+    L, m, n, c, B, eta, sc, lift = 30, 8192, 32, 4, 4, 0.25, 2.0 ** 40, 10
+    ctx = pf.pft_ctx_create(16, L, 4, 4, 60, 40, 60, sc, (0x7A12, 1, 2, 3))
+    t = 1 << 15
+    handles = []
+
+    def enc(z, level, scale, nonce):
+        pt = pf.pft_encode(ctx, z, scale, level)
+        h = pf.pft_encrypt(ctx, pt, pf.PFT_ENC_SK, nonce)
+        pf.pft_pt_destroy(pt)
+        handles.append(h)
+        return h
+
+    def dec(h, k):
+        pt = pf.pft_decrypt(ctx, h)
+        z = pf.pft_decode(ctx, pt, k).real
+        pf.pft_pt_destroy(pt)
+        return z
+
+    mask = None
+    try:
+        pf.pft_keygen(ctx, [1 << i for i in range(15)] + [k for k in range(3, n) if k & (k - 1)]
+                      + [-(1 << s) for s in range(5)], True)
+        H, O = synth.fasttext_weights(54, m, n, c)
+        V = np.zeros((B, t))
+        V[:, :m] = synth.documents(55, m, B)
+        Y = np.eye(c)[np.random.default_rng(56).integers(0, c, B)]
+        D, P, Mv = OF.train_pack_diag(np.vstack([H, np.zeros((t - m, n))]), O, t)
+        mask = pf.pft_encode(ctx, Mv, sc / 2.0 ** lift, L)
+        model = pf.pft_ft_enc_model_create_diag(ctx, [enc(D[k], L, sc, 10 + k) for k in range(n)],
+                                                enc(P, L - 1, sc, 100), mask, m, n, c, lift)
+        try:
+            dl, ll, ls = pf.pft_fasttext_train_spec(ctx, model, sc)
+            docs = [enc(V[b], dl, sc, 200 + b) for b in range(B)]
+            labels = [enc(OF.train_label_diag(Y[b], n, t), ll, ls, 300 + b) for b in range(B)]
+            gD = [pf.pft_ct_create(ctx) for _ in range(n)]
+            gP = [pf.pft_ct_create(ctx)]
+            handles.extend(gD + gP)
+            pf.pft_fasttext_train_step(ctx, model, docs, labels, eta, gD, gP)
+            ref_H, ref_O = OF.train_grads_plain(V[:, :m], Y, H, O)
+            ref_D, ref_P, _ = OF.train_pack_diag(np.vstack([ref_H, np.zeros((t - m, n))]), ref_O, t)
+            for k in range(n):
+                assert np.max(np.abs(dec(gD[k], t) - ref_D[k])) < 2.0 ** -20, k
+            assert np.max(np.abs(dec(gP[0], n * c) - ref_P[:n * c])) < 2.0 ** -20
+            assert pf.pft_ft_enc_model_levels(model) == (L - 7, L - 8)
+            for which, j, want in ((0, 0, D[0] - eta * ref_D[0]), (0, n - 1, D[n - 1] - eta * ref_D[n - 1]),
+                                   (1, 0, (P - eta * ref_P)[:n * c])):
+                w = pf.pft_ct_create(ctx)
+                handles.append(w)
+                pf.pft_ft_enc_model_get(ctx, model, which, j, w)
+                assert np.max(np.abs(dec(w, want.size) - want)) < 2.0 ** -20, (which, j)
+        finally:
+            pf.pft_ft_enc_model_destroy(model)
+    finally:
+        if mask is not None:
+            pf.pft_pt_destroy(mask)
+        for h in handles:
+            pf.pft_ct_destroy(h)
+        pf.pft_ctx_destroy(ctx)
