@@ -242,6 +242,39 @@ int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
 int pft_device_status(pft_ctx* ctx);
 int pft_wait_selftest(pft_ctx* ctx, long long polls);
 
+/* ---- persistent job queue (batching over uneven levels and ring sizes) -----
+ * HADD, subtraction and HMULPLAIN (Sec. 2.3) for ciphertexts of any contexts (rings of
+ * different N and prime chains, one device) at any levels, executed by ONE persistent launch
+ * on ctx's stream: resident CTAs claim tiles (one chunk of 2048 coefficients of one limb of one
+ * polynomial) in list order from a device counter.
+ *   op        PFT_JOB_ADD / PFT_JOB_SUB: out = a +- b (same context, level and scale);
+ *             PFT_JOB_MUL_PLAIN: out = a (x) p slot-wise (p of a's context, level >= a's,
+ *             leading limbs; scale multiplies)
+ *   out       a handle of a's context (sized by the call; it may alias a or b)
+ *   after     index of an earlier job that must have finished before this one starts, or -1.
+ *             Every buffer a job shares with an earlier job (read after write, write after
+ *             read or write) must belong to that earlier job or to one reached through the
+ *             chain of `after` links; otherwise the call fails with PFT_ERR_ARG.
+ *   wait_flag device pointer to a 32-bit word, or NULL: the job also waits until
+ *             *wait_flag >= wait_value (written by another stream's kernel or copy).
+ * Both waits are bounded by wait_timeout_s (0 < t <= 10 s) of the device's global timer; when
+ * one expires the CTA skips that tile (its results are invalid), counts it as done so nothing
+ * waits forever, and raises the device flag that pft_device_status reports as PFT_ERR_TIMEOUT.
+ * Every job context must have ctx's current stream (pft_set_stream).  Asynchronous; an empty
+ * list does nothing. */
+enum { PFT_JOB_ADD = 0, PFT_JOB_SUB = 1, PFT_JOB_MUL_PLAIN = 2 };
+typedef struct {
+    int op;
+    const pft_ct* a;
+    const pft_ct* b;
+    const pft_pt* p;
+    pft_ct* out;
+    int after;
+    const uint32_t* wait_flag;
+    uint32_t wait_value;
+} pft_job;
+int pft_run_jobs(pft_ctx* ctx, const pft_job* jobs, int n_jobs, double wait_timeout_s);
+
 /* ---- level and scale management (used by the training step of Sec. 4.2) ---
  * The paper keeps every operand of a step at one level and scale; training mixes
  * operands of different depths, which these exact operations reconcile. */

@@ -55,6 +55,14 @@ class pft_server_done(Structure):
                 ("t_submit", c_double), ("t_done", c_double)]
 
 
+class pft_job(Structure):
+    _fields_ = [("op", c_int), ("a", c_void_p), ("b", c_void_p), ("p", c_void_p), ("out", c_void_p),
+                ("after", c_int), ("wait_flag", c_void_p), ("wait_value", ctypes.c_uint32)]
+
+
+PFT_JOB_ADD, PFT_JOB_SUB, PFT_JOB_MUL_PLAIN = 0, 1, 2
+
+
 class pft_server_stats(Structure):
     _fields_ = [("waiting", c_int), ("active", c_int), ("exporting", c_int), ("max_active", c_int),
                 ("completed", ctypes.c_long), ("iterations", ctypes.c_long), ("bytes_in_use", c_size_t),
@@ -101,6 +109,7 @@ def lib():
             "pft_dot_plain_batch": [vp, pp, pp, i, i, i, pp],
             "pft_drop_level": [vp, vp, i, vp], "pft_add_const": [vp, vp, d, vp],
             "pft_device_status": [vp], "pft_wait_selftest": [vp, ctypes.c_longlong],
+            "pft_run_jobs": [vp, POINTER(pft_job), i, c_double],
             "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
@@ -163,7 +172,8 @@ def exported_symbols():
             "pft_ct_set_scale", "pft_ft_enc_model_create", "pft_ft_enc_model_get", "pft_ft_enc_model_levels",
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
-            "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag"]
+            "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag",
+            "pft_run_jobs"]
 
 
 def _check(rc, ctx=None):
@@ -472,6 +482,18 @@ def pft_device_status(ctx):
 
 def pft_wait_selftest(ctx, polls):
     _check(lib().pft_wait_selftest(ctx, int(polls)), ctx)
+
+
+def pft_run_jobs(ctx, jobs, wait_timeout_s=1.0):
+    """One persistent launch over elementwise jobs of any contexts and levels.  Each job is a
+    dict: op (PFT_JOB_*), a, b or p, out, optional after (index or -1), wait_flag (device
+    address of a 32-bit word) and wait_value."""
+    arr = (pft_job * max(1, len(jobs)))()
+    for k, j in enumerate(jobs):
+        h = lambda x: None if x is None else (x.value if isinstance(x, c_void_p) else x)  # noqa: E731
+        arr[k] = pft_job(int(j["op"]), h(j["a"]), h(j.get("b")), h(j.get("p")), h(j["out"]), int(j.get("after", -1)),
+                         j.get("wait_flag"), int(j.get("wait_value", 0)))
+    _check(lib().pft_run_jobs(ctx, arr, len(jobs), float(wait_timeout_s)), ctx)
 
 
 def pft_drop_level(ctx, a, level, out):

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 SO = os.path.join(OUT, "libprivft.so")
-SOURCES = ["ntt.cu", "poly.cu", "ckks.cu", "serve.cu", "train.cu", "hostmath.cpp"]
+SOURCES = ["ntt.cu", "poly.cu", "ckks.cu", "serve.cu", "train.cu", "queue.cu", "hostmath.cpp"]
 HEADERS = ["pft_internal.h", "evaluator.h", "modarith.cuh", os.path.join("..", "..", "include", "privft.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

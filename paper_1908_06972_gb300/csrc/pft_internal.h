@@ -164,6 +164,26 @@ void ks_inner_multi(const DevTables& t, const KsDesc* descs_host, int B, const K
                     cudaStream_t st);
 // Whether a kernel's bounded wait has expired since the last reset (reads a device flag).
 int wait_timeout_flag(bool reset, cudaStream_t st);
+// Persistent job queue: elementwise jobs over ciphertexts of any rings and levels in one launch.
+// A job is cut into tiles (one chunk of one limb of one polynomial); resident CTAs claim tiles in
+// order from a counter.  A job starts only after job `after` (an earlier index, or -1) has
+// finished all its tiles and, when wait_flag is set, once *wait_flag >= wait_value; both waits
+// are bounded by timeout_ns of %globaltimer, after which the CTA raises the sticky timeout flag
+// (read by wait_timeout_flag), skips the tile and still counts it as done.
+enum QOp : int { kQAdd = 0, kQSub = 1, kQMulPlain = 2 };
+struct QJob {
+    const u64* a;          // [2][level][N]
+    const u64* b;          // [2][level][N] (add, sub) or [>= level][N] (plaintext)
+    u64* out;              // [2][level][N]
+    const DPrime* primes;  // the ring's prime table
+    const u32* wait_flag;  // device word or null
+    u32 wait_value;
+    int op, logn, level, after, ntiles;
+    long long tile0;       // first tile of the job in the queue's order
+};
+__host__ __device__ inline int queue_chunk(int logn) { return logn >= 11 ? 2048 : 1 << logn; }  // per tile
+void job_queue(const QJob* jobs_dev, int n_jobs, long long total_tiles, u64* counters_dev, long long timeout_ns,
+               double bytes, cudaStream_t st);
 // Launches a wait that cannot complete, bounded by `polls` polls (it raises the flag).
 void wait_selftest(long long polls, cudaStream_t st);
 // r = (last + h) mod p, h = floor(p/2), p = prime nlimbs(out); limb k of out = (r - h) mod q_k.

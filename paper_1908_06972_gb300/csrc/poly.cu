@@ -779,6 +779,108 @@ int wait_timeout_flag(bool reset, cudaStream_t st) {
     return v;
 }
 
+// ---- persistent job queue -------------------------------------------------------------------
+constexpr int kQThreads = 256;
+
+__device__ __forceinline__ u64 globaltimer() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ u32 load_acquire(const u32* p) {
+    u32 v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// true once *p >= target; false after timeout_ns of %globaltimer
+__device__ __forceinline__ bool wait_at_least(const u32* p, u32 target, long long timeout_ns) {
+    const u64 t0 = globaltimer();
+    for (;;) {
+        if (load_acquire(p) >= target) return true;
+        if ((long long)(globaltimer() - t0) > timeout_ns) return false;
+        __nanosleep(256);
+    }
+}
+
+// counters: [0] next tile (claimed with atomicAdd), [1 + j] tiles of job j finished
+__global__ void __launch_bounds__(kQThreads) k_job_queue(const QJob* __restrict__ jobs, int n_jobs,
+                                                          long long total_tiles, u64* counters, long long timeout_ns) {
+    __shared__ long long s_tile;
+    __shared__ int s_job, s_ok;
+    u32* done = reinterpret_cast<u32*>(counters + 1);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(counters), 1ull);
+        __syncthreads();
+        const long long tile = s_tile;
+        if (tile >= total_tiles) return;  // uniform over the CTA
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n_jobs - 1;  // the job holding this tile: last job with tile0 <= tile
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].tile0 <= tile) lo = mid;
+                else hi = mid - 1;
+            }
+            const QJob& J = jobs[lo];
+            bool ok = true;
+            if (J.after >= 0) ok = wait_at_least(&done[J.after], (u32)jobs[J.after].ntiles, timeout_ns);
+            if (ok && J.wait_flag) ok = wait_at_least(J.wait_flag, J.wait_value, timeout_ns);
+            if (!ok) atomicExch(&g_wait_timeout, 1);
+            s_job = lo;
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_ok) {
+            const QJob& J = jobs[s_job];
+            const int n = 1 << J.logn, chunk = queue_chunk(J.logn), cpl = n / chunk;
+            const long long tl = tile - J.tile0;
+            const int poly = (int)(tl / ((long long)J.level * cpl));
+            const int rem = (int)(tl % ((long long)J.level * cpl));
+            const int limb = rem / cpl, c0 = (rem % cpl) * chunk;
+            const DPrime P = load_prime(J.primes, limb);
+            const size_t off = ((size_t)poly * J.level + limb) * (size_t)n + c0;
+            const size_t offb = J.op == kQMulPlain ? (size_t)limb * n + c0 : off;
+            for (int x = 2 * threadIdx.x; x < chunk; x += 2 * kQThreads) {
+                const ulonglong2 va = *reinterpret_cast<const ulonglong2*>(J.a + off + x);
+                const ulonglong2 vb = *reinterpret_cast<const ulonglong2*>(J.b + offb + x);
+                ulonglong2 r;
+                if (J.op == kQAdd) {
+                    r.x = addmod(va.x, vb.x, P.q);
+                    r.y = addmod(va.y, vb.y, P.q);
+                } else if (J.op == kQSub) {
+                    r.x = submod(va.x, vb.x, P.q);
+                    r.y = submod(va.y, vb.y, P.q);
+                } else {
+                    r.x = mulmod(va.x, vb.x, P);
+                    r.y = mulmod(va.y, vb.y, P);
+                }
+                *reinterpret_cast<ulonglong2*>(J.out + off + x) = r;
+            }
+        }
+        __syncthreads();  // the tile's writes precede its completion count
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[s_job], 1u);
+        }
+    }
+}
+
+void job_queue(const QJob* jobs_dev, int n_jobs, long long total_tiles, u64* counters_dev, long long timeout_ns,
+               double bytes, cudaStream_t st) {
+    if (total_tiles == 0) return;
+    static int resident = 0;  // CTAs per SM x SMs: every CTA of the grid is resident at once
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        PFT_CUDA(cudaGetDevice(&dev));
+        PFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_job_queue, kQThreads, 0));
+        resident = std::max(1, sms * per_sm);
+    }
+    const int grid = (int)std::min<long long>(resident, total_tiles);
+    PFT_PROF("queue", st, bytes);
+    k_job_queue<<<grid, kQThreads, 0, st>>>(jobs_dev, n_jobs, total_tiles, counters_dev, timeout_ns);
+    PFT_LAUNCH_CHECK("job queue");
+}
+
 // Any number of digits: the key is re-read (or regenerated) for every input.
 __global__ void k_ks_inner_multi_generic(DevTables t, KsBatch bt, int B, KeyRef kr, int L, int k, int alpha) {
     const u64* key = kr.ptr;

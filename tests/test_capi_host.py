@@ -55,3 +55,24 @@ def test_no_cpu_fallback_when_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(pft, "_LIB", None)
     with pytest.raises(pft.NativeLibraryMissing):
         pft.lib()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's sizes and offsets."""
+    import ctypes
+
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "privft.h"\n'
+                   "int main(void) {\n"
+                   '  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pft_job), offsetof(pft_job, a),\n'
+                   "         offsetof(pft_job, b), offsetof(pft_job, p), offsetof(pft_job, out),\n"
+                   "         offsetof(pft_job, after), offsetof(pft_job, wait_flag), offsetof(pft_job, wait_value),\n"
+                   "         sizeof(pft_server_done));\n"
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    J = pft.pft_job
+    want = [ctypes.sizeof(J), J.a.offset, J.b.offset, J.p.offset, J.out.offset, J.after.offset, J.wait_flag.offset,
+            J.wait_value.offset, ctypes.sizeof(pft.pft_server_done)]
+    assert got == want
