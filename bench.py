@@ -336,6 +336,10 @@ def run_gpu(args):
     if args.train > 0:
         tr = train_measure(pft, torch, args.train, args.train_plain_docs, args.train_diag > 0)
 
+    qu = None
+    if args.queue > 0:
+        qu = queue_measure(pft, torch, args.queue)
+
     sv = None
     if args.serve > 0:
         sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_low_load,
@@ -359,7 +363,7 @@ def run_gpu(args):
            "gpu_launches": int(all_launches), "roofline": roof,
            "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
                         "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
-           "fasttext": ft, "serving": sv, "training": tr}
+           "fasttext": ft, "serving": sv, "training": tr, "job_queue": qu}
     if rank == 0:
         print(json.dumps(out))
     for h in A + B + C:
@@ -636,6 +640,85 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, 
     for c in ctxs:
         pft.pft_ctx_destroy(c)
     return out
+
+
+# ---- persistent job queue over two rings ------------------------------------------------------
+QU_WORKLOAD = ("64 ciphertexts at N=2^16 (60 + 29x50-bit chain, levels U{5..30}) and 64 at N=2^15 "
+               "(60 + 17x40-bit chain, levels U{12..18}): per ciphertext one HADD and one HMULPLAIN "
+               "(plaintext at the ciphertext's level), all in one list")
+
+
+def queue_measure(pft, torch, reps):
+    """One pft_run_jobs launch over both rings against the per-ring batched calls (one launch
+    per op and ring); GB/s of algorithmic bytes (HADD 48, HMULPLAIN 40 bytes per coefficient
+    and limb) against the measured HBM copy rate."""
+    from paper_1908_06972_gb300 import synth
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    rng = np.random.default_rng(77)
+    rings = [(16, 30, 4, 4, 60, 50, 60, rng.integers(5, 31, 64)), (15, 18, 2, 2, 60, 40, 60, rng.integers(12, 19, 64))]
+    ctxs, rows, handles, pts = [], [], [], []
+    for logn, L, k, alpha, f, m, sp, lv in rings:
+        ctx = pft.pft_ctx_create(logn, L, k, alpha, f, m, sp, 2.0 ** 40, (0x9E, logn, 1, 2))
+        pft.pft_keygen(ctx, [], False)  # the secret key only: nothing here switches keys
+        ctxs.append(ctx)
+        r = []
+        def enc(z, nonce, level):
+            pt = pft.pft_encode(ctx, z, 2.0 ** 40, level)
+            h = pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, nonce)
+            pft.pft_pt_destroy(pt)
+            return h
+
+        for i, l in enumerate(lv):
+            l = int(l)
+            x, y = enc(synth.slots(i, 64), 2 * i, l), enc(synth.slots(i + 500, 64), 2 * i + 1, l)
+            p = pft.pft_encode(ctx, synth.slots(i + 900, 64), 2.0 ** 20, l)
+            o1, o2 = pft.pft_ct_create(ctx), pft.pft_ct_create(ctx)
+            handles += [x, y, o1, o2]
+            pts.append(p)
+            r.append((x, y, p, o1, o2, l, 1 << logn))
+        rows.append(r)
+    jobs = []
+    nbytes = 0.0
+    for r in rows:
+        for x, y, p, o1, o2, l, n in r:
+            jobs.append(dict(op=pft.PFT_JOB_ADD, a=x, b=y, out=o1))
+            jobs.append(dict(op=pft.PFT_JOB_MUL_PLAIN, a=x, p=p, out=o2))
+            nbytes += (48 + 40) * l * n
+
+    def per_ring():
+        for ctx, r in zip(ctxs, rows):
+            pft.pft_add_batch(ctx, [e[0] for e in r], [e[1] for e in r], [e[3] for e in r])
+            pft.pft_mul_plain_batch(ctx, [e[0] for e in r], [e[2] for e in r], [e[4] for e in r])
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    t_q = timed(lambda: pft.pft_run_jobs(ctxs[0], jobs))
+    pft.pft_device_status(ctxs[0])
+    t_r = timed(per_ring)
+    for h in handles:
+        pft.pft_ct_destroy(h)
+    for p in pts:
+        pft.pft_pt_destroy(p)
+    for c in ctxs:
+        pft.pft_ctx_destroy(c)
+    gbs_q, gbs_r = nbytes / t_q / 1e9, nbytes / t_r / 1e9
+    return {"workload": QU_WORKLOAD, "jobs": len(jobs), "algorithmic_gb": round(nbytes / 1e9, 3),
+            "one_launch_ms": round(1e3 * t_q, 3), "per_ring_batched_ms": round(1e3 * t_r, 3),
+            "roofline": {"bound": "hbm", "kernel": "k_job_queue", "achieved": round(gbs_q, 1),
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs_q / peaks["hbm_gbs"], 4)},
+            "per_ring_gbs": round(gbs_r, 1)}
 
 
 # ---- encrypted minibatch training (Sec. 4.2, Algorithm 5) -----------------------------------------
@@ -1021,6 +1104,7 @@ def main():
     ap.add_argument("--train", type=int, default=64, help="documents per encrypted training step (0: skip)")
     ap.add_argument("--train-plain-docs", type=int, default=2, help="documents timed on the plain training path")
     ap.add_argument("--train-diag", type=int, default=1, help="also time the rotation-light training layout (0: skip)")
+    ap.add_argument("--queue", type=int, default=10, help="repetitions of the two-ring job-queue leg (0: skip)")
     ap.add_argument("--serve", type=int, default=48, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
     ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")
