@@ -400,6 +400,18 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, Poly
 template <int MINB>
 static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
                                    cudaStream_t st) {
+    if (MINB == 4) {  // four CTAs of 35 KB shared memory: a carveout that fits them, the rest L1
+        static bool attr_set = false;
+        if (!attr_set) {
+            const int co = 64;
+            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<false, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<false, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<true, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig_epi<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+            attr_set = true;
+        }
+    }
     dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);  // 256 sub-transforms / 16 per CTA
     const double work = set_limbs(out) * (double)(t.n / 2) * 8;
     if (!inverse) {
