@@ -149,6 +149,7 @@ def run_gpu(args):
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED,
                              flags=pft.PFT_COMPRESSED_KEYS if args.compressed_keys else 0)
     tuned, tune_us = pft.pft_autotune(ctx)
+    bfly_ceiling = pft.pft_bfly_ceiling(ctx) / 1e9  # G butterflies/s of the butterfly on register data
     pft.pft_keygen(ctx, STEPS_ROT, True)
     lv = levels()
     n = 1 << LOGN
@@ -318,7 +319,10 @@ def run_gpu(args):
                 "launches": k_launches, "kernel_ms": round(k_ms, 3),
                 "kernel_share_of_step": round(k_ms / ms, 4),
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 9 IMAD per Shoup mulmod "
-                               "(estimated quotient)"}
+                               "(estimated quotient)",
+                "arith_ceiling": round(bfly_ceiling, 1), "frac_of_arith_ceiling": round(achieved / bfly_ceiling, 4),
+                "arith_ceiling_source": "measured live: the transforms' butterfly on register data, no memory "
+                                        "traffic (pft_bfly_ceiling)"}
     elif k_ms > 0:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}

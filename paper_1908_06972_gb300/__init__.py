@@ -109,7 +109,7 @@ def lib():
             "pft_dot_plain_batch": [vp, pp, pp, i, i, i, pp],
             "pft_drop_level": [vp, vp, i, vp], "pft_add_const": [vp, vp, d, vp],
             "pft_device_status": [vp], "pft_wait_selftest": [vp, ctypes.c_longlong],
-            "pft_run_jobs": [vp, POINTER(pft_job), i, c_double],
+            "pft_run_jobs": [vp, POINTER(pft_job), i, c_double], "pft_bfly_ceiling": [vp, POINTER(c_double)],
             "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
@@ -173,7 +173,7 @@ def exported_symbols():
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
             "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag",
-            "pft_run_jobs"]
+            "pft_run_jobs", "pft_bfly_ceiling"]
 
 
 def _check(rc, ctx=None):
@@ -482,6 +482,13 @@ def pft_device_status(ctx):
 
 def pft_wait_selftest(ctx, polls):
     _check(lib().pft_wait_selftest(ctx, int(polls)), ctx)
+
+
+def pft_bfly_ceiling(ctx):
+    """Butterflies per second of the transforms' butterfly arithmetic on register data."""
+    v = c_double()
+    _check(lib().pft_bfly_ceiling(ctx, ctypes.byref(v)), ctx)
+    return v.value
 
 
 def pft_run_jobs(ctx, jobs, wait_timeout_s=1.0):

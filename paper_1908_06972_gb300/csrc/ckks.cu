@@ -1797,6 +1797,13 @@ int pft_device_status(pft_ctx* c) {
     });
 }
 
+int pft_bfly_ceiling(pft_ctx* c, double* out) {
+    return guard(c, [&] {
+        NEED(c && out, PFT_ERR_ARG, "bad arguments");
+        *out = bfly_ceiling(c->tabs, c->stream);
+    });
+}
+
 int pft_wait_selftest(pft_ctx* c, long long polls) {
     return guard(c, [&] {
         NEED(c && polls >= 1 && polls <= (1ll << 20), PFT_ERR_ARG, "polls must lie in 1..2^20");

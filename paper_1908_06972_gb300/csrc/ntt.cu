@@ -720,6 +720,55 @@ static void run(const DevTables& t, const PolySet& in, const PolySet& out, bool 
 void ntt_forward(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
     run(t, in, out, false, st);
 }
+// Register-only ceiling of the transform's butterfly: each thread runs `rounds` rounds of two
+// stages of 8 independent Cooley-Tukey butterflies (the ct_bfly of the transforms, twiddle in
+// registers, no memory traffic); one word is written only if the data take a value they cannot
+// reach, which keeps the work.
+__global__ void __launch_bounds__(256) k_bfly_ceiling(u64* sink, u64 q, ulonglong2 W, int rounds) {
+    u64 x[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = ((u64)threadIdx.x * 16 + i + blockIdx.x) % q;
+    const ulonglong2 Wt = make_ulonglong2(W.x, W.y);
+    const u64 q2 = 2 * q;
+    for (int k = 0; k < rounds; k++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) ct_bfly<false>(x[i], x[i + 8], Wt, q, q2);
+#pragma unroll
+        for (int i = 0; i < 8; i++) ct_bfly<false>(x[2 * i], x[2 * i + 1], Wt, q, q2);
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc ^= x[i];
+    if (acc == ~0ull) sink[0] = acc;  // values stay below 8q < 2^63
+}
+
+double bfly_ceiling(const DevTables& t, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    PFT_CUDA(cudaGetDevice(&dev));
+    PFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DPrime p0;
+    PFT_CUDA(cudaMemcpy(&p0, t.primes, sizeof(DPrime), cudaMemcpyDeviceToHost));
+    ulonglong2 W0;
+    PFT_CUDA(cudaMemcpy(&W0, t.fwd + 1, sizeof(W0), cudaMemcpyDeviceToHost));  // a twiddle of q_0
+    u64* sink = nullptr;
+    PFT_CUDA(cudaMalloc(&sink, 8));
+    cudaEvent_t a, b;
+    PFT_CUDA(cudaEventCreate(&a));
+    PFT_CUDA(cudaEventCreate(&b));
+    const int grid = sms * 4, rounds = 2000;
+    k_bfly_ceiling<<<grid, 256, 0, st>>>(sink, p0.q, W0, 16);  // warm-up
+    PFT_CUDA(cudaEventRecord(a, st));
+    k_bfly_ceiling<<<grid, 256, 0, st>>>(sink, p0.q, W0, rounds);
+    PFT_CUDA(cudaEventRecord(b, st));
+    PFT_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    PFT_CUDA(cudaEventElapsedTime(&ms, a, b));
+    PFT_CUDA(cudaEventDestroy(a));
+    PFT_CUDA(cudaEventDestroy(b));
+    PFT_CUDA(cudaFree(sink));
+    return (double)grid * 256 * rounds * 16 / (ms / 1e3);
+}
+
 bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {
     if (io.count == 0) return true;
     if (t.logn != 16) return false;

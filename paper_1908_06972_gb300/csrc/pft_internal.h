@@ -107,6 +107,9 @@ struct NttEpi {
 // Forward transform of io (in place) fused with the epilogue; false (nothing launched) where
 // the ring or the transform variant has no fused kernel.
 bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st);
+// Butterflies per second of the transform's (exact-path) butterfly arithmetic on register data
+// only: the arithmetic ceiling the transforms are measured against (synchronous).
+double bfly_ceiling(const DevTables& t, cudaStream_t st);
 void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
 
 enum class EwOp { Add, Sub, Mul, Neg, Copy };

@@ -100,3 +100,10 @@ def test_level_one_ciphertexts(pe):
     with pytest.raises(pf.PftError) as e:
         pf.pft_rescale(ctx, ga, out)
     assert e.value.code == pf.PFT_ERR_LEVEL_MISMATCH
+
+
+def test_butterfly_ceiling_is_below_the_derived_bound(pe):
+    """The register-only butterfly rate is positive and below 152 SMs x 64 32-bit multiplies per
+    clock x 2.07 GHz / 9 multiplies per butterfly."""
+    v = pe.pft.pft_bfly_ceiling(pe.ctx)
+    assert 1e10 < v < 152 * 64 * 2.07e9 / 9
