@@ -110,9 +110,12 @@ __device__ __forceinline__ u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a -
 // Montgomery reduction with R = 2^64: for x = hi 2^64 + lo < q 2^63, returns x 2^-64 mod q
 // in [0, q).  m = lo (-q^-1) makes lo + m q = 0 mod 2^64 (carry out iff lo != 0), and
 // (x + m q) / 2^64 < 1.5 q.
-__device__ __forceinline__ u64 mont_reduce(u64 hi, u64 lo, u64 q, u64 mneg) {
+__device__ __forceinline__ u64 mont_reduce_lazy(u64 hi, u64 lo, u64 q, u64 mneg) {  // in [0, 2q)
     const u64 m = lo * mneg;
-    u64 r = hi + mulhi(m, q) + (lo != 0 ? 1 : 0);
+    return hi + mulhi(m, q) + (lo != 0 ? 1 : 0);
+}
+__device__ __forceinline__ u64 mont_reduce(u64 hi, u64 lo, u64 q, u64 mneg) {
+    const u64 r = mont_reduce_lazy(hi, lo, q, mneg);
     return r >= q ? r - q : r;
 }
 

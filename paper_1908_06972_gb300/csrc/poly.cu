@@ -321,7 +321,8 @@ void automorph(const DevTables& t, const PolySet& in, const PolySet& out, u64 g,
 // ---- fast basis conversion (ModUp of one digit, or ModDown from the special primes) ------
 // For each coefficient: y_i = x_i * qhat_i^-1 mod s_i (Shoup), then for every target row m
 // (rows [0, nrows) except [skip_lo, skip_hi), enumerated in order as targets 0..nt-1):
-//   out_m = sum_i y_i * (qhat_i mod t_m) mod t_m   (128-bit sum, one Montgomery reduction).
+//   out_m = sum_i y_i * (qhat_i mod t_m) mod t_m   (128-bit sum, one Montgomery reduction),
+// left in [0, 2 t_m): every output feeds a forward transform, whose butterflies take it.
 // Target prime of row m: m < split ? m : base2 + m - split.  Table: [ns] {inv, inv_shoup},
 // then [nt][ns] qhat_i 2^64 mod t_m (Montgomery form, target-major, each split into 30-bit
 // halves: low word = c mod 2^30, high word = c >> 30).  NS (the number of source primes) is a
@@ -420,8 +421,8 @@ __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
                 const u64 q = sQ[m0 + u], mneg = sM[m0 + u];
                 const U128 va = acc3_value(a[u]), vb = acc3_value(b[u]);
                 ulonglong2 r;
-                r.x = mont_reduce(va.hi, va.lo, q, mneg);
-                r.y = mont_reduce(vb.hi, vb.lo, q, mneg);
+                r.x = mont_reduce_lazy(va.hi, va.lo, q, mneg);
+                r.y = mont_reduce_lazy(vb.hi, vb.lo, q, mneg);
                 *reinterpret_cast<ulonglong2*>(dst + ((size_t)sRow[m0 + u] << logn)) = r;
             }
         }
