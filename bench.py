@@ -224,76 +224,74 @@ def run_gpu(args):
     h2d = sum(a.nbytes for a, _ in host_in)
     d2h = sum(o.nbytes for o in host_out)
 
-    # Pipelined through the public API on a copy stream: step i+1's inputs are copied in
-    # (pft_ct_import_batch) and step i's results copied out (pft_ct_export_batch_async, into
-    # one of two page-locked buffers) while the compute stream runs; every step's results are
-    # in host memory before the timed region ends.
+    # Pipelined through the public API on a copy stream: step i+1's inputs are copied into one of
+    # two fixed sets of input handles (pft_ct_import_batch_into) and step i's results out of one
+    # of two sets of outputs into page-locked buffers (pft_ct_export_batch_async) while the
+    # compute stream runs; the streams order themselves with events (an import waits behind the
+    # export of the step that last read its set, a step waits for the export that last read its
+    # outputs), so the host never blocks before the end; every step's results are in host memory
+    # before the timed region ends.
     S = torch.cuda.current_stream()
     Cs = torch.cuda.Stream()
     C2 = [C, [pft.pft_ct_create(ctx) for _ in range(BATCH)]]
+    IN2 = [[pft.pft_ct_create(ctx) for _ in range(2 * BATCH)] for _ in range(2)]
     outs2 = [host_out, [torch.empty(o.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
                         for o in host_out]]
     marks = []
 
     def on_copy_stream(fn):
         pft.pft_set_stream(ctx, Cs.cuda_stream)
-        r = fn()
+        fn()
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(Cs)
         pft.pft_set_stream(ctx, S.cuda_stream)
-        return r, ev
+        return ev
 
-    def import_next():
-        return on_copy_stream(lambda: pft.pft_ct_import_batch(ctx, [arr for arr, _ in host_in],
-                                                              [sc for _, sc in host_in]))
+    def import_into(k):
+        return on_copy_stream(lambda: pft.pft_ct_import_batch_into(ctx, [arr for arr, _ in host_in],
+                                                                   [sc for _, sc in host_in], IN2[k % 2]))
 
-    pending = []
     host = {"import": 0.0, "compute": 0.0, "export": 0.0, "wait": 0.0}
+    exported = {}
 
-    def step_e2e(k, cur, last):
-        ins, ready = cur
-        S.wait_event(ready)
+    def step_e2e(k, ready, last):
         h0 = time.perf_counter()
-        nxt = import_next() if not last else None
+        nxt = import_into(k + 1) if not last else None
         h1 = time.perf_counter()
+        S.wait_event(ready)
+        if k - 2 in exported:
+            S.wait_event(exported.pop(k - 2))  # the outputs of step k - 2 have been read
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(S)
-        out_cts, out_host = C2[k % 2], outs2[k % 2]
-        step_batched(ins[0::2], ins[1::2], out_cts)
+        ins = IN2[k % 2]
+        step_batched(ins[0::2], ins[1::2], C2[k % 2])
         ev[1].record(S)
         h2 = time.perf_counter()
         Cs.wait_event(ev[1])
-        _, done = on_copy_stream(lambda: pft.pft_ct_export_batch_async(ctx, out_cts, out_host))
-        pending.append((done, ins))
+        exported[k] = on_copy_stream(lambda: pft.pft_ct_export_batch_async(ctx, C2[k % 2], outs2[k % 2]))
         h3 = time.perf_counter()
-        while len(pending) > 1:  # the previous step's results have landed: release its inputs
-            d, old = pending.pop(0)
-            d.synchronize()
-            for h in old:
-                pft.pft_ct_destroy(h)
-        h4 = time.perf_counter()
-        for key, dt in (("import", h1 - h0), ("compute", h2 - h1), ("export", h3 - h2), ("wait", h4 - h3)):
+        for key, dt in (("import", h1 - h0), ("compute", h2 - h1), ("export", h3 - h2)):
             host[key] += dt
         marks.append(ev)
         return nxt
 
     def drain():
-        while pending:
-            d, old = pending.pop(0)
-            d.synchronize()
-            for h in old:
-                pft.pft_ct_destroy(h)
+        h = time.perf_counter()
+        Cs.synchronize()
+        S.synchronize()
+        exported.clear()
+        host["wait"] += time.perf_counter() - h
 
-    step_e2e(0, import_next(), True)
+    step_e2e(0, import_into(0), True)
     drain()
     barrier()
     marks.clear()
     for key in host:
         host[key] = 0.0
     t0 = time.perf_counter()
-    cur = import_next()
+    ready = import_into(0)
     for k in range(args.steps):
-        cur = step_e2e(k, cur, k == args.steps - 1)
+        ready = step_e2e(k, ready, k == args.steps - 1)
     drain()
     barrier()
     e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
@@ -301,7 +299,7 @@ def run_gpu(args):
     e2e_split = {"compute_ms": round(sum(ev[0].elapsed_time(ev[1]) for ev in marks) / len(marks), 2),
                  "wall_ms": round(1e3 * e2e_s / args.steps, 2),
                  "host_ms": {key: round(1e3 * v / args.steps, 2) for key, v in host.items()}}
-    for h in C2[1]:
+    for h in C2[1] + IN2[0] + IN2[1]:
         pft.pft_ct_destroy(h)
 
     # roofline of the timed kernel family

@@ -205,6 +205,12 @@ int pft_ct_export(pft_ctx* ctx, const pft_ct* ct, uint64_t* coeffs, size_t n);
  * (pinned host memory makes the copies asynchronous).  Import creates B new handles. */
 int pft_ct_import_batch(pft_ctx* ctx, const uint64_t* const* coeffs, const int* levels, const double* scales, int B,
                         pft_ct** out);
+/* The same into B existing handles of ctx (created by pft_ct_create or earlier calls): a
+ * handle's buffer is reused when it is large enough, so repeated imports allocate nothing.
+ * Stream-ordered like every operation: work queued earlier on the context's stream that
+ * reads these handles completes before the copies overwrite them. */
+int pft_ct_import_batch_into(pft_ctx* ctx, const uint64_t* const* coeffs, const int* levels, const double* scales,
+                             int B, pft_ct* const* cts);
 int pft_ct_export_batch(pft_ctx* ctx, const pft_ct* const* cts, int B, uint64_t* const* coeffs);
 /* The same without the final synchronisation: the copies are queued on the context's stream
  * and coeffs[i] (page-locked host memory) holds the result once that stream has reached

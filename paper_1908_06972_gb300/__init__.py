@@ -98,6 +98,7 @@ def lib():
             "pft_encrypt": [vp, vp, i, u32, pp], "pft_decrypt": [vp, vp, pp],
             "pft_ct_import": [vp, u64, i, d, pp], "pft_ct_export": [vp, vp, u64, c_size_t],
             "pft_ct_import_batch": [vp, pp, ip, POINTER(c_double), i, pp],
+            "pft_ct_import_batch_into": [vp, pp, ip, POINTER(c_double), i, pp],
             "pft_ct_export_batch": [vp, pp, i, pp], "pft_ct_export_batch_async": [vp, pp, i, pp],
             "pft_add": [vp, vp, vp, vp], "pft_sub": [vp, vp, vp, vp], "pft_add_plain": [vp, vp, vp, vp],
             "pft_mul_plain": [vp, vp, vp, vp], "pft_mul_relin": [vp, vp, vp, vp],
@@ -173,7 +174,7 @@ def exported_symbols():
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
             "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag",
-            "pft_run_jobs", "pft_bfly_ceiling"]
+            "pft_run_jobs", "pft_bfly_ceiling", "pft_ct_import_batch_into"]
 
 
 def _check(rc, ctx=None):
@@ -405,6 +406,15 @@ def pft_ct_import_batch(ctx, arrays, scales):
     out = (c_void_p * max(1, B))()
     _check(lib().pft_ct_import_batch(ctx, ptrs, levels, sc, B, out), ctx)
     return [c_void_p(out[i]) for i in range(B)]
+
+
+def pft_ct_import_batch_into(ctx, arrays, scales, cts):
+    """Imports arrays[i] into the existing handle cts[i] (its buffer reused when large enough)."""
+    B = len(arrays)
+    ptrs = (c_void_p * max(1, B))(*[a.ctypes.data for a in arrays])
+    levels = (c_int * max(1, B))(*[a.shape[1] for a in arrays])
+    sc = (c_double * max(1, B))(*scales)
+    _check(lib().pft_ct_import_batch_into(ctx, ptrs, levels, sc, B, _arr(cts)), ctx)
 
 
 def pft_ct_export_batch(ctx, cts, arrays):

@@ -1625,6 +1625,31 @@ int pft_ct_import_batch(pft_ctx* c, const uint64_t* const* coeffs, const int* le
     });
 }
 
+int pft_ct_import_batch_into(pft_ctx* c, const uint64_t* const* coeffs, const int* levels, const double* scales,
+                             int B, pft_ct* const* cts) {
+    return guard(c, [&] {
+        NEED(c && coeffs && levels && scales && cts && B >= 0, PFT_ERR_ARG, "bad arguments");
+        for (int i = 0; i < B; i++) {
+            NEED(coeffs[i] && cts[i] && levels[i] >= 1 && levels[i] <= c->L, PFT_ERR_ARG,
+                 "bad ciphertext " + std::to_string(i));
+            NEED(!cts[i]->ctx || cts[i]->ctx == c, PFT_ERR_ARG, "handle from another context");
+            for (int j = 0; j < i; j++) NEED(cts[j] != cts[i], PFT_ERR_ARG, "a handle appears twice");
+        }
+        std::vector<PolyRef> r;
+        for (int i = 0; i < B; i++) {
+            pft_ct* ct = cts[i];
+            ct->ctx = c;
+            ensure_ct(c, ct, levels[i]);
+            ct->scale = scales[i];
+            PFT_CUDA(cudaMemcpyAsync(ct->data, coeffs[i], (size_t)2 * levels[i] * c->n * 8, cudaMemcpyHostToDevice,
+                                     c->stream));
+            r.push_back(cpoly(ct->data, levels[i], c->n, 0));
+            r.push_back(cpoly(ct->data, levels[i], c->n, 1));
+        }
+        ntt_fwd(c, r, r);
+    });
+}
+
 static void export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs, bool sync);
 
 int pft_ct_export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* const* coeffs) {

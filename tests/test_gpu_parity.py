@@ -295,6 +295,16 @@ def test_batched_import_export_round_trip(p1):
     torch.cuda.synchronize()
     for c, arr in zip(cts, pinned):
         assert np.array_equal(arr, c.c)
+    # into existing handles: buffers reused (same addresses) when large enough, levels may change
+    ptr = [pf.pft_ct_data(h) for h in hs]
+    new = [o.encrypt_sk(o.encode(synth.slots(950 + i, 64), level=lvl), 650 + i) for i, lvl in enumerate([2, 1, 2])]
+    pf.pft_ct_import_batch_into(p1.ctx, [c.c for c in new], [c.scale for c in new], hs)
+    for c, h in zip(new, hs):
+        p1.assert_equal(h, c, "import_batch_into")
+    assert [pf.pft_ct_data(h) for h in hs] == ptr
+    with pytest.raises(pf.PftError) as e:  # one handle twice
+        pf.pft_ct_import_batch_into(p1.ctx, [c.c for c in new[:2]], [c.scale for c in new[:2]], [hs[0], hs[0]])
+    assert e.value.code == pf.PFT_ERR_ARG
 
 
 def test_graph_replay_matches_oracle(gpu):
