@@ -338,6 +338,10 @@ def run_gpu(args):
     if args.train > 0:
         tr = train_measure(pft, torch, args.train, args.train_plain_docs, args.train_diag > 0)
 
+    ops = None
+    if args.ops > 0:
+        ops = ops_measure(pft, torch, synth, ctx, args.ops)
+
     qu = None
     if args.queue > 0:
         qu = queue_measure(pft, torch, args.queue)
@@ -365,7 +369,7 @@ def run_gpu(args):
            "gpu_launches": int(all_launches), "roofline": roof,
            "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
                         "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
-           "fasttext": ft, "serving": sv, "training": tr, "job_queue": qu}
+           "fasttext": ft, "serving": sv, "training": tr, "job_queue": qu, "ops": ops}
     if rank == 0:
         print(json.dumps(out))
     for h in A + B + C:
@@ -642,6 +646,66 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, 
     for c in ctxs:
         pft.pft_ctx_destroy(c)
     return out
+
+
+# ---- primitive operations at the top level ----------------------------------------------------
+OPS_WORKLOAD = ("the benchmark chain (N=2^16, 60 + 29x50 bits + 4 special primes of 60 bits, about 1750 bits of "
+                "modulus, 128-bit) at its top level 30: one ciphertext per call, and 64 per batched call")
+
+
+def ops_measure(pft, torch, synth, ctx, reps):
+    """Latency of each primitive for one ciphertext at level 30 and the time per ciphertext of
+    the batched call over 64, with CUDA events around `reps` calls after a warm-up."""
+    L_TOP, NB = L, 64
+    pts, cts = [], []
+
+    def enc(seed, nonce):
+        pt = pft.pft_encode(ctx, synth.slots(seed, 256), SCALE, L_TOP)
+        h = pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, nonce)
+        pft.pft_pt_destroy(pt)
+        cts.append(h)
+        return h
+
+    A = [enc(7000 + i, 9000 + 2 * i) for i in range(NB)]
+    B = [enc(8000 + i, 9001 + 2 * i) for i in range(NB)]
+    P = [pft.pft_encode(ctx, synth.slots(9500 + i, 256), SCALE, L_TOP) for i in range(NB)]
+    pts += P
+    C = [pft.pft_ct_create(ctx) for _ in range(NB)]
+    D = [pft.pft_ct_create(ctx) for _ in range(NB)]
+    cts += C + D
+    pft.pft_mul_relin_batch(ctx, A, B, C)  # C at level 30 with the product's scale, for rescale
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    one = {"hmul_relin": lambda: pft.pft_mul_relin(ctx, A[0], B[0], D[0]),
+           "hmulplain": lambda: pft.pft_mul_plain(ctx, A[0], P[0], D[0]),
+           "haddplain": lambda: pft.pft_add_plain(ctx, A[0], P[0], D[0]),
+           "rescale": lambda: pft.pft_rescale(ctx, C[0], D[0]),
+           "rotate": lambda: pft.pft_rotate(ctx, A[0], 1, D[0])}
+    many = {"hmul_relin": lambda: pft.pft_mul_relin_batch(ctx, A, B, D),
+            "hmulplain": lambda: pft.pft_mul_plain_batch(ctx, A, P, D),
+            "rescale": lambda: pft.pft_rescale_batch(ctx, C, D),
+            "rotate": lambda: pft.pft_rotate_batch(ctx, A, 1, D)}
+    lat = {k: round(timed(f), 4) for k, f in one.items()}
+    per = {k: round(timed(f) / NB, 4) for k, f in many.items()}
+    for h in cts:
+        pft.pft_ct_destroy(h)
+    for p in pts:
+        pft.pft_pt_destroy(p)
+    return {"workload": OPS_WORKLOAD, "unit": "ms", "level": L_TOP, "latency_one_ciphertext_ms": lat,
+            "per_ciphertext_in_batch_of_64_ms": per,
+            "hmul_relin_per_s": {"one_at_a_time": round(1e3 / lat["hmul_relin"], 1),
+                                 "batched": round(1e3 / per["hmul_relin"], 1)}}
 
 
 # ---- persistent job queue over two rings ------------------------------------------------------
@@ -1107,6 +1171,7 @@ def main():
     ap.add_argument("--train-plain-docs", type=int, default=2, help="documents timed on the plain training path")
     ap.add_argument("--train-diag", type=int, default=1, help="also time the rotation-light training layout (0: skip)")
     ap.add_argument("--queue", type=int, default=10, help="repetitions of the two-ring job-queue leg (0: skip)")
+    ap.add_argument("--ops", type=int, default=20, help="repetitions of each primitive at the top level (0: skip)")
     ap.add_argument("--serve", type=int, default=48, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
     ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")
