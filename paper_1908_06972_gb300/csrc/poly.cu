@@ -435,6 +435,10 @@ void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st
         std::vector<BconvJob> sel;
         for (int i = 0; i < n_jobs; i++)
             if (jobs[i].ns == ns) sel.push_back(jobs[i]);
+        // longest jobs (most targets) first, so that short ones fill the last wave
+        std::stable_sort(sel.begin(), sel.end(), [](const BconvJob& x, const BconvJob& y) {
+            return x.nrows - (x.skip_hi - x.skip_lo) > y.nrows - (y.skip_hi - y.skip_lo);
+        });
         for (size_t a = 0; a < sel.size(); a += kMaxBconv) {
             const int cnt = (int)std::min(sel.size() - a, (size_t)kMaxBconv);
             BconvBatch b;
@@ -656,7 +660,9 @@ __global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, 
                                                        int alpha, int stage_digits) {
     extern __shared__ __align__(128) u64 ring[];  // [kKsStages][stage_digits][kKsChunk]
     __shared__ __align__(8) u64 bars[kKsStages];
-    const int row = blockIdx.y;
+    // special rows first: every input uses them, so their CTAs are the longest and should not
+    // form the last wave
+    const int row = (int)blockIdx.y < k ? L + (int)blockIdx.y : (int)blockIdx.y - k;
     const int logn = t.logn;
     const int rows_total = L + k;
     const int need = bt.need[row];
