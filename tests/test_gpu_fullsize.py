@@ -47,6 +47,35 @@ def test_p2_keys_match(p2):
     assert np.array_equal(p2.pft.pft_key_export(p2.ctx, 0), p2.orc.keys[0])
 
 
+def test_job_queue_two_rings_full_size(p2, gpu):
+    """One persistent launch over the benchmark ring (N = 2^16, levels 30 and 11) and an
+    N = 2^15 ring (60 + 17 x 40 bits, level 18), with a dependent job: bit for bit against the
+    oracle's HADD / HMULPLAIN."""
+    from oracle.ckks import Plaintext
+
+    q = Pair(gpu, 15, 18, 2, 2, first_bits=60, mid_bits=40, special_bits=60, seed=(0x15, 1, 2, 3),
+             relin=False, gpu_keys=False, insecure=False)
+    try:
+        pf, jobs, checks = p2.pft, [], []
+        for p, lvl, tag in ((p2, 30, 300), (q, 18, 400), (p2, 11, 500)):
+            o = p.orc
+            x = o.encrypt_sk(o.encode(synth.slots(tag, 256), level=lvl), tag)
+            y = o.encrypt_sk(o.encode(synth.slots(tag + 1, 256), level=lvl), tag + 1)
+            pt = o.encode(synth.slots(tag + 2, 256), scale=2.0 ** 30, level=lvl)
+            gx, gy, gp = p.ct(x), p.ct(y), p.pt(pt)
+            s_, m_ = p.empty(), p.empty()
+            jobs += [dict(op=pf.PFT_JOB_ADD, a=gx, b=gy, out=s_),
+                     dict(op=pf.PFT_JOB_MUL_PLAIN, a=s_, p=gp, out=m_, after=len(jobs))]
+            s = o.add(x, y)
+            checks += [(p, s_, s, "add"), (p, m_, o.mul_plain(s, Plaintext(pt.m, pt.scale)), "mul_plain")]
+        pf.pft_run_jobs(p2.ctx, jobs)
+        pf.pft_device_status(p2.ctx)
+        for p, h, want, what in checks:
+            p.assert_equal(h, want, "%s N=%d level %d" % (what, p.N, want.c.shape[1]))
+    finally:
+        q.close()
+
+
 @pytest.fixture(scope="module")
 def p3(gpu):
     steps = [1 << i for i in range(15)]
