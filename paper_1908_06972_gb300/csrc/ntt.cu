@@ -12,8 +12,8 @@
 // N points split into independent sub-transforms of 2^S points at stride T =
 // N >> (s0 + S); a CTA loads C of them into shared memory with coalesced loads,
 // each thread keeps 16 points in registers and applies up to 4 stages per round
-// (Harvey lazy butterflies: forward values in [0, 4q), inverse in [0, 2q), [0, 4q) in the
-// N = 2^16 kernels), and
+// (Harvey butterflies with an estimated Shoup quotient: forward values in [0, 8q), uncorrected
+// for primes below 2^57 in the N = 2^16 kernels; inverse values in [0, 4q)), and
 // rounds exchange through shared memory.  N <= 2^14: one pass, one CTA per limb.
 // N = 2^15, 2^16: two passes (8 + 7 or 8 + 8 stages).
 #include <cooperative_groups.h>
@@ -562,13 +562,7 @@ __global__ void __launch_bounds__(C*(1 << (S - 4)))
                     if (e & (1 << lb)) continue;
                     const int mid = base | (e << w0);
                     const int i = (hi << (S - p - 1)) + (mid >> (p + 1));
-                    const ulonglong2 W = __ldg(&tw[(1 << s) + i]);
-                    u64 X = x[e];
-                    const u64 Y = x[e | (1 << lb)];
-                    if (X >= q2) X -= q2;
-                    const u64 Tm = mul_shoup_lazy(Y, W.x, W.y, q);
-                    x[e] = X + Tm;
-                    x[e | (1 << lb)] = X - Tm + q2;
+                    ct_bfly<false>(x[e], x[e | (1 << lb)], __ldg(&tw[(1 << s) + i]), q, q2);
                 }
             }
 #pragma unroll
@@ -599,20 +593,16 @@ __global__ void __launch_bounds__(C*(1 << (S - 4)))
 #pragma unroll
                 for (int e = 0; e < 16; e++) {
                     if (e & (1 << lb)) continue;
-                    const u64 X = x[e];
-                    const u64 Y = x[e | (1 << lb)];
-                    u64 Sm = X + Y;
-                    if (Sm >= q2) Sm -= q2;
-                    const u64 D = X - Y + q2;
                     if (s == 0) {  // last inverse stage: fold N^-1 into both outputs
+                        u64 Sm = x[e] + x[e | (1 << lb)];
+                        if (Sm >= 2 * q2) Sm -= 2 * q2;
+                        const u64 D = x[e] - x[e | (1 << lb)] + 2 * q2;
                         x[e] = mul_shoup_lazy(Sm, NI.x, NI.y, q);
                         x[e | (1 << lb)] = mul_shoup_lazy(D, NI1.x, NI1.y, q);
                     } else {
                         const int mid = base | (e << w0);
                         const int i = (hi << (S - p - 1)) + (mid >> (p + 1));
-                        const ulonglong2 W = __ldg(&tw[(1 << s) + i]);
-                        x[e] = Sm;
-                        x[e | (1 << lb)] = mul_shoup_lazy(D, W.x, W.y, q);
+                        gs_bfly(x[e], x[e | (1 << lb)], __ldg(&tw[(1 << s) + i]), q, q2);
                     }
                 }
             }
@@ -638,10 +628,7 @@ __global__ void __launch_bounds__(C*(1 << (S - 4)))
         const int u = ubase + c2;
         const size_t j = ((size_t)(u >> logT) << (S + logT)) + ((size_t)mid << logT) + (u & (T - 1));
         u64 v = sm[c2 * SUB + mid + (mid >> 4)];
-        if (is_final) {
-            if (v >= q2) v -= q2;
-            if (v >= q) v -= q;
-        }
+        if (is_final) v = canon8(v, q, q2);  // forward values below 8q, inverse below 2q
         dst[j] = v;
     }
 }
