@@ -115,6 +115,7 @@ static void build_tables(pft_ctx* c) {
     // ModUp tables per (level l, digit j): [ns]{qhat_inv, shoup}, then [targets][ns] qhat mod target
     // (Montgomery form, 30-bit split), targets = rows 0..l+k-1 outside the digit, in order
     c->modup_tab.assign((size_t)L * c->beta_max, nullptr);
+    c->modup_tab_u.assign((size_t)L * c->beta_max, nullptr);
     for (int l = 1; l <= L; l++) {
         const int beta = (l + c->alpha - 1) / c->alpha, E = l + k;
         for (int j = 0; j < beta; j++) {
@@ -141,11 +142,18 @@ static void build_tables(pft_ctx* c) {
                 }
             }
             c->modup_tab[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
+            for (int i = 0; i < ns; i++) {
+                const u64 qi = c->primes[lo + i];
+                tab[2 * i] = mulmod_host(tab[2 * i], invmod_host((u64)c->n % qi, qi), qi);
+                tab[2 * i + 1] = shoup(tab[2 * i], qi);
+            }
+            c->modup_tab_u[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
         }
     }
     // ModDown tables per level: [k]{phat_inv, shoup}, then [l][k] phat mod q_m (Montgomery form,
     // 30-bit split)
     c->moddown_tab.assign(L, nullptr);
+    c->moddown_tab_u.assign(L, nullptr);
     for (int l = 1; l <= L; l++) {
         std::vector<u64> tab(2 * k + (size_t)k * l);
         for (int i = 0; i < k; i++) {
@@ -165,6 +173,12 @@ static void build_tables(pft_ctx* c) {
             }
         }
         c->moddown_tab[l - 1] = tab_upload(c, tab);
+        for (int i = 0; i < k; i++) {
+            const u64 pi = c->primes[L + i];
+            tab[2 * i] = mulmod_host(tab[2 * i], invmod_host((u64)c->n % pi, pi), pi);
+            tab[2 * i + 1] = shoup(tab[2 * i], pi);
+        }
+        c->moddown_tab_u[l - 1] = tab_upload(c, tab);
     }
     // rescale constants per level l >= 2: for k' < l-1: {0, p^-1, shoup}, p = q_{l-1}
     c->rescale_consts.assign(L, nullptr);
@@ -333,14 +347,16 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
     auto ext = [&](size_t b, int j) { return Ext.u() + (oExt[b] + (size_t)j * Eof(b)) * limb; };
     auto uu = [&](size_t b, int pol) { return U.u() + (oU[b] + (size_t)pol * Eof(b)) * limb; };
     auto cv = [&](size_t b, int pol) { return Cv.u() + (oCv[b] + (size_t)pol * io[b].l) * limb; };
-    // 1. coefficient form of d
+    // 1. coefficient form of d (times N where the transform variant allows it: the conversion
+    // tables then carry N^-1)
+    bool unscaled = true;
     {
         std::vector<PolyRef> in, out;
         for (size_t b = 0; b < B; b++) {
             in.push_back(ref((u64*)io[b].d, io[b].l));
             out.push_back(ref(dc(b), io[b].l));
         }
-        ntt_inv(c, in, out);
+        unscaled = ntt_inv_unscaled(c, in, out);
     }
     // 2. ModUp: fast basis conversion of every digit to the other rows; digit rows copied
     {
@@ -352,7 +368,7 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
                 BconvJob J;
                 J.src = dc(b) + (size_t)lo * limb;
                 J.dst = ext(b, j);
-                J.table = c->modup_tab[(size_t)(l - 1) * c->beta_max + j];
+                J.table = (unscaled ? c->modup_tab_u : c->modup_tab)[(size_t)(l - 1) * c->beta_max + j];
                 J.ns = hi - lo;
                 J.src_p0 = lo;
                 J.nrows = E;
@@ -403,7 +419,7 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
                 BconvJob J;
                 J.src = uu(b, pol) + (size_t)l * limb;
                 J.dst = cv(b, pol);
-                J.table = c->moddown_tab[l - 1];
+                J.table = nullptr;  // chosen below, with the form of the transform
                 J.ns = k;
                 J.src_p0 = L;
                 J.nrows = l;
@@ -415,7 +431,8 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
                 jobs.push_back(J);
             }
         }
-        ntt_inv(c, sp, sp);
+        const bool unscaled5 = ntt_inv_unscaled(c, sp, sp);
+        for (BconvJob& J : jobs) J.table = (unscaled5 ? c->moddown_tab_u : c->moddown_tab)[J.nrows - 1];
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
     }
     // 6. out = acc + (u_Q - conv) P^-1, fused with the last forward pass of conv where the

@@ -23,6 +23,9 @@ struct pft_ctx {
     std::vector<void*> owned;  // table buffers
     // basis-conversion tables: modup[(l-1) * beta_max + j], moddown[l-1] (device offsets)
     std::vector<const u64*> modup_tab, moddown_tab;
+    // the same with every source constant times N^-1 (for inputs of an inverse transform that
+    // skipped its N^-1)
+    std::vector<const u64*> modup_tab_u, moddown_tab_u;
     const u64* moddown_consts = nullptr;           // [L][3] {0, P^-1, shoup}
     std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {0, p^-1, shoup}
     std::vector<const u64*> pmodq_consts;          // digit j -> [alpha][3] {0, P mod q_m, shoup}
@@ -146,6 +149,16 @@ inline void ntt_fwd(pft_ctx* c, const std::vector<PolyRef>& in, const std::vecto
 }
 inline void ntt_inv(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
     chunks(out.size(), [&](size_t a, size_t b) { ntt_inverse(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
+}
+// N times the inverse transform where the transform variant has that kernel (true), else the
+// inverse transform itself (false)
+inline bool ntt_inv_unscaled(pft_ctx* c, const std::vector<PolyRef>& in, const std::vector<PolyRef>& out) {
+    bool unscaled = true;
+    chunks(out.size(), [&](size_t a, size_t b) {
+        if (unscaled) unscaled = ntt_inverse_unscaled(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream);
+    });
+    if (!unscaled) ntt_inv(c, in, out);
+    return unscaled;
 }
 inline void ew(pft_ctx* c, EwOp op, const std::vector<PolyRef>& a, const std::vector<PolyRef>& b,
                const std::vector<PolyRef>& out) {

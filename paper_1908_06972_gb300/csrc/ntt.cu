@@ -86,7 +86,7 @@ __device__ __forceinline__ u64 canon8(u64 v, u64 q, u64 q2) {
 // One round = four stages on 16 registers: register e holds element (e << W0) | wpart of
 // the current 256-point sub-transform; DIMHI = 0 for column stages (s = 7 - p), 8 for row
 // stages (s = 15 - p, r = the row being transformed).
-template <bool INV, int W0, int DIMHI, bool LAZY = false>
+template <bool INV, int W0, int DIMHI, bool LAZY = false, bool UNSCALED = false>
 __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, const ulonglong2* __restrict__ tw,
                                             u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1) {
 #pragma unroll
@@ -101,7 +101,7 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
             const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
             if (!INV) {
                 ct_bfly<LAZY>(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
-            } else if (s == 0) {  // last inverse stage: N^-1 folded into both outputs
+            } else if (s == 0 && !UNSCALED) {  // last inverse stage: N^-1 folded into both outputs
                 u64 S = x[e] + x[e | (1 << lb)];
                 if (S >= 2 * q2) S -= 2 * q2;
                 const u64 D = x[e] - x[e | (1 << lb)] + 2 * q2;
@@ -230,7 +230,9 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(512, MINB)
 constexpr int kRowStride = 273;  // 256 + 16 padding + 1
 constexpr u64 kLazyBound = 1ull << 57;  // forward butterflies skip the correction below this prime
 
-template <bool INV, int LOGT, int MINB>
+// UNSCALED (inverse): the last stage is a plain Gentleman-Sande butterfly (no N^-1) and the
+// output stays in [0, 4q): N times the inverse transform, for a consumer that scales anyway.
+template <bool INV, int LOGT, int MINB, bool UNSCALED = false>
 __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet in, PolySet out, int is_final) {
     __shared__ u64 sm[256 * 17];
     const int poly = blockIdx.z, limb = blockIdx.y;
@@ -272,9 +274,10 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = sm[((e << 4) | w) * 17 + cc];
-        ntt16_round<true, 4, 0>(x, w, 0, tw, q, q2, NI, NI1);
+        ntt16_round<true, 4, 0, false, UNSCALED>(x, w, 0, tw, q, q2, NI, NI1);
 #pragma unroll
-        for (int e = 0; e < 16; e++) dst[(size_t)((e << 4) | w) << LOGT] = is_final ? canon4(x[e], q, q2) : x[e];
+        for (int e = 0; e < 16; e++)
+            dst[(size_t)((e << 4) | w) << LOGT] = is_final && !UNSCALED ? canon4(x[e], q, q2) : x[e];
     }
 }
 
@@ -443,6 +446,31 @@ static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const Po
                                  cudaStream_t st) {
     if (minb == 4) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
     else launch_ntt16_twopass_v<3>(t, in, out, inverse, st);
+}
+
+template <int MINB>
+static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& in, const PolySet& out,
+                                            cudaStream_t st) {
+    if (MINB == 4) {  // the same carveout as the scaled kernels of this variant
+        static bool attr_set = false;
+        if (!attr_set) {
+            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB, true>,
+                                          cudaFuncAttributePreferredSharedMemoryCarveout, 64));
+            attr_set = true;
+        }
+    }
+    dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);
+    const double work = set_limbs(out) * (double)(t.n / 2) * 8;
+    {
+        PFT_PROF("ntt.inv.contig", st, work);
+        k_ntt8_contig<true, MINB><<<grid, 256, 0, st>>>(t, in, out, 0);
+    }
+    PFT_LAUNCH_CHECK("intt pass B");
+    {
+        PFT_PROF("ntt.inv.strided", st, work);
+        k_ntt8_strided<true, 8, MINB, true><<<grid, 256, 0, st>>>(t, out, out, 1);
+    }
+    PFT_LAUNCH_CHECK("intt pass A (unscaled)");
 }
 
 template <int MINB>
@@ -754,6 +782,16 @@ double bfly_ceiling(const DevTables& t, cudaStream_t st) {
     PFT_CUDA(cudaEventDestroy(b));
     PFT_CUDA(cudaFree(sink));
     return (double)grid * 256 * rounds * 16 / (ms / 1e3);
+}
+
+bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
+    if (out.count == 0) return true;
+    if (t.logn != 16) return false;
+    const int v16 = ntt16_variant(t);
+    if (v16 != 0 && v16 != 1) return false;
+    if (v16 == 1) launch_ntt16_inverse_unscaled_v<4>(t, in, out, st);
+    else launch_ntt16_inverse_unscaled_v<3>(t, in, out, st);
+    return true;
 }
 
 bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {

@@ -107,6 +107,10 @@ struct NttEpi {
 // Forward transform of io (in place) fused with the epilogue; false (nothing launched) where
 // the ring or the transform variant has no fused kernel.
 bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st);
+// N times the inverse transform (no N^-1 at the last stage, values in [0, 4q)) for consumers
+// that scale their input anyway; false (nothing launched) where the ring or the transform
+// variant has no such kernel.
+bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
 // Butterflies per second of the transform's (exact-path) butterfly arithmetic on register data
 // only: the arithmetic ceiling the transforms are measured against (synchronous).
 double bfly_ceiling(const DevTables& t, cudaStream_t st);
