@@ -658,7 +658,7 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
     // ModUp of c1, once
     {
         std::vector<PolyRef> in{ref(c1, l)}, out{ref(Dc.u(), l)};
-        ntt_inv(c, in, out);
+        const bool unscaled = ntt_inv_unscaled(c, in, out);  // N^-1 then in the conversion tables
         std::vector<BconvJob> jobs;
         std::vector<PolyRef> cin, cout, rows;
         for (int j = 0; j < beta; j++) {
@@ -666,7 +666,7 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
             BconvJob J;
             J.src = Dc.u() + (size_t)lo * limb;
             J.dst = ext(Ext.u(), j);
-            J.table = c->modup_tab[(size_t)(l - 1) * c->beta_max + j];
+            J.table = (unscaled ? c->modup_tab_u : c->modup_tab)[(size_t)(l - 1) * c->beta_max + j];
             J.ns = hi - lo;
             J.src_p0 = lo;
             J.nrows = E;
@@ -717,7 +717,7 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
             BconvJob J;
             J.src = up + (size_t)l * limb;
             J.dst = Cv.u() + (size_t)pol * l * limb;
-            J.table = c->moddown_tab[l - 1];
+            J.table = nullptr;  // chosen with the form of the transform
             J.ns = k;
             J.src_p0 = L;
             J.nrows = l;
@@ -728,7 +728,8 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
             J.pad = 0;
             jobs.push_back(J);
         }
-        ntt_inv(c, sp, sp);
+        const bool unscaled_sp = ntt_inv_unscaled(c, sp, sp);
+        for (BconvJob& J : jobs) J.table = (unscaled_sp ? c->moddown_tab_u : c->moddown_tab)[l - 1];
         bconv(c->tabs, jobs.data(), (int)jobs.size(), c->stream);
         const std::vector<PolyRef> xs{ref(U.u(), l), ref(U.u() + (size_t)E * limb, l)};
         const std::vector<PolyRef> as{ref(A0.u(), l), ref(nullptr, l)};
