@@ -7,7 +7,12 @@
  * below 2^62), CKKS encoding of N/2 complex slots, KEYGEN/ENC/DEC, HADD, HMUL
  * (+ relinearisation), HADDPLAIN, HMULPLAIN, RESCALE (Eq. 1, Algorithm 3) and
  * ROTATE (Sec. 2.3 and the rotation discussion of Sec. 5.3).  The inference
- * entry point follows Sec. 3.1 (Fig. 3, Algorithm 2).
+ * entry point follows Sec. 3.1 (Fig. 3, Algorithm 2); the training entry points
+ * follow Sec. 4.2 (Algorithm 5).  Beyond the paper: batched forms of every operation
+ * over ciphertexts at mixed levels, hoisted rotations, CUDA-graph capture, seeded
+ * compressed keys, rotation-light (diagonal) inference and training, a request
+ * server with continuous batching, and a persistent job queue over rings of
+ * different N.
  *
  * Conventions shared by every call
  *   - Every function returns an int status: PFT_OK (0) or a PFT_ERR_* code.
