@@ -253,9 +253,10 @@ int pft_rotate(pft_ctx* ctx, const pft_ct* a, int32_t step, pft_ct* out);
 int pft_device_status(pft_ctx* ctx);
 int pft_wait_selftest(pft_ctx* ctx, long long polls);
 /* Arithmetic ceiling of the transforms: butterflies per second of the transforms' own
- * Cooley-Tukey butterfly (Shoup product with the estimated quotient, Harvey corrections) on
- * register-resident data with no memory traffic, 4 CTAs per SM, timed with CUDA events on the
- * context's stream (synchronous; about 10 ms).  *out: butterflies per second. */
+ * Cooley-Tukey butterfly (Shoup product with the estimated quotient; the faster of its
+ * corrected and uncorrected forms) on register-resident data with no memory traffic, 4 CTAs
+ * per SM, timed with CUDA events on the context's stream (synchronous; about 20 ms).
+ * *out: butterflies per second. */
 int pft_bfly_ceiling(pft_ctx* ctx, double* out);
 
 /* ---- persistent job queue (batching over uneven levels and ring sizes) -----
