@@ -370,10 +370,11 @@ int pft_graph_destroy(pft_graph* graph);
  *          PFT_ERR_ARG with a message naming the limit
  *   out    device pointer, [2][level-1][N]; must not overlap `in`; receives the rescaled
  *          ciphertext (its scale is the input scale divided by q_{level-1})
- * Work is queued on the context stream.  The first call on a device looks up the device
- * address of the fixed array; make that first call before any stream capture.  All calls
- * on a device share the array and it keeps the last call's contents: calls whose GPU work
- * overlaps (different streams or contexts on the same device) race on it. */
+ * Work is queued on the context stream.  The context's device (the one current at
+ * pft_ctx_create, which also looked up the array's device address there) must be current,
+ * else PFT_ERR_ARG.  All calls on a device share the array and it keeps the last call's
+ * contents: calls whose GPU work overlaps (different streams or contexts on the same device)
+ * race on it. */
 int pft_rescale_noalloc(pft_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
 
 /* ---- raw transforms on caller memory (kernel-level access) ----------------

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <set>
 #include <stdexcept>
 
 #include "evaluator.h"
@@ -17,7 +19,35 @@ void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 void check_cuda(cudaError_t e, const char* what) {
     if (e != cudaSuccess) fail(PFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+static std::mutex& handles_mu() {
+    static std::mutex m;
+    return m;
+}
+static std::set<const void*>& handles() {
+    static std::set<const void*> h;
+    return h;
+}
+bool first_on_device(const void* key) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> seen;
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> g(mu);
+    return seen.insert({key, dev}).second;
+}
 }  // namespace pft
+void handle_add(const void* h) {
+    std::lock_guard<std::mutex> g(pft::handles_mu());
+    pft::handles().insert(h);
+}
+void handle_remove(const void* h) {
+    std::lock_guard<std::mutex> g(pft::handles_mu());
+    pft::handles().erase(h);
+}
+bool handle_live(const void* h) {
+    std::lock_guard<std::mutex> g(pft::handles_mu());
+    return pft::handles().count(h) != 0;
+}
 
 // ---- context construction ---------------------------------------------------------------
 static u64 shoup(u64 w, u64 q) { return (u64)(((unsigned __int128)w << 64) / q); }
@@ -468,8 +498,8 @@ static std::map<int, std::vector<int>> by_level(const pft_ct* const* a, int B) {
 void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, int B, pft_ct* const* out,
                          EwOp op) {
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
-        check_ct(b[i]);
+        check_ct(c, a[i]);
+        check_ct(c, b[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
         NEED(a[i]->level == b[i]->level, PFT_ERR_LEVEL_MISMATCH, "HADD operands at different levels");
         NEED(a[i]->scale == b[i]->scale, PFT_ERR_SCALE_MISMATCH, "HADD operands at different scales");
@@ -492,8 +522,8 @@ void op_add_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const* b, in
 void op_mul_plain_batch(pft_ctx* c, const pft_ct* const* a, const pft_pt* const* p, int B,
                                pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
-        check_pt(p[i]);
+        check_ct(c, a[i]);
+        check_pt(c, p[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
         NEED(a[i]->level == p[i]->level, PFT_ERR_LEVEL_MISMATCH, "HMULPLAIN operands at different levels");
     }
@@ -519,8 +549,8 @@ void op_mul_relin_batch(pft_ctx* c, const pft_ct* const* a, const pft_ct* const*
                                pft_ct* const* out) {
     NEED(c->keys.count(0), PFT_ERR_NO_KEY, "no relinearisation key");
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
-        check_ct(b[i]);
+        check_ct(c, a[i]);
+        check_ct(c, b[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
         NEED(a[i]->level == b[i]->level, PFT_ERR_LEVEL_MISMATCH, "HMUL operands at different levels");
     }
@@ -588,7 +618,7 @@ static void mul_relin_group(pft_ctx* c, const pft_ct* const* a, const pft_ct* co
 
 static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
+        check_ct(c, a[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
     }
     const u32 g = galois_of(c->n, step);
@@ -640,7 +670,7 @@ static void op_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t s
 // extended digits (evaluation form) are permuted by each step's automorphism, then go through
 // the inner product with that step's key and ModDown; out_i = (aut(c0) + u0', u1').
 void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n, pft_ct* const* outs) {
-    check_ct(a);
+    check_ct(c, a);
     NEED(n >= 0 && (n == 0 || (steps && outs)), PFT_ERR_ARG, "bad arguments");
     const int l = a->level, k = c->k, L = c->L, alpha = c->alpha, E = l + k, beta = (l + alpha - 1) / alpha;
     const size_t limb = (size_t)c->n;
@@ -740,7 +770,7 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
 
 void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
+        check_ct(c, a[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
         NEED(a[i]->level >= 2, PFT_ERR_LEVEL_MISMATCH, "rescale needs at least two primes");
     }
@@ -784,7 +814,7 @@ void op_rescale_batch(pft_ctx* c, const pft_ct* const* a, int B, pft_ct* const* 
 // ---- level and scale management --------------------------------------------------------------
 void op_drop_level_batch(pft_ctx* c, const pft_ct* const* a, int B, int level, pft_ct* const* out) {
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
+        check_ct(c, a[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
         NEED(level >= 1 && level <= a[i]->level, PFT_ERR_LEVEL_MISMATCH, "target level above the input level");
     }
@@ -817,7 +847,7 @@ void op_const_batch(pft_ctx* c, const pft_ct* const* a, int B, double value, dou
                     pft_ct* const* out) {
     int lmax = 0;
     for (int i = 0; i < B; i++) {
-        check_ct(a[i]);
+        check_ct(c, a[i]);
         NEED(out[i], PFT_ERR_ARG, "null output");
         lmax = std::max(lmax, a[i]->level);
     }
@@ -901,7 +931,7 @@ void relin_batch(pft_ctx* c, const std::vector<RelinIO>& io) {
 // ---- encryption ----------------------------------------------------------------------------
 static void encrypt(pft_ctx* c, const pft_pt* pt, int mode, u32 nonce, pft_ct* out) {
     NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
-    check_pt(pt);
+    check_pt(c, pt);
     const int l = pt->level, n = c->n;
     const size_t limb = n;
     ensure_ct(c, out, l);
@@ -1009,7 +1039,7 @@ void ft_check_doc(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int
         NEED(n_chunks == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
     NEED(v, PFT_ERR_ARG, "null input");
     for (int i = 0; i < n_chunks; i++) {
-        check_ct(v[i]);
+        check_ct(c, v[i]);
         NEED(v[i]->level == v[0]->level, PFT_ERR_LEVEL_MISMATCH, "the inputs of one document differ in level");
         NEED(v[i]->scale == v[0]->scale, PFT_ERR_SCALE_MISMATCH, "the inputs of one document differ in scale");
     }
@@ -1243,21 +1273,24 @@ static void fasttext_batch(pft_ctx* c, const pft_ft_model* M, const pft_ct* cons
 // overlaps (other streams, other contexts on the same device) race on it.
 constexpr size_t kNoAllocScratchWords = (size_t)4 << 20;  // 32 MiB
 static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchWords];
-static u64* g_noalloc_addr[128] = {nullptr};  // device address of the array, per device ordinal
 
-// Device address of the array for the current device.  The first call on a device looks it
-// up (host code cannot use the array's name as a device address).
-static u64* noalloc_scratch() {
+// Device address of the array on the current device.  Host code cannot use the array's name
+// as a device address, so pft_ctx_create looks it up (once per device, under a lock) and keeps
+// it in the context.
+static u64* noalloc_scratch_lookup() {
+    static std::mutex mu;
+    static std::map<int, u64*> addr;
     int dev = -1;
     PFT_CUDA(cudaGetDevice(&dev));
-    NEED(dev >= 0 && dev < 128, PFT_ERR_ARG, "device ordinal out of range");
-    if (!g_noalloc_addr[dev]) {
+    std::lock_guard<std::mutex> g(mu);
+    u64*& a = addr[dev];
+    if (!a) {
         void* p = nullptr;
         PFT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         NEED(p != nullptr, PFT_ERR_CUDA, "no device address for the fixed scratch array");
-        g_noalloc_addr[dev] = (u64*)p;
+        a = (u64*)p;
     }
-    return g_noalloc_addr[dev];
+    return a;
 }
 
 // ---- launch accounting ---------------------------------------------------------------------
@@ -1391,7 +1424,9 @@ int pft_ctx_create(const pft_params* prm, const pft_allocator* alloc, pft_ctx** 
             c->alloc = *alloc;
             c->has_alloc = true;
         }
+        PFT_CUDA(cudaGetDevice(&c->device));
         build_tables(c.get());
+        c->noalloc_scratch = noalloc_scratch_lookup();
     });
     if (rc != PFT_OK) {
         for (void* p : c->owned) cudaFree(p);
@@ -1530,33 +1565,35 @@ int pft_ct_create(pft_ctx* c, pft_ct** out) {
 }
 int pft_ct_destroy(pft_ct* ct) {
     if (!ct) return PFT_OK;
+    if (!handle_live(ct)) return PFT_ERR_ARG;  // destroyed already, or never a handle
     dfree(ct->ctx, ct->data);
     delete ct;
     return PFT_OK;
 }
 int pft_pt_destroy(pft_pt* pt) {
     if (!pt) return PFT_OK;
+    if (!handle_live(pt)) return PFT_ERR_ARG;
     dfree(pt->ctx, pt->data);
     delete pt;
     return PFT_OK;
 }
 int pft_ct_level(const pft_ct* ct, int* level) {
-    if (!ct || !level) return PFT_ERR_ARG;
+    if (!ct || !level || !handle_live(ct)) return PFT_ERR_ARG;
     *level = ct->level;
     return PFT_OK;
 }
 int pft_ct_scale(const pft_ct* ct, double* scale) {
-    if (!ct || !scale) return PFT_ERR_ARG;
+    if (!ct || !scale || !handle_live(ct)) return PFT_ERR_ARG;
     *scale = ct->scale;
     return PFT_OK;
 }
 int pft_pt_level(const pft_pt* pt, int* level) {
-    if (!pt || !level) return PFT_ERR_ARG;
+    if (!pt || !level || !handle_live(pt)) return PFT_ERR_ARG;
     *level = pt->level;
     return PFT_OK;
 }
 int pft_ct_data(const pft_ct* ct, uint64_t** p) {
-    if (!ct || !p) return PFT_ERR_ARG;
+    if (!ct || !p || !handle_live(ct)) return PFT_ERR_ARG;
     *p = ct->data;
     return PFT_OK;
 }
@@ -1582,7 +1619,7 @@ int pft_pt_import(pft_ctx* c, const uint64_t* coeffs, int level, double scale, p
 
 int pft_pt_export(pft_ctx* c, const pft_pt* pt, uint64_t* coeffs, size_t nw) {
     return guard(c, [&] {
-        check_pt(pt);
+        check_pt(c, pt);
         NEED(c && coeffs && nw >= (size_t)pt->level * c->n, PFT_ERR_ARG, "bad arguments");
         Scratch t(c, (size_t)pt->level * c->n * 8);
         std::vector<PolyRef> in{ref(pt->data, pt->level)}, o{ref(t.u(), pt->level)};
@@ -1608,7 +1645,7 @@ int pft_ct_import(pft_ctx* c, const uint64_t* coeffs, int level, double scale, p
 
 int pft_ct_export(pft_ctx* c, const pft_ct* ct, uint64_t* coeffs, size_t nw) {
     return guard(c, [&] {
-        check_ct(ct);
+        check_ct(c, ct);
         const size_t words = (size_t)2 * ct->level * c->n;
         NEED(c && coeffs && nw >= words, PFT_ERR_ARG, "bad arguments");
         Scratch t(c, words * 8);
@@ -1683,7 +1720,7 @@ static void export_batch(pft_ctx* c, const pft_ct* const* cts, int B, uint64_t* 
         NEED(c && cts && coeffs && B >= 0, PFT_ERR_ARG, "bad arguments");
         size_t maxw = 0;
         for (int i = 0; i < B; i++) {
-            check_ct(cts[i]);
+            check_ct(c, cts[i]);
             NEED(coeffs[i], PFT_ERR_ARG, "null output buffer");
             maxw = std::max(maxw, (size_t)2 * cts[i]->level * c->n);
         }
@@ -1742,7 +1779,7 @@ int pft_encode(pft_ctx* c, const double* re_im, int n_slots, double scale, int l
 
 int pft_decode(pft_ctx* c, const pft_pt* pt, double* re_im, int n_slots) {
     return guard(c, [&] {
-        check_pt(pt);
+        check_pt(c, pt);
         NEED(c && re_im && n_slots >= 0 && n_slots <= c->n / 2, PFT_ERR_ARG, "bad arguments");
         const int l = pt->level;
         std::vector<u64> rows((size_t)l * c->n);
@@ -1770,7 +1807,7 @@ int pft_encrypt(pft_ctx* c, const pft_pt* pt, int mode, uint32_t nonce, pft_ct**
 
 int pft_decrypt(pft_ctx* c, const pft_ct* ct, pft_pt** out) {
     return guard(c, [&] {
-        check_ct(ct);
+        check_ct(c, ct);
         NEED(c && out, PFT_ERR_ARG, "bad arguments");
         NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
         const int l = ct->level;
@@ -1793,8 +1830,8 @@ int pft_sub(pft_ctx* c, const pft_ct* a, const pft_ct* b, pft_ct* out) {
 }
 int pft_add_plain(pft_ctx* c, const pft_ct* a, const pft_pt* p, pft_ct* out) {
     return guard(c, [&] {
-        check_ct(a);
-        check_pt(p);
+        check_ct(c, a);
+        check_pt(c, p);
         NEED(out, PFT_ERR_ARG, "null output");
         NEED(a->level == p->level, PFT_ERR_LEVEL_MISMATCH, "HADDPLAIN operands at different levels");
         NEED(a->scale == p->scale, PFT_ERR_SCALE_MISMATCH, "HADDPLAIN operands at different scales");
@@ -1869,14 +1906,14 @@ int pft_dot_plain_batch(pft_ctx* c, const pft_ct* const* cts, const pft_pt* cons
         std::vector<const u64*> A, Bv;
         std::vector<u64*> O;
         for (int k = 0; k < (pts_shared ? K : K * n_out); k++) {
-            check_pt(pts[k]);
+            check_pt(c, pts[k]);
             NEED(pts[k]->level == l, PFT_ERR_LEVEL_MISMATCH, "plaintexts must sit at the ciphertexts' level");
         }
         std::vector<double> sc(n_out);
         for (int o = 0; o < n_out; o++) {
             for (int k = 0; k < K; k++) {
                 const pft_ct* x = cts[(size_t)o * K + k];
-                check_ct(x);
+                check_ct(c, x);
                 NEED(x->level == l, PFT_ERR_LEVEL_MISMATCH, "all ciphertexts must share one level");
                 const double s = x->scale * pts[pts_shared ? k : (size_t)o * K + k]->scale;
                 if (k == 0) sc[o] = s;
@@ -2037,7 +2074,12 @@ int pft_rescale_noalloc(pft_ctx* c, const uint64_t* in, int level, uint64_t* out
         const u64* in_end = in + 2 * l * n;
         const u64* out_end = out + 2 * (l - 1) * n;
         NEED(out_end <= in || in_end <= out, PFT_ERR_ARG, "rescale_noalloc: output overlaps input");
-        u64* last = noalloc_scratch();
+        int dev = -1;
+        PFT_CUDA(cudaGetDevice(&dev));
+        NEED(dev == c->device, PFT_ERR_ARG,
+             "rescale_noalloc: the current device (" + std::to_string(dev) + ") is not the context's device (" +
+                 std::to_string(c->device) + ")");
+        u64* last = c->noalloc_scratch;
         u64* rb = last + 2 * n;
         u64* src = (u64*)in;
         std::vector<PolyRef> lin, lout, rr, x, o;
@@ -2079,7 +2121,7 @@ int pft_ft_model_import(pft_ctx* c, const pft_pt* const* H_pts, const pft_pt* co
         M->chunks = chunks_n;
         M->level = H_pts[0]->level;
         auto copy_pt = [&](const pft_pt* p) {
-            check_pt(p);
+            check_pt(c, p);
             pft_pt* q = new_pt(c);
             ensure_pt(c, q, p->level);
             q->scale = p->scale;
@@ -2207,7 +2249,7 @@ int pft_ft_model_import_diag(pft_ctx* c, const pft_pt* const* D_pts, const pft_p
         M->level = D_pts[0]->level;
         M->variant = 1;
         auto copy_pt = [&](const pft_pt* p) {
-            check_pt(p);
+            check_pt(c, p);
             pft_pt* q = new_pt(c);
             ensure_pt(c, q, p->level);
             q->scale = p->scale;

@@ -10,9 +10,16 @@
 
 using namespace pft;
 
+#define NEED(cond, code, msg) \
+    do {                      \
+        if (!(cond)) fail(code, msg); \
+    } while (0)
+
 // ---- handles ---------------------------------------------------------------------------
 struct pft_ctx {
     pft_params prm;
+    int device = 0;                 // CUDA device current at creation; all work runs there
+    u64* noalloc_scratch = nullptr;  // device address of the fixed array of pft_rescale_noalloc
     int logn = 0, n = 0, L = 0, k = 0, alpha = 0, beta_max = 0;
     std::vector<u64> primes;  // q_0..q_{L-1}, p_0..p_{k-1}
     pft_allocator alloc{};
@@ -40,12 +47,23 @@ struct pft_ctx {
     bool compressed_keys = false;
 };
 
+// Every ciphertext and plaintext object -- the handles given to callers and the library's own
+// temporaries -- is recorded while it exists, so that a call given a destroyed handle (or a
+// pointer that never was one) fails with PFT_ERR_ARG instead of reading freed memory.  A
+// pointer value that a later handle happens to reuse is that later handle.
+void handle_add(const void* h);
+void handle_remove(const void* h);
+bool handle_live(const void* h);
 struct pft_ct {
     pft_ctx* ctx = nullptr;
     u64* data = nullptr;
     size_t cap = 0;  // words
     int level = 0;
     double scale = 1.0;
+    pft_ct() { handle_add(this); }
+    pft_ct(const pft_ct& o) : ctx(o.ctx), data(o.data), cap(o.cap), level(o.level), scale(o.scale) { handle_add(this); }
+    pft_ct& operator=(const pft_ct&) = default;
+    ~pft_ct() { handle_remove(this); }
 };
 struct pft_pt {
     pft_ctx* ctx = nullptr;
@@ -53,6 +71,10 @@ struct pft_pt {
     size_t cap = 0;
     int level = 0;
     double scale = 1.0;
+    pft_pt() { handle_add(this); }
+    pft_pt(const pft_pt& o) : ctx(o.ctx), data(o.data), cap(o.cap), level(o.level), scale(o.scale) { handle_add(this); }
+    pft_pt& operator=(const pft_pt&) = default;
+    ~pft_pt() { handle_remove(this); }
 };
 struct pft_graph {
     cudaGraph_t graph = nullptr;
@@ -98,6 +120,9 @@ inline T* upload(pft_ctx* c, Scratch& s, const std::vector<T>& v) {
     return (T*)s.p;
 }
 inline void ensure_ct(pft_ctx* c, pft_ct* ct, int level) {
+    NEED(ct && handle_live(ct), PFT_ERR_ARG, "output is not a live ciphertext handle");
+    NEED(!ct->ctx || ct->ctx == c, PFT_ERR_ARG, "output handle from another context");
+    ct->ctx = c;
     const size_t need = (size_t)2 * level * c->n;
     if (ct->cap < need) {
         dfree(c, ct->data);
@@ -109,6 +134,9 @@ inline void ensure_ct(pft_ctx* c, pft_ct* ct, int level) {
     ct->level = level;
 }
 inline void ensure_pt(pft_ctx* c, pft_pt* pt, int level) {
+    NEED(pt && handle_live(pt), PFT_ERR_ARG, "output is not a live plaintext handle");
+    NEED(!pt->ctx || pt->ctx == c, PFT_ERR_ARG, "output handle from another context");
+    pt->ctx = c;
     const size_t need = (size_t)level * c->n;
     if (pt->cap < need) {
         dfree(c, pt->data);
@@ -196,12 +224,23 @@ inline int guard(pft_ctx* c, F f) {
         return PFT_ERR_ARG;
     }
 }
-#define NEED(cond, code, msg) \
-    do {                      \
-        if (!(cond)) fail(code, msg); \
-    } while (0)
-inline void check_ct(const pft_ct* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty ciphertext"); }
-inline void check_pt(const pft_pt* a) { NEED(a && a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty plaintext"); }
+inline void check_ct(const pft_ct* a) {
+    NEED(a && handle_live(a), PFT_ERR_ARG, "not a live ciphertext handle (destroyed, or never created)");
+    NEED(a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty ciphertext");
+}
+inline void check_pt(const pft_pt* a) {
+    NEED(a && handle_live(a), PFT_ERR_ARG, "not a live plaintext handle (destroyed, or never created)");
+    NEED(a->ctx && a->data && a->level > 0, PFT_ERR_ARG, "empty plaintext");
+}
+// The same, for a handle that must belong to context c.
+inline void check_ct(const pft_ctx* c, const pft_ct* a) {
+    check_ct(a);
+    NEED(a->ctx == c, PFT_ERR_ARG, "ciphertext handle from another context");
+}
+inline void check_pt(const pft_ctx* c, const pft_pt* a) {
+    check_pt(a);
+    NEED(a->ctx == c, PFT_ERR_ARG, "plaintext handle from another context");
+}
 
 // ---- operations shared by the translation units (ckks.cu) ----------------------------------
 // Galois element 5^step mod 2N of a left rotation by `step` slots.

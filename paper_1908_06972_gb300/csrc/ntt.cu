@@ -404,15 +404,13 @@ template <int MINB>
 static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
                                    cudaStream_t st) {
     if (MINB == 4) {  // four CTAs of 35 KB shared memory: a carveout that fits them, the rest L1
-        static bool attr_set = false;
-        if (!attr_set) {
+        if (first_on_device((const void*)&k_ntt8_contig_epi<MINB>)) {
             const int co = 64;
             PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<false, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
             PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
             PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<false, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
             PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<true, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
             PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig_epi<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-            attr_set = true;
         }
     }
     dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);  // 256 sub-transforms / 16 per CTA
@@ -452,12 +450,9 @@ template <int MINB>
 static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& in, const PolySet& out,
                                             cudaStream_t st) {
     if (MINB == 4) {  // the same carveout as the scaled kernels of this variant
-        static bool attr_set = false;
-        if (!attr_set) {
+        if (first_on_device((const void*)&k_ntt8_strided<true, 8, MINB, true>))
             PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB, true>,
                                           cudaFuncAttributePreferredSharedMemoryCarveout, 64));
-            attr_set = true;
-        }
     }
     dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);
     const double work = set_limbs(out) * (double)(t.n / 2) * 8;
@@ -493,12 +488,9 @@ static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttE
 template <bool INV, int MINB>
 static void launch_ntt16_cluster_v(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
     const size_t smem = (size_t)256 * kN16Stride * sizeof(u64);
-    static bool attr_set = false;
-    if (!attr_set) {
+    if (first_on_device((const void*)&k_ntt16_cluster<INV, MINB>))
         PFT_CUDA(cudaFuncSetAttribute(k_ntt16_cluster<INV, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        attr_set = true;
-    }
     dim3 grid(8, (unsigned)out.max_limbs, (unsigned)out.count);
     PFT_PROF(INV ? "ntt.inv.cluster" : "ntt.fwd.cluster", st, set_limbs(out) * (double)(t.n / 2) * 16);
     k_ntt16_cluster<INV, MINB><<<grid, 512, smem, st>>>(t, in, out);
@@ -667,11 +659,8 @@ static void launch_pass(const DevTables& t, const PolySet& in, const PolySet& ou
     constexpr int TPS = 1 << (S - 4);
     constexpr int SUB = (1 << S) + (1 << (S - 4));
     const size_t smem = (size_t)C * SUB * sizeof(u64);
-    static bool attr_set = false;  // per template instance
-    if (!attr_set) {
+    if (first_on_device((const void*)&k_ntt_pass<S, C, INV>))
         PFT_CUDA(cudaFuncSetAttribute(k_ntt_pass<S, C, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
     const int logT = t.logn - s0 - S;
     dim3 grid((unsigned)((t.n >> S) / C), (unsigned)out.max_limbs, (unsigned)out.count);
     PFT_PROF(INV ? (logT > 0 ? "ntt.inv.strided" : "ntt.inv.contig") : (logT > 0 ? "ntt.fwd.strided" : "ntt.fwd.contig"),

@@ -73,6 +73,9 @@ struct Error {
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 #define PFT_CUDA(x) ::pft::check_cuda((x), #x)
+// True on the first call for (key, current device), false afterwards: kernel attributes
+// (shared-memory size, carveout) are per device, so each device sets them once.
+bool first_on_device(const void* key);
 #define PFT_LAUNCH_CHECK(what) ::pft::check_cuda(cudaGetLastError(), what)
 
 // Launch accounting: every kernel launch is counted; launches whose name starts

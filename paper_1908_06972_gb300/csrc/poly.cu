@@ -956,13 +956,12 @@ void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const KeyRef
             const int sd = beta_max <= 4 ? 4 : 8;
             dim3 gb((unsigned)(t.n / kKsChunk), (unsigned)(L + k));
             const size_t smem = (size_t)kKsStages * sd * kKsChunk * 8;
-            static bool attr = false;  // the 8-digit ring needs 48 KiB of dynamic shared memory
-            if (!attr) {
+            // the 8-digit ring needs 48 KiB of dynamic shared memory
+            if (first_on_device((const void*)&k_ks_inner_bulk<8>)) {
                 PFT_CUDA(cudaFuncSetAttribute(k_ks_inner_bulk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)((size_t)kKsStages * 8 * kKsChunk * 8)));
                 PFT_CUDA(cudaFuncSetAttribute(k_ks_inner_bulk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)((size_t)kKsStages * 8 * kKsChunk * 8)));
-                attr = true;
             }
             if (sd == 4) k_ks_inner_bulk<4><<<gb, 128, smem, st>>>(t, bt, cnt, key, L, k, alpha, sd);
             else k_ks_inner_bulk<8><<<gb, 128, smem, st>>>(t, bt, cnt, key, L, k, alpha, sd);

@@ -178,7 +178,7 @@ void fwd_tile(pft_ctx* c, pft_ft_tape& T, const pft_ct* const* w, int b0, int b1
     for (pft_ct* x : ux) x->scale = 8.0 * x->scale;
     op_const_batch(c, ux.data(), (int)ux.size(), -0.5, 0.0, false, ux.data());
     for (size_t i = 0; i < ws.size(); i++) {
-        check_ct(ws[i]);
+        check_ct(c, ws[i]);
         NEED(ws[i]->level == ux[i]->level, PFT_ERR_LEVEL_MISMATCH,
              "labels must be encrypted at the level pft_fasttext_train_spec gives");
         NEED(ws[i]->scale == ux[i]->scale, PFT_ERR_SCALE_MISMATCH,
@@ -300,7 +300,7 @@ void sgd(pft_ctx* c, std::vector<pft_ct>& X, const pft_ct* const* dX, int n, dou
     const int l = dX[0]->level;
     const double sc = dX[0]->scale, target = X[0].scale;
     for (int j = 0; j < n; j++) {
-        check_ct(dX[j]);
+        check_ct(c, dX[j]);
         NEED(dX[j]->level == l && dX[j]->scale == sc, PFT_ERR_SCALE_MISMATCH, "gradients differ in level or scale");
     }
     NEED(l >= 2, PFT_ERR_LEVEL_MISMATCH, "no level left for the update");
@@ -448,7 +448,7 @@ void fwd_tile_diag(pft_ctx* c, pft_ft_tape& T, const pft_ct* const* w, int b0, i
     for (pft_ct* x : ux) x->scale = 8.0 * x->scale;
     op_const_batch(c, ux.data(), nb, -0.5, 0.0, false, ux.data());
     for (int i = 0; i < nb; i++) {
-        check_ct(ws[i]);
+        check_ct(c, ws[i]);
         NEED(ws[i]->level == ux[i]->level, PFT_ERR_LEVEL_MISMATCH,
              "labels must be encrypted at the level pft_fasttext_train_spec gives");
         NEED(ws[i]->scale == ux[i]->scale, PFT_ERR_SCALE_MISMATCH,
@@ -534,8 +534,8 @@ void check_batch(pft_ctx* c, const pft_ft_enc_model* M, const pft_ct* const* doc
     for (int st : steps)
         NEED(c->keys.count(galois_of(c->n, st)), PFT_ERR_NO_KEY, "missing rotation key for step " + std::to_string(st));
     for (int b = 0; b < B; b++) {
-        check_ct(docs[b]);
-        check_ct(labels[b]);
+        check_ct(c, docs[b]);
+        check_ct(c, labels[b]);
         NEED(docs[b]->level == l0, PFT_ERR_LEVEL_MISMATCH, "documents must sit at the model level");
         NEED(docs[b]->scale == docs[0]->scale, PFT_ERR_SCALE_MISMATCH, "documents differ in scale");
     }
@@ -592,8 +592,8 @@ int pft_ft_enc_model_create(pft_ctx* c, const pft_ct* const* H, const pft_ct* co
         M->n = n;
         M->c = cl;
         for (int j = 0; j < n; j++) {
-            check_ct(H[j]);
-            check_ct(O[j]);
+            check_ct(c, H[j]);
+            check_ct(c, O[j]);
             NEED(H[j]->level == H[0]->level && H[j]->scale == H[0]->scale, PFT_ERR_LEVEL_MISMATCH,
                  "embedding ciphertexts differ in level or scale");
             NEED(O[j]->level == H[0]->level - 1 && O[j]->scale == O[0]->scale, PFT_ERR_LEVEL_MISMATCH,
@@ -619,8 +619,8 @@ int pft_ft_enc_model_create_diag(pft_ctx* c, const pft_ct* const* D, const pft_c
         const int t = c->n / 2;
         NEED(m <= t && (n & (n - 1)) == 0 && t % n == 0 && (size_t)n * cl <= (size_t)t, PFT_ERR_ARG,
              "the diagonal layout needs m <= t, n a power of two dividing t and n c <= t");
-        check_ct(P);
-        check_pt(mask);
+        check_ct(c, P);
+        check_pt(c, mask);
         std::unique_ptr<pft_ft_enc_model> M(new pft_ft_enc_model());
         M->ctx = c;
         M->m = m;
@@ -629,7 +629,7 @@ int pft_ft_enc_model_create_diag(pft_ctx* c, const pft_ct* const* D, const pft_c
         M->variant = 1;
         M->lift = lift_bits;
         for (int k = 0; k < n; k++) {
-            check_ct(D[k]);
+            check_ct(c, D[k]);
             NEED(D[k]->level == D[0]->level && D[k]->scale == D[0]->scale, PFT_ERR_LEVEL_MISMATCH,
                  "diagonal ciphertexts differ in level or scale");
         }

@@ -42,3 +42,9 @@ def documents(seed, m, count, w_min=20, w_max=200, a=1.1):
         ids = rng.choice(m, size=w, p=p)
         out[d] = np.bincount(ids, minlength=m) / w
     return out
+
+
+def batch_levels(count=64, lo=5, hi=30, seed=20241203):
+    """Levels of a batch of ciphertexts, uniform in [lo, hi] (the mixed-level batch workload)."""
+    rng = np.random.default_rng(seed)
+    return [int(x) for x in rng.integers(lo, hi + 1, count)]

@@ -41,6 +41,33 @@ def test_rescale_noalloc_matches_rescale(gpu):
             for h in (ct, ref):
                 pft.pft_ct_destroy(h)
             pft.pft_pt_destroy(pt)
+        # input and output may not overlap
+        pt = pft.pft_encode(ctx, synth.slots(70, 64), 2.0 ** 50, 4)
+        ct = pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, 600)
+        p_in = pft.pft_ct_data(ct)
+        with pytest.raises(pft.PftError) as e:
+            pft.pft_rescale_noalloc(ctx, p_in, 4, p_in + 8 * n)
+        assert e.value.code == pft.PFT_ERR_ARG and "overlap" in str(e.value)
+        pft.pft_ct_destroy(ct)
+        pft.pft_pt_destroy(pt)
+        # the largest accepted size fills the array exactly: 2 N level = 4 Mi words at level 32
+        top = pft.pft_ctx_create(16, 32, 2, 4, 60, 40, 60, 2.0 ** 40, (3, 3, 3, 3))
+        try:
+            pt = pft.pft_encode(top, synth.slots(71, 1024), 2.0 ** 40, 32)
+            ct = pft.pft_encrypt(top, pt, pft.PFT_ENC_SK, 700)
+            out = torch.empty((2, 31, n), dtype=torch.int64, device="cuda")
+            pft.pft_rescale_noalloc(top, pft.pft_ct_data(ct), 32, out.data_ptr())
+            ref = pft.pft_ct_create(top)
+            pft.pft_rescale(top, ct, ref)
+            want = pft.pft_ct_export(top, ref)
+            pft.pft_ntt(top, out.data_ptr(), 2, 31, 1)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy().view(np.uint64), want), "level 32 differs"
+            for h in (ct, ref):
+                pft.pft_ct_destroy(h)
+            pft.pft_pt_destroy(pt)
+        finally:
+            pft.pft_ctx_destroy(top)
         # sizes beyond the fixed array are refused with a clear error
         big = pft.pft_ctx_create(16, 40, 2, 4, 60, 40, 60, 2.0 ** 40, (1, 1, 1, 1), flags=pft.PFT_ALLOW_INSECURE)
         try:
