@@ -39,14 +39,20 @@ SEED = (0x5EED0001, 0x5EED0002, 0x5EED0003, 0x5EED0004)
 WORKLOAD = ("N=2^16, 30 limbs (60 + 29x50 bits) + 4 special (60 bits), digits of 4 primes; "
             "batch 64 ciphertexts at levels U{5..30}; per ciphertext mul_relin then 16 chained "
             "rotations (2^0..2^14, -1)")
-# ALU roofline: 152 SMs x 64 32-bit IMAD per SM per clock x 2.07 GHz, at 9 IMAD per 64-bit
-# Shoup butterfly multiply with an estimated quotient (3 for the quotient, 3 for each of the
-# two low halves).
+# Nominal integer figures (context only; the reported bound uses the measured multiply rates):
+# 152 SMs x 64 32-bit IMAD per SM per clock x 2.07 GHz, 9 IMAD per Shoup butterfly.
 SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 9
 # DRAM bytes (read + written) per limb and pass of the N = 2^16 transform kernels: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum over the four two-pass launches of the
 # 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes.
 NTT_DRAM_BYTES_PER_LIMB_PASS = 1.0121e6
+NTT16_VARIANTS = ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"]
+
+
+def alu_bound(lo, hi):
+    """Butterflies/s the integer multiply pipe allows: each butterfly (a Shoup product with the
+    estimated quotient) issues 5 multiplies that produce a high word and 4 low-word ones."""
+    return 1.0 / (5.0 / hi + 4.0 / lo)
 
 
 def levels():
@@ -150,6 +156,7 @@ def run_gpu(args):
                              flags=pft.PFT_COMPRESSED_KEYS if args.compressed_keys else 0)
     tuned, tune_us = pft.pft_autotune(ctx)
     bfly_ceiling = pft.pft_bfly_ceiling(ctx) / 1e9  # G butterflies/s of the butterfly on register data
+    mul_lo, mul_hi, mul_wide = pft.pft_mul_rates(ctx)  # measured 32-bit multiply issue rates
     pft.pft_keygen(ctx, STEPS_ROT, True)
     lv = levels()
     n = 1 << LOGN
@@ -308,7 +315,7 @@ def run_gpu(args):
     clk_med = clk.summary().get("sm_mhz")  # median SM clock sampled during the timed region
     if k_ms > 0 and args.roofline_kernel.startswith("ntt"):
         achieved = k_work / (k_ms / 1e3) / 1e9  # Gbutterfly/s (one Shoup mulmod each)
-        peak = SMS * IMAD_PER_CLK * SM_MHZ_MAX * 1e6 / IMAD_PER_MULMOD / 1e9
+        peak = alu_bound(mul_lo, min(mul_hi, mul_wide)) / 1e9
         limb_passes = k_work / max(1, k_launches) / ((1 << LOGN) // 2 * 8)
         roof = {"bound": "alu", "kernel": args.roofline_kernel, "achieved": round(achieved, 2),
                 "peak": round(peak, 2), "unit": "Gmulmod/s", "frac": round(achieved / peak, 4),
@@ -318,8 +325,13 @@ def run_gpu(args):
                                   "times the mean limb-passes per launch in the step",
                 "launches": k_launches, "kernel_ms": round(k_ms, 3),
                 "kernel_share_of_step": round(k_ms / ms, 4),
-                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 9 IMAD per Shoup mulmod "
-                               "(estimated quotient)",
+                "peak_source": "derived from the multiply issue rates measured live (pft_mul_rates): "
+                               "1 / (5 / high-word rate + 4 / low-word rate) butterflies/s; a butterfly is "
+                               "5 multiplies producing a high word and 4 low-word multiply-adds",
+                "mul_rates_per_sm_clk": {"lo": round(mul_lo / SMS / (SM_MHZ_MAX * 1e6), 1),
+                                         "hi": round(mul_hi / SMS / (SM_MHZ_MAX * 1e6), 1),
+                                         "wide": round(mul_wide / SMS / (SM_MHZ_MAX * 1e6), 1)},
+                "peak_nominal_64imad": round(SMS * IMAD_PER_CLK * SM_MHZ_MAX * 1e6 / IMAD_PER_MULMOD / 1e9, 1),
                 "arith_ceiling": round(bfly_ceiling, 1), "frac_of_arith_ceiling": round(achieved / bfly_ceiling, 4),
                 "peak_at_median_clock": round(peak * clk_med / SM_MHZ_MAX, 2) if clk_med else None,
                 "frac_at_median_clock": round(achieved / (peak * clk_med / SM_MHZ_MAX), 4) if clk_med else None,
@@ -371,8 +383,8 @@ def run_gpu(args):
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "split": e2e_split},
            "gpu_launches": int(all_launches), "roofline": roof,
-           "autotune": {"ntt16_variant": ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"][tuned],
-                        "us_fwd_inv_2x32limbs": [round(x, 1) for x in tune_us[:4]]}, "cpu_baseline": cpu, "clocks": clk.summary(),
+           "autotune": {"ntt16_variant": NTT16_VARIANTS[tuned],
+                        "us_fwd_inv_2x32limbs": dict(zip(NTT16_VARIANTS, [round(x, 1) for x in tune_us]))}, "cpu_baseline": cpu, "clocks": clk.summary(),
            "fasttext": ft, "serving": sv, "training": tr, "job_queue": qu, "ops": ops}
     if rank == 0:
         print(json.dumps(out))
@@ -1033,7 +1045,8 @@ def run_case_ntt(args):
     inv_ms, inv_n, _, inv_work = pft.pft_prof_stop()
     torch.cuda.synchronize()
     ok = bool(np.array_equal(t.cpu().numpy().view(np.uint64), host))
-    peak = SMS * IMAD_PER_CLK * SM_MHZ_MAX * 1e6 / IMAD_PER_MULMOD
+    lo, hi, wide = pft.pft_mul_rates(ctx)
+    peak = alu_bound(lo, min(hi, wide))
     bytes_per_pass = polys * L * n * 8 * 2
     res = {"case": "ntt", "polys": polys, "limbs": L, "N": n, "round_trip_exact": ok,
            "fwd_us_per_pass": round(1e3 * fwd_ms / fwd_n, 2), "inv_us_per_pass": round(1e3 * inv_ms / inv_n, 2),

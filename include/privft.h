@@ -258,6 +258,14 @@ int pft_wait_selftest(pft_ctx* ctx, long long polls);
  * per SM, timed with CUDA events on the context's stream (synchronous; about 20 ms).
  * *out: butterflies per second. */
 int pft_bfly_ceiling(pft_ctx* ctx, double* out);
+/* Issue rates of the 32-bit integer multiply forms a butterfly is made of, in operations per
+ * second over the whole GPU, timed with CUDA events on the context's stream (synchronous; about
+ * 10 ms): lo = low-word multiply-add (mad.lo), hi = high-word multiply (mul.hi / mad.hi),
+ * wide = widening multiply (mad.wide).  A butterfly (one Shoup product with the estimated
+ * quotient) takes 5 multiplies that produce a high word and 4 low-word multiply-adds, so the
+ * transforms' arithmetic bound is 1 / (5 / min(hi, wide) + 4 / lo) butterflies per second.
+ * Any pointer may be NULL. */
+int pft_mul_rates(pft_ctx* ctx, double* lo, double* hi, double* wide);
 
 /* ---- persistent job queue (batching over uneven levels and ring sizes) -----
  * HADD, subtraction and HMULPLAIN (Sec. 2.3) for ciphertexts of any contexts (rings of
@@ -335,8 +343,9 @@ int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, 
  * `cap` per-variant times in microseconds, chosen the selected index.  Other ring degrees
  * have a single variant.  The environment variable PFT_NTT16 (twopass, twopass4, cluster,
  * generic) overrides the choice. */
+#define PFT_NTT16_VARIANTS 4
 int pft_autotune(pft_ctx* ctx, double* us_out, int cap, int* chosen);
-/* Pin the N = 2^16 transform variant (0..3 in the order above) without timing. */
+/* Pin the N = 2^16 transform variant (0..PFT_NTT16_VARIANTS-1 in the order above) without timing. */
 int pft_set_transform_variant(pft_ctx* ctx, int variant);
 
 /* ---- CUDA graphs of batched operations ------------------------------------

@@ -23,6 +23,7 @@ PFT_ERR_OOM, PFT_ERR_CUDA, PFT_ERR_TIMEOUT, PFT_ERR_SECURITY, PFT_ERR_NOT_IMPLEM
 PFT_ALLOW_INSECURE = 1
 PFT_COMPRESSED_KEYS = 2
 PFT_ENC_PK, PFT_ENC_SK = 0, 1
+PFT_NTT16_VARIANTS = 4  # N = 2^16 transform variants (pft_autotune, pft_set_transform_variant)
 
 
 class NativeLibraryMissing(RuntimeError):
@@ -111,6 +112,7 @@ def lib():
             "pft_drop_level": [vp, vp, i, vp], "pft_add_const": [vp, vp, d, vp],
             "pft_device_status": [vp], "pft_wait_selftest": [vp, ctypes.c_longlong],
             "pft_run_jobs": [vp, POINTER(pft_job), i, c_double], "pft_bfly_ceiling": [vp, POINTER(c_double)],
+            "pft_mul_rates": [vp, POINTER(c_double), POINTER(c_double), POINTER(c_double)],
             "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
@@ -174,7 +176,7 @@ def exported_symbols():
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
             "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag",
-            "pft_run_jobs", "pft_bfly_ceiling", "pft_ct_import_batch_into"]
+            "pft_run_jobs", "pft_bfly_ceiling", "pft_ct_import_batch_into", "pft_mul_rates"]
 
 
 def _check(rc, ctx=None):
@@ -492,6 +494,13 @@ def pft_device_status(ctx):
 
 def pft_wait_selftest(ctx, polls):
     _check(lib().pft_wait_selftest(ctx, int(polls)), ctx)
+
+
+def pft_mul_rates(ctx):
+    """Measured 32-bit multiply issue rates (ops/s, whole GPU): (low-word, high-word, widening)."""
+    lo, hi, wide = c_double(), c_double(), c_double()
+    _check(lib().pft_mul_rates(ctx, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(wide)), ctx)
+    return lo.value, hi.value, wide.value
 
 
 def pft_bfly_ceiling(ctx):

@@ -1884,6 +1884,12 @@ int pft_bfly_ceiling(pft_ctx* c, double* out) {
     });
 }
 
+int pft_mul_rates(pft_ctx* c, double* lo, double* hi, double* wide) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "null context");
+        mul_rates(c->stream, lo, hi, wide);
+    });
+}
 int pft_wait_selftest(pft_ctx* c, long long polls) {
     return guard(c, [&] {
         NEED(c && polls >= 1 && polls <= (1ll << 20), PFT_ERR_ARG, "polls must lie in 1..2^20");

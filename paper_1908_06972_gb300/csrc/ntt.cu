@@ -18,6 +18,8 @@
 // N = 2^15, 2^16: two passes (8 + 7 or 8 + 8 stages).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include <cstdlib>
 #include <cstring>
 
@@ -41,6 +43,40 @@ __device__ __forceinline__ u64 mulhi_est(u64 x, u64 w) {
     const uint32_t wl = (uint32_t)w, wh = (uint32_t)(w >> 32);
     return (u64)xh * wh + ((u64)__umulhi(xh, wl) + __umulhi(xl, wh));
 }
+// y w - q_est q (mod 2^64) with q_est = mulhi_est(y, w'), written as 32-bit multiply-adds with
+// explicit carries: the quotient takes two high-word products and one widening product (the
+// partial sums hi(yh w'l) + hi(yl w'h) enter the widening product as its 64-bit addend), the
+// low 64 bits of y w + q_est (-q) take two widening products and four low-word multiply-adds.
+// The same value as y * w + mulhi_est(y, w') * nq in 64-bit C arithmetic, in fewer
+// instructions than the compiler forms from that expression.  nq = -q mod 2^64.
+__device__ __forceinline__ u64 shoup_est(u64 y, u64 w, u64 wp, u64 nq) {
+    u64 T;
+    asm("{\n\t"
+        ".reg .u32 yl, yh, pl, ph, t, r, c, wl, wh, ql, qh, nl, nh, tl, th;\n\t"
+        ".reg .u64 Q, A;\n\t"
+        "mov.b64 {yl, yh}, %1;\n\t"
+        "mov.b64 {pl, ph}, %3;\n\t"
+        "mul.hi.u32 t, yh, pl;\n\t"
+        "mad.hi.cc.u32 r, yl, ph, t;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "mov.b64 A, {r, c};\n\t"
+        "mad.wide.u32 Q, yh, ph, A;\n\t"
+        "mov.b64 {wl, wh}, %2;\n\t"
+        "mov.b64 {ql, qh}, Q;\n\t"
+        "mov.b64 {nl, nh}, %4;\n\t"
+        "mul.wide.u32 A, yl, wl;\n\t"
+        "mad.wide.u32 A, ql, nl, A;\n\t"
+        "mov.b64 {tl, th}, A;\n\t"
+        "mad.lo.u32 th, yl, wh, th;\n\t"
+        "mad.lo.u32 th, yh, wl, th;\n\t"
+        "mad.lo.u32 th, ql, nh, th;\n\t"
+        "mad.lo.u32 th, qh, nl, th;\n\t"
+        "mov.b64 %0, {tl, th};\n\t"
+        "}"
+        : "=l"(T)
+        : "l"(y), "l"(w), "l"(wp), "l"(nq));
+    return T;
+}
 // Cooley-Tukey (Harvey) with the estimated quotient, so WY lies in [0, 4q):
 // X, Y in [0, 8q) -> X + WY, X - WY in [0, 8q) (X corrected below 4q; primes below 2^61).
 // LAZY (primes below 2^57): no correction of X, values grow by less than 4q per stage: the
@@ -49,7 +85,7 @@ template <bool LAZY = false>
 __device__ __forceinline__ void ct_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64 q2) {
     const u64 q4 = 2 * q2;
     if (!LAZY && X >= q4) X -= q4;
-    const u64 T = Y * W.x + mulhi_est(Y, W.y) * (0 - q);
+    const u64 T = shoup_est(Y, W.x, W.y, 0 - q);
     Y = X - T + q4;
     X = X + T;
 }
@@ -61,7 +97,7 @@ __device__ __forceinline__ void gs_bfly(u64& X, u64& Y, ulonglong2 W, u64 q, u64
     if (S >= q4) S -= q4;
     const u64 D = X - Y + q4;
     X = S;
-    Y = D * W.x + mulhi_est(D, W.y) * (0 - q);
+    Y = shoup_est(D, W.x, W.y, 0 - q);
 }
 __device__ __forceinline__ u64 canon4(u64 v, u64 q, u64 q2) {
     if (v >= q2) v -= q2;
@@ -99,8 +135,9 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
             if (e & (1 << lb)) continue;
             const int elem = (e << W0) | wpart;
             const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
+            const ulonglong2 W = __ldg(&tw[idx]);
             if (!INV) {
-                ct_bfly<LAZY>(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
+                ct_bfly<LAZY>(x[e], x[e | (1 << lb)], W, q, q2);
             } else if (s == 0 && !UNSCALED) {  // last inverse stage: N^-1 folded into both outputs
                 u64 S = x[e] + x[e | (1 << lb)];
                 if (S >= 2 * q2) S -= 2 * q2;
@@ -108,11 +145,12 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
                 x[e] = mul_shoup_lazy(S, NI.x, NI.y, q);
                 x[e | (1 << lb)] = mul_shoup_lazy(D, NI1.x, NI1.y, q);
             } else {
-                gs_bfly(x[e], x[e | (1 << lb)], __ldg(&tw[idx]), q, q2);
+                gs_bfly(x[e], x[e | (1 << lb)], W, q, q2);
             }
         }
     }
 }
+
 
 constexpr int kN16Stride = 33;  // shared layout [256][33]: element (a, lane) at a * 33 + lane
 
@@ -401,18 +439,24 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, Poly
 }
 
 template <int MINB>
+static void prepare_twopass(void) {
+    if (MINB == 4 && first_on_device((const void*)&k_ntt8_contig_epi<MINB>)) {
+        // four CTAs of 35 KB shared memory: a carveout that fits them, the rest L1
+        const int co = 64;
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<false, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB, true>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<false, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<true, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig_epi<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+    }
+}
+
+template <int MINB>
 static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
                                    cudaStream_t st) {
-    if (MINB == 4) {  // four CTAs of 35 KB shared memory: a carveout that fits them, the rest L1
-        if (first_on_device((const void*)&k_ntt8_contig_epi<MINB>)) {
-            const int co = 64;
-            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<false, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<false, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<true, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig_epi<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-        }
-    }
+    prepare_twopass<MINB>();
     dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);  // 256 sub-transforms / 16 per CTA
     const double work = set_limbs(out) * (double)(t.n / 2) * 8;
     if (!inverse) {
@@ -440,20 +484,17 @@ static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const 
     }
 }
 
-static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse, int minb,
+// variant 0: 3 CTAs per SM; 1: 4 CTAs per SM
+static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse, int v16,
                                  cudaStream_t st) {
-    if (minb == 4) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
+    if (v16 == 1) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
     else launch_ntt16_twopass_v<3>(t, in, out, inverse, st);
 }
 
 template <int MINB>
 static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& in, const PolySet& out,
                                             cudaStream_t st) {
-    if (MINB == 4) {  // the same carveout as the scaled kernels of this variant
-        if (first_on_device((const void*)&k_ntt8_strided<true, 8, MINB, true>))
-            PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB, true>,
-                                          cudaFuncAttributePreferredSharedMemoryCarveout, 64));
-    }
+    prepare_twopass<MINB>();
     dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);
     const double work = set_limbs(out) * (double)(t.n / 2) * 8;
     {
@@ -470,6 +511,7 @@ static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& i
 
 template <int MINB>
 static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {
+    prepare_twopass<MINB>();
     dim3 grid(16, (unsigned)io.max_limbs, (unsigned)io.count);
     const double work = set_limbs(io) * (double)(t.n / 2) * 8;
     {
@@ -696,7 +738,7 @@ static void run(const DevTables& t, const PolySet& in, const PolySet& out, bool 
     }
     const int v16 = t.logn == 16 ? ntt16_variant(t) : -1;
     if (v16 == 0 || v16 == 1) {
-        launch_ntt16_twopass(t, in, out, inverse, v16 == 1 ? 4 : 3, st);
+        launch_ntt16_twopass(t, in, out, inverse, v16, st);
     } else if (v16 == 2) {
         if (!inverse) launch_ntt16_cluster<false>(t, in, out, st);
         else launch_ntt16_cluster<true>(t, in, out, st);
@@ -779,6 +821,60 @@ double bfly_ceiling(const DevTables& t, cudaStream_t st) {
     PFT_CUDA(cudaEventDestroy(b));
     PFT_CUDA(cudaFree(sink));
     return best;
+}
+
+// Issue rates of the two forms of 32-bit integer multiply the butterflies use: the low-word
+// multiply-add (mad.lo) and the forms that produce a high word (mad.hi, mad.wide).  Each thread
+// runs 8 independent chains of one form; the result word is written only for a value the
+// chains cannot reach, which keeps the work.
+template <int FORM>
+__global__ void __launch_bounds__(256) k_mul_rate(u32* sink, u32 a, u32 b, int rounds) {
+    u32 x[8];
+    u64 y[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        x[i] = threadIdx.x * 8 + i + blockIdx.x;
+        y[i] = x[i];
+    }
+    for (int k = 0; k < rounds; k++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            if (FORM == 0) x[i] = x[i] * a + b;
+            if (FORM == 1) x[i] = __umulhi(x[i], a) + b;
+            if (FORM == 2) y[i] = (u64)(u32)y[i] * a + y[i];
+        }
+    }
+    u32 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc ^= x[i] ^ (u32)y[i] ^ (u32)(y[i] >> 32);
+    if (acc == 0x9e3779b9u) sink[0] = acc;
+}
+
+void mul_rates(cudaStream_t st, double* lo, double* hi, double* wide) {
+    int dev = 0, sms = 0;
+    PFT_CUDA(cudaGetDevice(&dev));
+    PFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    u32* sink = nullptr;
+    PFT_CUDA(cudaMalloc(&sink, 64));
+    cudaEvent_t a, b;
+    PFT_CUDA(cudaEventCreate(&a));
+    PFT_CUDA(cudaEventCreate(&b));
+    const int grid = sms * 8, rounds = 8000;
+    double* outs[3] = {lo, hi, wide};
+    for (int form = 0; form < 3; form++) {
+        auto kern = form == 0 ? k_mul_rate<0> : form == 1 ? k_mul_rate<1> : k_mul_rate<2>;
+        kern<<<grid, 256, 0, st>>>(sink, 3, 5, 16);  // warm-up
+        PFT_CUDA(cudaEventRecord(a, st));
+        kern<<<grid, 256, 0, st>>>(sink, 3, 5, rounds);
+        PFT_CUDA(cudaEventRecord(b, st));
+        PFT_CUDA(cudaEventSynchronize(b));
+        float ms = 0;
+        PFT_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (outs[form]) *outs[form] = (double)grid * 256 * rounds * 8 / (ms / 1e3);
+    }
+    PFT_CUDA(cudaEventDestroy(a));
+    PFT_CUDA(cudaEventDestroy(b));
+    PFT_CUDA(cudaFree(sink));
 }
 
 bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {

@@ -117,6 +117,9 @@ bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& 
 // Butterflies per second of the transform's (exact-path) butterfly arithmetic on register data
 // only: the arithmetic ceiling the transforms are measured against (synchronous).
 double bfly_ceiling(const DevTables& t, cudaStream_t st);
+// Measured issue rates (operations per second, whole GPU) of the 32-bit multiply forms the
+// butterflies use: low-word multiply-add, high-word multiply, widening multiply (synchronous).
+void mul_rates(cudaStream_t st, double* lo, double* hi, double* wide);
 void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
 
 enum class EwOp { Add, Sub, Mul, Neg, Copy };

@@ -37,7 +37,7 @@ def test_transform_extreme_inputs(gpu, logn, bits):
         idx = np.arange(n) if logn <= 11 else np.r_[0:32, n // 2 - 16:n // 2 + 16, n - 32:n]
         want = [[OC.eval_at(x[poly, r], OP.root_2n(q, logn), q, logn, idx) for r, q in enumerate(primes)]
                 for poly in range(3)]
-        for variant in range(4) if logn == 16 else [None]:  # every N = 2^16 kernel variant
+        for variant in range(gpu.PFT_NTT16_VARIANTS) if logn == 16 else [None]:  # every N = 2^16 kernel variant
             if variant is not None:
                 gpu.pft_set_transform_variant(p.ctx, variant)
             t = torch.from_numpy(x.view(np.int64).copy()).cuda()

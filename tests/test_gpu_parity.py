@@ -352,12 +352,13 @@ def test_every_transform_variant_bit_exact(p16):
     """pft_autotune picks among the N = 2^16 transform variants; each one gives the same bits."""
     o, pf, ctx = p16.orc, p16.pft, p16.ctx
     chosen, us = pf.pft_autotune(ctx)
-    assert 0 <= chosen < 4 and all(u > 0 for u in us[:4])
+    nv = pf.PFT_NTT16_VARIANTS
+    assert 0 <= chosen < nv and all(u > 0 for u in us[:nv])
     a = o.encrypt_sk(o.encode(synth.slots(31, 512), level=6), 41)
     b = o.encrypt_sk(o.encode(synth.slots(32, 512), level=6), 42)
     want = o.mul_relin(a, b)
     ga, gb = p16.ct(a), p16.ct(b)
-    for v in range(4):
+    for v in range(nv):
         pf.pft_set_transform_variant(ctx, v)
         m = p16.empty()
         pf.pft_mul_relin(ctx, ga, gb, m)

@@ -53,6 +53,7 @@ def test_rescale_noalloc_matches_rescale(gpu):
         # the largest accepted size fills the array exactly: 2 N level = 4 Mi words at level 32
         top = pft.pft_ctx_create(16, 32, 2, 4, 60, 40, 60, 2.0 ** 40, (3, 3, 3, 3))
         try:
+            pft.pft_keygen(top, [], False)
             pt = pft.pft_encode(top, synth.slots(71, 1024), 2.0 ** 40, 32)
             ct = pft.pft_encrypt(top, pt, pft.PFT_ENC_SK, 700)
             out = torch.empty((2, 31, n), dtype=torch.int64, device="cuda")
