@@ -116,6 +116,22 @@ static void build_tables(pft_ctx* c) {
     }
     c->tabs.fwd = tab_upload(c, fwd);
     c->tabs.inv = tab_upload(c, inv);
+    c->tabs.fwd_rows = c->tabs.inv_rows = nullptr;
+    if (logn == 16) {  // lane-major copy of the twiddles of stages 12..15 (row passes)
+        std::vector<ulonglong2> fr((size_t)P * 256 * 240), ir((size_t)P * 256 * 240);
+        for (int i = 0; i < P; i++)
+            for (int u = 0; u < 256; u++)
+                for (int kk = 0; kk < 4; kk++)
+                    for (int j = 0; j < (1 << kk); j++)
+                        for (int w = 0; w < 16; w++) {
+                            const size_t src = (size_t)i * n + (1u << (12 + kk)) + ((size_t)u << (4 + kk)) + (w << kk) + j;
+                            const size_t dst = (((size_t)i * 256 + u) * 15 + ((1 << kk) - 1 + j)) * 16 + w;
+                            fr[dst] = fwd[src];
+                            ir[dst] = inv[src];
+                        }
+        c->tabs.fwd_rows = tab_upload(c, fr);
+        c->tabs.inv_rows = tab_upload(c, ir);
+    }
     c->tabs.ninv = tab_upload(c, ninv);
     c->tabs.inv1ninv = tab_upload(c, inv1);
 

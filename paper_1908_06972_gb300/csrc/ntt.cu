@@ -122,9 +122,14 @@ __device__ __forceinline__ u64 canon8(u64 v, u64 q, u64 q2) {
 // One round = four stages on 16 registers: register e holds element (e << W0) | wpart of
 // the current 256-point sub-transform; DIMHI = 0 for column stages (s = 7 - p), 8 for row
 // stages (s = 15 - p, r = the row being transformed).
-template <bool INV, int W0, int DIMHI, bool LAZY = false, bool UNSCALED = false>
+// LM (the row round W0 = 0 of stages 12..15, thread = row r, lane w): the twiddles come from
+// the lane-major copy of that round's twiddles, lm = its entries for (prime, row r, lane w):
+// slot (2^k - 1 + j) of stage 12 + k at lm[16 (2^k - 1 + j)].
+template <bool INV, int W0, int DIMHI, bool LAZY = false, bool UNSCALED = false, bool LM = false>
 __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, const ulonglong2* __restrict__ tw,
-                                            u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1) {
+                                            u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1,
+                                            const ulonglong2* __restrict__ lm = nullptr) {
+    static_assert(!LM || (W0 == 0 && DIMHI == 8), "lane-major twiddles serve the row round of stages 12..15");
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int lb = INV ? k : 3 - k;
@@ -135,7 +140,7 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
             if (e & (1 << lb)) continue;
             const int elem = (e << W0) | wpart;
             const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
-            const ulonglong2 W = __ldg(&tw[idx]);
+            const ulonglong2 W = LM ? __ldg(&lm[16 * ((1 << (s - 12)) - 1 + (e >> (p + 1)))]) : __ldg(&tw[idx]);
             if (!INV) {
                 ct_bfly<LAZY>(x[e], x[e | (1 << lb)], W, q, q2);
             } else if (s == 0 && !UNSCALED) {  // last inverse stage: N^-1 folded into both outputs
@@ -319,9 +324,21 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet
     }
 }
 
+// ---- lane-major copy of the twiddles of stages 12..15 ---------------------------------------
+// In the round of stages 12..15 of a row pass, thread (row u, lane w) uses the 15 twiddles
+// 2^(12+k) + u 2^(4+k) + w 2^k + j (k < 4, j < 2^k): row- and lane-specific, each read once.
+// Read from the natural table, one warp load touches 32 cache lines for 16 bytes each.  The
+// lane-major copy holds, per prime and row, [15 slots][16 lanes] (slot 2^k - 1 + j), so the 16
+// lanes of a row read 256 contiguous bytes per load.
+constexpr int kRowTwSlots = 15;
+__device__ __forceinline__ const ulonglong2* lm_base(const ulonglong2* rows, int pi, int u, int w) {
+    return rows + ((size_t)pi * 256 + u) * (kRowTwSlots * 16) + w;
+}
+
 // Forward stages 8..15 of the 16 rows of this CTA (limb `limb` of prime pi, rows read from
 // src): canonical results are left in sm, row c2 point m at c2 * kRowStride + m + (m >> 4),
 // after a barrier.
+template <bool LM = false>
 __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* __restrict__ src, int pi, u64* sm) {
     const int logn = t.logn;
     const int w = threadIdx.x & 15, cc = threadIdx.x >> 4;
@@ -330,6 +347,7 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
     const u64 q2 = 2 * q;
     const ulonglong2* tw = t.fwd + ((size_t)pi << logn);
     const ulonglong2 NI = make_ulonglong2(0, 0);
+    const ulonglong2* lm = LM ? lm_base(t.fwd_rows, pi, u, w) : nullptr;
     u64* my = sm + cc * kRowStride;
     u64 x[16];
     const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
@@ -343,7 +361,7 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
 #pragma unroll
     for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
     if (lazy) {
-        ntt16_round<false, 0, 8, true>(x, w << 4, u, tw, q, q2, NI, NI);
+        ntt16_round<false, 0, 8, true, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm);
         // values below 66q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
         // (mu = floor(2^(64+s) / q)), then one correction
         const u64 one_p = __ldg(&t.primes[pi].mu) >> __ldg(&t.primes[pi].s);
@@ -353,14 +371,14 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
             my[w * 17 + e] = r >= q ? r - q : r;
         }
     } else {
-        ntt16_round<false, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI);
+        ntt16_round<false, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm);
 #pragma unroll
         for (int e = 0; e < 16; e++) my[w * 17 + e] = canon8(x[e], q, q2);
     }
     __syncthreads();
 }
 
-template <bool INV, int MINB>
+template <bool INV, int MINB, bool LM = false>
 __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet in, PolySet out, int is_final) {
     __shared__ u64 sm[16 * kRowStride];
     const int poly = blockIdx.z, limb = blockIdx.y;
@@ -371,7 +389,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     const u64* src = in.p[poly].ptr + ((size_t)limb << logn);
     u64* dst = Ro.ptr + ((size_t)limb << logn);
     if (!INV) {
-        contig_fwd_rows(t, src, pi, sm);
+        contig_fwd_rows<LM>(t, src, pi, sm);
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             const int f = threadIdx.x + 256 * k;
@@ -387,6 +405,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     const ulonglong2* tw = t.inv + ((size_t)pi << logn);
     const ulonglong2 NI = __ldg(&t.ninv[pi]);
     const ulonglong2 NI1 = __ldg(&t.inv1ninv[pi]);
+    const ulonglong2* lm = LM ? lm_base(t.inv_rows, pi, u, w) : nullptr;
     u64* my = sm + cc * kRowStride;
     u64 x[16];
 #pragma unroll
@@ -398,7 +417,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
-    ntt16_round<true, 0, 8>(x, w << 4, u, tw, q, q2, NI, NI1);
+    ntt16_round<true, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI1, lm);
 #pragma unroll
     for (int e = 0; e < 16; e++) my[w * 17 + e] = x[e];
     __syncthreads();
@@ -412,7 +431,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
 // Forward stages 8..15 fused with the ModDown epilogue: for the canonical transform value v,
 // out = (x + c - v) s mod q (+ acc when the polynomial has one), with per-limb constants
 // {c, s, s'} (Shoup) at consts[3 limb].  The rows of `in` hold the output of stages 0..7.
-template <int MINB>
+template <int MINB, bool LM = false>
 __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, PolySet in, NttEpi e) {
     __shared__ u64 sm[16 * kRowStride];
     const int poly = blockIdx.z, limb = blockIdx.y;
@@ -421,7 +440,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, Poly
     const int logn = t.logn;
     const int pi = prime_of(Ri, limb);
     const size_t base = (size_t)limb << logn;
-    contig_fwd_rows(t, Ri.ptr + base, pi, sm);
+    contig_fwd_rows<LM>(t, Ri.ptr + base, pi, sm);
     const u64 q = __ldg(&t.primes[pi].q);
     const u64 c = __ldg(&e.consts[3 * limb]), s = __ldg(&e.consts[3 * limb + 1]), sp = __ldg(&e.consts[3 * limb + 2]);
     const u64* __restrict__ xs = e.x.p[poly].ptr + base;
@@ -440,20 +459,26 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, Poly
 
 template <int MINB>
 static void prepare_twopass(void) {
-    if (MINB == 4 && first_on_device((const void*)&k_ntt8_contig_epi<MINB>)) {
+    if (MINB == 4 && first_on_device((const void*)&k_ntt8_contig_epi<MINB, true>)) {
         // four CTAs of 35 KB shared memory: a carveout that fits them, the rest L1
         const int co = 64;
         PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<false, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
         PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
         PFT_CUDA(cudaFuncSetAttribute(k_ntt8_strided<true, 8, MINB, true>,
                                       cudaFuncAttributePreferredSharedMemoryCarveout, co));
-        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<false, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<true, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
-        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig_epi<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<false, MINB, true>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig<true, MINB, true>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
+        PFT_CUDA(cudaFuncSetAttribute(k_ntt8_contig_epi<MINB, true>, cudaFuncAttributePreferredSharedMemoryCarveout, co));
     }
 }
 
-template <int MINB>
+template <bool INV, int MINB, bool LM>
+static void launch_contig(const DevTables& t, const PolySet& in, const PolySet& out, int is_final, cudaStream_t st) {
+    dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);
+    k_ntt8_contig<INV, MINB, LM><<<grid, 256, 0, st>>>(t, in, out, is_final);
+}
+
+template <int MINB, bool LM>
 static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
                                    cudaStream_t st) {
     prepare_twopass<MINB>();
@@ -467,13 +492,13 @@ static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const 
         PFT_LAUNCH_CHECK("ntt pass A");
         {
             PFT_PROF("ntt.fwd.contig", st, work);
-            k_ntt8_contig<false, MINB><<<grid, 256, 0, st>>>(t, out, out, 1);
+            launch_contig<false, MINB, LM>(t, out, out, 1, st);
         }
         PFT_LAUNCH_CHECK("ntt pass B");
     } else {
         {
             PFT_PROF("ntt.inv.contig", st, work);
-            k_ntt8_contig<true, MINB><<<grid, 256, 0, st>>>(t, in, out, 0);
+            launch_contig<true, MINB, LM>(t, in, out, 0, st);
         }
         PFT_LAUNCH_CHECK("intt pass B");
         {
@@ -484,14 +509,14 @@ static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const 
     }
 }
 
-// variant 0: 3 CTAs per SM; 1: 4 CTAs per SM
+// variant 0: 3 CTAs per SM; 1: 4 CTAs per SM (both with the lane-major row twiddles)
 static void launch_ntt16_twopass(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse, int v16,
                                  cudaStream_t st) {
-    if (v16 == 1) launch_ntt16_twopass_v<4>(t, in, out, inverse, st);
-    else launch_ntt16_twopass_v<3>(t, in, out, inverse, st);
+    if (v16 == 1) launch_ntt16_twopass_v<4, true>(t, in, out, inverse, st);
+    else launch_ntt16_twopass_v<3, true>(t, in, out, inverse, st);
 }
 
-template <int MINB>
+template <int MINB, bool LM>
 static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& in, const PolySet& out,
                                             cudaStream_t st) {
     prepare_twopass<MINB>();
@@ -499,7 +524,7 @@ static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& i
     const double work = set_limbs(out) * (double)(t.n / 2) * 8;
     {
         PFT_PROF("ntt.inv.contig", st, work);
-        k_ntt8_contig<true, MINB><<<grid, 256, 0, st>>>(t, in, out, 0);
+        launch_contig<true, MINB, LM>(t, in, out, 0, st);
     }
     PFT_LAUNCH_CHECK("intt pass B");
     {
@@ -509,7 +534,7 @@ static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& i
     PFT_LAUNCH_CHECK("intt pass A (unscaled)");
 }
 
-template <int MINB>
+template <int MINB, bool LM>
 static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {
     prepare_twopass<MINB>();
     dim3 grid(16, (unsigned)io.max_limbs, (unsigned)io.count);
@@ -522,7 +547,7 @@ static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttE
     {
         // named apart from the plain transform launches: it also moves the epilogue's operands
         PFT_PROF("epi.ntt_moddown", st, work);
-        k_ntt8_contig_epi<MINB><<<grid, 256, 0, st>>>(t, io, e);
+        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e);
     }
     PFT_LAUNCH_CHECK("ntt pass B + ModDown epilogue");
 }
@@ -882,8 +907,8 @@ bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& 
     if (t.logn != 16) return false;
     const int v16 = ntt16_variant(t);
     if (v16 != 0 && v16 != 1) return false;
-    if (v16 == 1) launch_ntt16_inverse_unscaled_v<4>(t, in, out, st);
-    else launch_ntt16_inverse_unscaled_v<3>(t, in, out, st);
+    if (v16 == 1) launch_ntt16_inverse_unscaled_v<4, true>(t, in, out, st);
+    else launch_ntt16_inverse_unscaled_v<3, true>(t, in, out, st);
     return true;
 }
 
@@ -892,8 +917,8 @@ bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e
     if (t.logn != 16) return false;
     const int v16 = ntt16_variant(t);
     if (v16 != 0 && v16 != 1) return false;
-    if (v16 == 1) launch_ntt16_epi_v<4>(t, io, e, st);
-    else launch_ntt16_epi_v<3>(t, io, e, st);
+    if (v16 == 1) launch_ntt16_epi_v<4, true>(t, io, e, st);
+    else launch_ntt16_epi_v<3, true>(t, io, e, st);
     return true;
 }
 void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {

@@ -61,6 +61,11 @@ struct DevTables {
     ulonglong2* inv;       // [P][N] (psi^-brv(i), shoup)
     ulonglong2* ninv;      // [P] (N^-1, shoup)
     ulonglong2* inv1ninv;  // [P] (psi^-brv(1) N^-1, shoup)
+    // N = 2^16 only (else null): the twiddles of stages 12..15 of fwd / inv in lane-major order,
+    // [P][256 rows u][15 slots][16 lanes w]: slot 2^k - 1 + j, lane w holds entry
+    // 2^(12+k) + u 2^(4+k) + w 2^k + j of the natural table
+    ulonglong2* fwd_rows;
+    ulonglong2* inv_rows;
     int ntt_variant;       // N = 2^16 transform: 0 two-pass (3 CTAs/SM), 1 two-pass (4 CTAs/SM),
                            // 2 one-launch cluster, 3 generic staged passes
 };
