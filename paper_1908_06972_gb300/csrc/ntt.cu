@@ -324,6 +324,18 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet
     }
 }
 
+// Canonical residue of x < 66q (the output range of the uncorrected forward stages) for a prime
+// of s + 1 >= 25 bits, with r = floor(2^(s+32) / q) (= mu >> 32) and sh = s - 24.  The quotient
+// is below 66, so one 32-bit high product estimates it: with xh = floor(x / 2^sh) < 2^32,
+// est = floor(xh r / 2^56) is at most x/q and more than x/q - 2^-22, i.e. floor(x/q) or one
+// less; x - est q then lies in [0, 2q) and one conditional subtraction finishes.
+__device__ __forceinline__ u64 reduce_below66(u64 x, u64 q, u32 r, u32 sh) {
+    const u32 xh = (u32)(x >> sh);
+    const u32 est = __umulhi(xh, r) >> 24;
+    const u64 v = x - (u64)est * q;
+    return v >= q ? v - q : v;
+}
+
 // ---- lane-major copy of the twiddles of stages 12..15 ---------------------------------------
 // In the round of stages 12..15 of a row pass, thread (row u, lane w) uses the 15 twiddles
 // 2^(12+k) + u 2^(4+k) + w 2^k + j (k < 4, j < 2^k): row- and lane-specific, each read once.
@@ -362,13 +374,18 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
     for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
     if (lazy) {
         ntt16_round<false, 0, 8, true, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm);
-        // values below 66q: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
-        // (mu = floor(2^(64+s) / q)), then one correction
-        const u64 one_p = __ldg(&t.primes[pi].mu) >> __ldg(&t.primes[pi].s);
+        const u32 ps = __ldg(&t.primes[pi].s);
+        if (ps >= 24) {
+            const u32 r = (u32)(__ldg(&t.primes[pi].mu) >> 32);
 #pragma unroll
-        for (int e = 0; e < 16; e++) {
-            u64 r = x[e] - mulhi(x[e], one_p) * q;
-            my[w * 17 + e] = r >= q ? r - q : r;
+            for (int e = 0; e < 16; e++) my[w * 17 + e] = reduce_below66(x[e], q, r, ps - 24);
+        } else {  // primes below 2^25: Shoup multiplication by 1 with 1' = floor(2^64 / q) = mu >> s
+            const u64 one_p = __ldg(&t.primes[pi].mu) >> ps;
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const u64 v = x[e] - mulhi(x[e], one_p) * q;
+                my[w * 17 + e] = v >= q ? v - q : v;
+            }
         }
     } else {
         ntt16_round<false, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm);
