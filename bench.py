@@ -349,6 +349,10 @@ def run_gpu(args):
     ft = None
     if args.fasttext:
         ft = fasttext_measure(pft, torch, max(1, args.steps // 2), 1)
+        if args.fasttext_l30:
+            ft["level30"] = fasttext_measure_l30(pft, torch)
+            ft["level30"]["frac_of_alu_bound"] = round(
+                ft["level30"]["batched_gmulmod_s"] / (alu_bound(mul_lo, min(mul_hi, mul_wide)) / 1e9), 4)
 
     tr = None
     if args.train > 0:
@@ -545,6 +549,88 @@ def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
             "max_abs_err_vs_fp64": err, "rotations_per_inference": FT_N * 15,
             "diagonal_variant": {"batched_value": round(FT_BATCH * steps / tdb, 3), "max_abs_err_vs_fp64": derr,
                                  "rotations_per_inference": FT_N - 1 + 9 + 6, "input_scale": "2^50"}}
+
+
+# Algorithmic mulmods of one key switch at level l (k special primes, digits of alpha primes, N =
+# 2^16): transforms (l inverse, beta (l + k) - l forward for ModUp, 2k inverse and 2l forward for
+# ModDown, N/2 log2 N butterflies each), ModUp conversion, inner product, ModDown conversion and
+# scaling; the same count as the hot-path scope's per-unit figures.
+def ks_mulmods(l, k=K_SP, alpha=ALPHA, logn=LOGN):
+    n = 1 << logn
+    E, beta = l + k, -(-l // alpha)
+    digits = [min(alpha, l - j * alpha) for j in range(beta)]
+    n_ntt = l + sum(E - a for a in digits) + 2 * k + 2 * l
+    return n * (n_ntt * logn / 2 + sum(digits) + sum(a * (E - a) for a in digits) + 2 * beta * E + 2 * (k + k * l + l))
+
+
+def fasttext_mulmods(l, cols=FT_N, logn=LOGN):
+    """One Fig. 3 inference at level l: cols column products, log2(N/2) rotations per column
+    (TotalSum), a rescale per column, the output products and a final rescale."""
+    n = 1 << logn
+    rot = ks_mulmods(l)  # a rotation's automorphism and the TotalSum additions take no mulmods
+    rescale = lambda lv: 2 * (lv * (n // 2) * logn + (lv - 1) * n)  # noqa: E731
+    return cols * (2 * l * n + (logn - 1) * rot + rescale(l)) + cols * 2 * (l - 1) * n + rescale(l - 1)
+
+
+def fasttext_measure_l30(pft, torch, level=30, batch=8):
+    """The fastText inference at the top of the 30-prime chain: batch `batch` and batch 1 of the
+    Fig. 3 sequence (960 rotations per inference) and 32 documents of the rotation-light one."""
+    from paper_1908_06972_gb300 import synth
+
+    ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, 60, 40, 60, 2.0 ** 40, SEED)
+    pft.pft_keygen(ctx, [1 << i for i in range(15)], False)
+    H, O = synth.fasttext_weights(77, FT_M, FT_N, FT_C)
+    docs = synth.documents(78, FT_M, FT_BATCH)
+    t = (1 << LOGN) // 2
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def enc(d, scale, nonce):
+        pt = pft.pft_encode(ctx, docs[d], scale, level)
+        h = pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, nonce)
+        pft.pft_pt_destroy(pt)
+        return h
+
+    model = pft.pft_ft_model_create(ctx, H, O, level)
+    vs = [enc(d, 2.0 ** 40, 9100 + d) for d in range(batch)]
+    scores = [pft.pft_ct_create(ctx) for _ in range(FT_BATCH)]
+    batched = lambda: pft.pft_fasttext_infer_batch(ctx, model, vs, 1, scores[:batch])  # noqa: E731
+    batched()
+    tb = timed(batched)
+    ts = timed(lambda: pft.pft_fasttext_infer(ctx, model, [vs[0]], scores[0]))
+    dec = pft.pft_decrypt(ctx, scores[0])
+    err = float(np.max(np.abs(pft.pft_decode(ctx, dec, FT_C)[:FT_C].real - fp64_scores(docs[0], H, O))))
+    pft.pft_pt_destroy(dec)
+    for h in vs:
+        pft.pft_ct_destroy(h)
+    pft.pft_ft_model_destroy(model)
+    pft.pft_add_rotation_keys(ctx, list(range(1, FT_N)) + [FT_N << s for s in range(9)])
+    dmodel = pft.pft_ft_model_create_diag(ctx, H, O, level)
+    dvs = [enc(d, 2.0 ** 50, 9600 + d) for d in range(FT_BATCH)]
+    dbatched = lambda: pft.pft_fasttext_infer_batch(ctx, dmodel, dvs, 1, scores)  # noqa: E731
+    dbatched()
+    tdb = timed(dbatched)
+    dec = pft.pft_decrypt(ctx, scores[0])
+    derr = float(np.max(np.abs(pft.pft_decode(ctx, dec, t).real[[FT_N * cc for cc in range(FT_C)]]
+                               - fp64_scores(docs[0], H, O))))
+    pft.pft_pt_destroy(dec)
+    for h in dvs + scores:
+        pft.pft_ct_destroy(h)
+    pft.pft_ft_model_destroy(dmodel)
+    pft.pft_ctx_destroy(ctx)
+    mm = fasttext_mulmods(level)
+    return {"level": level, "unit": "inferences/s", "batched_value": round(batch / tb, 3), "batch": batch,
+            "batch1_value": round(1 / ts, 3), "max_abs_err_vs_fp64": err,
+            "gmulmod_per_inference": round(mm / 1e9, 1), "batched_gmulmod_s": round(mm * batch / tb / 1e9, 1),
+            "diagonal_variant": {"batched_value": round(FT_BATCH / tdb, 3), "batch": FT_BATCH,
+                                 "max_abs_err_vs_fp64": derr, "input_scale": "2^50"}}
 
 
 # ---- serving loop: Poisson arrivals, continuous batching ------------------------------------------
@@ -1186,6 +1272,7 @@ def main():
     ap.add_argument("--case", default="step", choices=["step", "ntt", "ks"])
     ap.add_argument("--fasttext", type=int, default=1, help="also measure encrypted fastText inference")
     ap.add_argument("--graph", type=int, default=1, help="also measure the step as one CUDA-graph launch")
+    ap.add_argument("--fasttext-l30", type=int, default=1, help="also measure fastText at level 30")
     ap.add_argument("--compressed-keys", action="store_true",
                     help="seeded compressed switching keys (the step and --case ks)")
     ap.add_argument("--train", type=int, default=64, help="documents per encrypted training step (0: skip)")
