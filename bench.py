@@ -46,7 +46,6 @@ SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 9
 # dram__bytes_read.sum + dram__bytes_write.sum over the four two-pass launches of the
 # 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes.
 NTT_DRAM_BYTES_PER_LIMB_PASS = 1.0121e6
-NTT16_VARIANTS = ["two-pass 3 CTA/SM", "two-pass 4 CTA/SM", "cluster", "generic"]
 
 
 def alu_bound(lo, hi):
@@ -155,6 +154,7 @@ def run_gpu(args):
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED,
                              flags=pft.PFT_COMPRESSED_KEYS if args.compressed_keys else 0)
     tuned, tune_us = pft.pft_autotune(ctx)
+    tune_report = pft.pft_autotune_report(ctx)
     bfly_ceiling = pft.pft_bfly_ceiling(ctx) / 1e9  # G butterflies/s of the butterfly on register data
     mul_lo, mul_hi, mul_wide = pft.pft_mul_rates(ctx)  # measured 32-bit multiply issue rates
     pft.pft_keygen(ctx, STEPS_ROT, True)
@@ -387,8 +387,7 @@ def run_gpu(args):
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "split": e2e_split},
            "gpu_launches": int(all_launches), "roofline": roof,
-           "autotune": {"ntt16_variant": NTT16_VARIANTS[tuned],
-                        "us_fwd_inv_2x32limbs": dict(zip(NTT16_VARIANTS, [round(x, 1) for x in tune_us]))}, "cpu_baseline": cpu, "clocks": clk.summary(),
+           "autotune": tune_report, "cpu_baseline": cpu, "clocks": clk.summary(),
            "fasttext": ft, "serving": sv, "training": tr, "job_queue": qu, "ops": ops}
     if rank == 0:
         print(json.dumps(out))

@@ -337,15 +337,30 @@ int pft_rescale_batch(pft_ctx* ctx, const pft_ct* const* a, int B, pft_ct* const
 int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, pft_ct* const* out);
 
 /* ---- autotuning -----------------------------------------------------------
- * Times every N = 2^16 transform variant of the library (two-pass with 3 or 4 resident CTAs
- * per SM, one-launch 8-CTA cluster, generic staged passes) on a forward + inverse transform
- * of 2 x 32 limbs and keeps the fastest for this context.  us_out (may be NULL) receives up to
- * `cap` per-variant times in microseconds, chosen the selected index.  Other ring degrees
- * have a single variant.  The environment variable PFT_NTT16 (twopass, twopass4, cluster,
- * generic) overrides the choice. */
+ * A search over the ring's transform plans, per launch size.  A plan is one of the
+ * specialised N = 2^16 kernels (two-pass 8 + 8 with register rounds at 3 or 4 resident CTAs per
+ * SM; one launch on an 8-CTA cluster exchanging through distributed shared memory) or a sequence
+ * of generic shared-memory passes with a chosen number of stages and sub-transforms per CTA
+ * (N = 2^16: 8+8 at two tile widths, 6+10, 10+6, 7+9, 9+7, 5+5+6; N = 2^15: 8+7, 7+8, 9+6, 6+9,
+ * 5+5+5; N <= 2^14 has a single one-pass plan).  For each launch-size bucket (total limbs of a
+ * launch: <= 64, <= 512, larger) every plan is timed on a forward + inverse transform of a
+ * representative launch (32, 256, 1024 limbs; median of 3 CUDA-event timings on the context's
+ * stream) and the fastest is kept for launches of that size.  us_out (may be NULL) receives up
+ * to `cap` plan times (microseconds) of the largest bucket, *chosen its choice (an index into
+ * the plan list of pft_autotune_report).  Synchronous.  The environment variable PFT_NTT16
+ * (twopass, twopass4, cluster, generic) overrides every choice at N = 2^16. */
 #define PFT_NTT16_VARIANTS 4
 int pft_autotune(pft_ctx* ctx, double* us_out, int cap, int* chosen);
-/* Pin the N = 2^16 transform variant (0..PFT_NTT16_VARIANTS-1 in the order above) without timing. */
+/* The last search as JSON text: {"N": n, "buckets": [{"limbs": k, "chosen": name,
+ * "us_fwd_inv": {plan name: microseconds, ...}}, ...]} ("buckets" empty before a search or for a
+ * ring with one plan).  buf (may be NULL) receives up to cap - 1 bytes and a terminating zero;
+ * *len (may be NULL) the full length. */
+int pft_autotune_report(pft_ctx* ctx, char* buf, size_t cap, size_t* len);
+/* Use plan `plan` (index into the ring's plan list, in the order above) for every launch size;
+ * -1: back to the fixed variant. */
+int pft_set_transform_plan(pft_ctx* ctx, int plan);
+/* Pin the N = 2^16 transform variant (0..PFT_NTT16_VARIANTS-1: two-pass 3 CTAs/SM, two-pass 4
+ * CTAs/SM, cluster, generic 8 + 8) for every launch size, without timing. */
 int pft_set_transform_variant(pft_ctx* ctx, int variant);
 
 /* ---- CUDA graphs of batched operations ------------------------------------

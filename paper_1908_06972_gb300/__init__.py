@@ -113,6 +113,8 @@ def lib():
             "pft_device_status": [vp], "pft_wait_selftest": [vp, ctypes.c_longlong],
             "pft_run_jobs": [vp, POINTER(pft_job), i, c_double], "pft_bfly_ceiling": [vp, POINTER(c_double)],
             "pft_mul_rates": [vp, POINTER(c_double), POINTER(c_double), POINTER(c_double)],
+            "pft_autotune_report": [vp, ctypes.c_char_p, c_size_t, POINTER(c_size_t)],
+            "pft_set_transform_plan": [vp, i],
             "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
@@ -176,7 +178,8 @@ def exported_symbols():
             "pft_ft_enc_model_destroy", "pft_fasttext_train_spec", "pft_fasttext_train_forward", "pft_ft_tape_score",
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
             "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag",
-            "pft_run_jobs", "pft_bfly_ceiling", "pft_ct_import_batch_into", "pft_mul_rates"]
+            "pft_run_jobs", "pft_bfly_ceiling", "pft_ct_import_batch_into", "pft_mul_rates",
+            "pft_autotune_report", "pft_set_transform_plan"]
 
 
 def _check(rc, ctx=None):
@@ -561,10 +564,24 @@ def pft_rescale_noalloc(ctx, in_ptr, level, out_ptr):
 
 def pft_autotune(ctx):
     """Times the transform variants, keeps the fastest; returns (chosen index, times in us)."""
-    us = (c_double * 8)()
+    us = (c_double * 16)()
     chosen = c_int()
-    _check(lib().pft_autotune(ctx, us, 8, ctypes.byref(chosen)), ctx)
-    return chosen.value, [us[i] for i in range(8)]
+    _check(lib().pft_autotune(ctx, us, 16, ctypes.byref(chosen)), ctx)
+    return chosen.value, [us[i] for i in range(16)]
+
+
+def pft_autotune_report(ctx):
+    """The last autotuning search as a dict (parsed from the library's JSON text)."""
+    import json
+    n = c_size_t()
+    _check(lib().pft_autotune_report(ctx, None, 0, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib().pft_autotune_report(ctx, buf, n.value + 1, None), ctx)
+    return json.loads(buf.value.decode())
+
+
+def pft_set_transform_plan(ctx, plan):
+    _check(lib().pft_set_transform_plan(ctx, plan), ctx)
 
 
 def pft_set_transform_variant(ctx, variant):

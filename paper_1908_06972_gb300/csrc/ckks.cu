@@ -5,6 +5,7 @@
 // arithmetic runs in the kernels of ntt.cu and poly.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -90,6 +91,7 @@ static void build_tables(pft_ctx* c) {
     }
     c->tabs.logn = logn;
     c->tabs.n = n;
+    for (int b = 0; b < kNttBuckets; b++) c->tabs.plan[b].kind = -1;  // until the autotuner chooses
     c->tabs.primes = tab_upload(c, dp);
     // twiddles
     std::vector<ulonglong2> fwd((size_t)P * n), inv((size_t)P * n), ninv(P), inv1(P);
@@ -1998,48 +2000,104 @@ int pft_rotate_batch(pft_ctx* c, const pft_ct* const* a, int B, int32_t step, pf
     });
 }
 
+// The autotuner: for each launch-size bucket (by the launch's total limbs: <= 64, <= 512, larger)
+// it times every transform plan of the ring (ntt_candidates: the specialised kernels and generic
+// staged passes of several stage splits and tile widths) on a forward + inverse transform of a
+// representative launch (32, 256 and 1024 limbs of the chain's primes), median of 3, and keeps
+// the fastest plan for that bucket.
 int pft_autotune(pft_ctx* c, double* us_out, int cap, int* chosen) {
     return guard(c, [&] {
         NEED(c, PFT_ERR_ARG, "null context");
-        const int nv = c->logn == 16 ? kNttVariants : 1;
-        std::vector<double> us(nv, 0.0);
-        if (nv > 1) {
-            // a representative launch: 64 limbs of the chain, forward then inverse, 3 repetitions
-            const int limbs = std::min(c->L + c->k, 32), polys = 2;
-            Scratch buf(c, (size_t)polys * limbs * c->n * 8);
-            PFT_CUDA(cudaMemsetAsync(buf.p, 0, (size_t)polys * limbs * c->n * 8, c->stream));
-            std::vector<PolyRef> r;
-            for (int i = 0; i < polys; i++) r.push_back(ref(buf.u() + (size_t)i * limbs * c->n, limbs));
+        constexpr int kMaxCand = 16;
+        DevTables::Plan cand[kMaxCand];
+        const char* names[kMaxCand];
+        const int nc = ntt_candidates(c->logn, cand, names, kMaxCand);
+        std::string js = "{\"N\": " + std::to_string(c->n) + ", \"buckets\": [";
+        int best_last = 0;
+        std::vector<double> us_last(std::max(nc, 1), 0.0);
+        if (nc > 1) {
+            const int reps_limbs[kNttBuckets] = {32, 256, 1024};
+            const int limbs = std::min(c->L + c->k, 32);
             cudaEvent_t e0, e1;
             PFT_CUDA(cudaEventCreate(&e0));
             PFT_CUDA(cudaEventCreate(&e1));
-            const int keep = c->tabs.ntt_variant;
-            for (int v = 0; v < nv; v++) {
-                c->tabs.ntt_variant = v;
-                ntt_fwd(c, r, r);  // warm-up (and one-time kernel attributes)
-                ntt_inv(c, r, r);
-                PFT_CUDA(cudaEventRecord(e0, c->stream));
-                for (int rep = 0; rep < 3; rep++) {
-                    ntt_fwd(c, r, r);
+            for (int b = 0; b < kNttBuckets; b++) {
+                const int polys = std::max(1, reps_limbs[b] / limbs);
+                Scratch buf(c, (size_t)polys * limbs * c->n * 8);
+                PFT_CUDA(cudaMemsetAsync(buf.p, 0, (size_t)polys * limbs * c->n * 8, c->stream));
+                std::vector<PolyRef> r;
+                for (int i = 0; i < polys; i++) r.push_back(ref(buf.u() + (size_t)i * limbs * c->n, limbs));
+                std::vector<double> us(nc, 0.0);
+                for (int v = 0; v < nc; v++) {
+                    c->tabs.plan[b] = cand[v];
+                    ntt_fwd(c, r, r);  // warm-up (and one-time kernel attributes)
                     ntt_inv(c, r, r);
+                    double t3[3];
+                    for (int rep = 0; rep < 3; rep++) {
+                        PFT_CUDA(cudaEventRecord(e0, c->stream));
+                        ntt_fwd(c, r, r);
+                        ntt_inv(c, r, r);
+                        PFT_CUDA(cudaEventRecord(e1, c->stream));
+                        PFT_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        PFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        t3[rep] = 1e3 * ms;
+                    }
+                    std::sort(t3, t3 + 3);
+                    us[v] = t3[1];
                 }
-                PFT_CUDA(cudaEventRecord(e1, c->stream));
-                PFT_CUDA(cudaEventSynchronize(e1));
-                float ms = 0;
-                PFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                us[v] = 1e3 * ms / 3;
+                int best = 0;
+                for (int v = 1; v < nc; v++)
+                    if (us[v] < us[best]) best = v;
+                c->tabs.plan[b] = cand[best];
+                char head[160];
+                snprintf(head, sizeof(head), "%s{\"limbs\": %d, \"chosen\": \"%s\", \"us_fwd_inv\": {", b ? ", " : "",
+                         polys * limbs, names[best]);
+                js += head;
+                for (int v = 0; v < nc; v++) {
+                    char item[160];
+                    snprintf(item, sizeof(item), "%s\"%s\": %.1f", v ? ", " : "", names[v], us[v]);
+                    js += item;
+                }
+                js += "}}";
+                if (b == kNttBuckets - 1) {
+                    best_last = best;
+                    us_last = us;
+                }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            int best = 0;
-            for (int v = 1; v < nv; v++)
-                if (us[v] < us[best]) best = v;
-            c->tabs.ntt_variant = best;
-            (void)keep;
         }
-        if (chosen) *chosen = c->tabs.ntt_variant;
+        js += "]}";
+        c->autotune_report = js;
+        if (chosen) *chosen = best_last;
         if (us_out)
-            for (int v = 0; v < nv && v < cap; v++) us_out[v] = us[v];
+            for (int v = 0; v < nc && v < cap; v++) us_out[v] = us_last[v];
+    });
+}
+
+int pft_autotune_report(pft_ctx* c, char* buf, size_t cap, size_t* len) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "null context");
+        if (len) *len = c->autotune_report.size();
+        if (buf && cap) {
+            const size_t k = std::min(cap - 1, c->autotune_report.size());
+            memcpy(buf, c->autotune_report.data(), k);
+            buf[k] = 0;
+        }
+    });
+}
+
+int pft_set_transform_plan(pft_ctx* c, int plan) {
+    return guard(c, [&] {
+        NEED(c, PFT_ERR_ARG, "null context");
+        DevTables::Plan cand[16];
+        const int nc = ntt_candidates(c->logn, cand, nullptr, 16);
+        NEED(plan >= -1 && plan < nc, PFT_ERR_ARG, "plan out of range");
+        for (int b = 0; b < kNttBuckets; b++) {
+            if (plan < 0) c->tabs.plan[b].kind = -1;
+            else c->tabs.plan[b] = cand[plan];
+        }
     });
 }
 
@@ -2047,6 +2105,7 @@ int pft_set_transform_variant(pft_ctx* c, int variant) {
     return guard(c, [&] {
         NEED(c && variant >= 0 && variant < kNttVariants, PFT_ERR_ARG, "variant out of range");
         c->tabs.ntt_variant = variant;
+        for (int b = 0; b < kNttBuckets; b++) c->tabs.plan[b].kind = -1;  // the fixed variant everywhere
     });
 }
 

@@ -20,6 +20,7 @@ struct pft_ctx {
     pft_params prm;
     int device = 0;                 // CUDA device current at creation; all work runs there
     u64* noalloc_scratch = nullptr;  // device address of the fixed array of pft_rescale_noalloc
+    std::string autotune_report;     // JSON of the last pft_autotune search
     int logn = 0, n = 0, L = 0, k = 0, alpha = 0, beta_max = 0;
     std::vector<u64> primes;  // q_0..q_{L-1}, p_0..p_{k-1}
     pft_allocator alloc{};

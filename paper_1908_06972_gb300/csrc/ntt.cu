@@ -588,7 +588,9 @@ static void launch_ntt16_cluster(const DevTables& t, const PolySet& in, const Po
 
 // N = 2^16 variant: the context's choice (pft_autotune), unless PFT_NTT16 names one
 // (twopass, twopass4, cluster, generic).
-static int ntt16_variant(const DevTables& t) {
+// the N = 2^16 kernel family of a launch of `limbs` limbs: the environment's choice, else the
+// autotuned plan of the launch's size bucket, else the context's fixed variant
+static int ntt16_variant(const DevTables& t, double limbs = -1) {
     static int env = -2;
     if (env == -2) {
         const char* e = getenv("PFT_NTT16");
@@ -599,7 +601,12 @@ static int ntt16_variant(const DevTables& t) {
                  : strcmp(e, "generic") == 0  ? 3
                                               : -1;
     }
-    return env >= 0 ? env : t.ntt_variant;
+    if (env >= 0) return env;
+    if (limbs >= 0) {
+        const int k = t.plan[ntt_bucket(limbs)].kind;
+        if (k >= 0) return k;
+    }
+    return t.ntt_variant;
 }
 
 template <int S, int C, bool INV>
@@ -753,6 +760,70 @@ static void launch_pass(const DevTables& t, const PolySet& in, const PolySet& ou
     PFT_LAUNCH_CHECK("ntt pass");
 }
 
+// One pass of a generic plan: the (S, C) shapes the autotuner searches (256 threads per CTA, and
+// 128 for 8 stages with 8 sub-transforms per CTA).
+template <bool INV>
+static void launch_generic_pass(const DevTables& t, const PolySet& in, const PolySet& out, int S, int C, int s0,
+                                int is_final, cudaStream_t st) {
+    switch (S * 1000 + C) {
+        case 5128: launch_pass<5, 128, INV>(t, in, out, s0, is_final, st); break;
+        case 6064: launch_pass<6, 64, INV>(t, in, out, s0, is_final, st); break;
+        case 7032: launch_pass<7, 32, INV>(t, in, out, s0, is_final, st); break;
+        case 7016: launch_pass<7, 16, INV>(t, in, out, s0, is_final, st); break;
+        case 8016: launch_pass<8, 16, INV>(t, in, out, s0, is_final, st); break;
+        case 8008: launch_pass<8, 8, INV>(t, in, out, s0, is_final, st); break;
+        case 9008: launch_pass<9, 8, INV>(t, in, out, s0, is_final, st); break;
+        case 10004: launch_pass<10, 4, INV>(t, in, out, s0, is_final, st); break;
+        default: fail(PFT_ERR_ARG, "internal: no kernel for this transform pass shape");
+    }
+}
+// A generic plan: forward passes in order (stage offsets accumulate), inverse in reverse order.
+static void run_generic(const DevTables& t, const DevTables::Plan& p, const PolySet& in, const PolySet& out,
+                        bool inverse, cudaStream_t st) {
+    int s0[3] = {0, 0, 0};
+    for (int i = 1; i < p.npass; i++) s0[i] = s0[i - 1] + p.S[i - 1];
+    if (!inverse) {
+        for (int i = 0; i < p.npass; i++)
+            launch_generic_pass<false>(t, i == 0 ? in : out, out, p.S[i], p.C[i], s0[i], i == p.npass - 1, st);
+    } else {
+        for (int i = p.npass - 1; i >= 0; i--)
+            launch_generic_pass<true>(t, i == p.npass - 1 ? in : out, out, p.S[i], p.C[i], s0[i], i == 0, st);
+    }
+}
+
+int ntt_candidates(int logn, DevTables::Plan* out, const char** names, int cap) {
+    struct Cand {
+        const char* name;
+        DevTables::Plan p;
+    };
+    static const Cand c16[] = {
+        {"two-pass 8+8 (register rounds), 3 CTAs/SM", {0, 0, {0, 0, 0}, {0, 0, 0}}},
+        {"two-pass 8+8 (register rounds), 4 CTAs/SM", {1, 0, {0, 0, 0}, {0, 0, 0}}},
+        {"one launch, 8-CTA cluster (DSMEM exchange)", {2, 0, {0, 0, 0}, {0, 0, 0}}},
+        {"staged 8+8, 16 sub-transforms/CTA", {3, 2, {8, 8, 0}, {16, 16, 0}}},
+        {"staged 8+8, 8 sub-transforms/CTA", {3, 2, {8, 8, 0}, {8, 8, 0}}},
+        {"staged 6+10", {3, 2, {6, 10, 0}, {64, 4, 0}}},
+        {"staged 10+6", {3, 2, {10, 6, 0}, {4, 64, 0}}},
+        {"staged 7+9", {3, 2, {7, 9, 0}, {32, 8, 0}}},
+        {"staged 9+7", {3, 2, {9, 7, 0}, {8, 32, 0}}},
+        {"staged 5+5+6 (three passes)", {3, 3, {5, 5, 6}, {128, 128, 64}}},
+    };
+    static const Cand c15[] = {
+        {"staged 8+7", {3, 2, {8, 7, 0}, {16, 16, 0}}},
+        {"staged 7+8", {3, 2, {7, 8, 0}, {16, 16, 0}}},
+        {"staged 9+6", {3, 2, {9, 6, 0}, {8, 64, 0}}},
+        {"staged 6+9", {3, 2, {6, 9, 0}, {64, 8, 0}}},
+        {"staged 5+5+5 (three passes)", {3, 3, {5, 5, 5}, {128, 128, 128}}},
+    };
+    const Cand* c = logn == 16 ? c16 : logn == 15 ? c15 : nullptr;
+    const int n = logn == 16 ? (int)(sizeof(c16) / sizeof(c16[0])) : logn == 15 ? (int)(sizeof(c15) / sizeof(c15[0])) : 0;
+    for (int i = 0; i < n && i < cap; i++) {
+        if (out) out[i] = c[i].p;
+        if (names) names[i] = c[i].name;
+    }
+    return n;
+}
+
 template <bool INV>
 static void run_single(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
     switch (t.logn) {
@@ -778,7 +849,12 @@ static void run(const DevTables& t, const PolySet& in, const PolySet& out, bool 
         else run_single<false>(t, in, out, st);
         return;
     }
-    const int v16 = t.logn == 16 ? ntt16_variant(t) : -1;
+    const DevTables::Plan& pl = t.plan[ntt_bucket(set_limbs(out))];
+    const int v16 = t.logn == 16 ? ntt16_variant(t, set_limbs(out)) : (pl.kind == 3 ? 3 : -1);
+    if (v16 == 3 && pl.kind == 3) {  // a generic plan chosen for this launch size
+        run_generic(t, pl, in, out, inverse, st);
+        return;
+    }
     if (v16 == 0 || v16 == 1) {
         launch_ntt16_twopass(t, in, out, inverse, v16, st);
     } else if (v16 == 2) {
@@ -922,7 +998,7 @@ void mul_rates(cudaStream_t st, double* lo, double* hi, double* wide) {
 bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
     if (out.count == 0) return true;
     if (t.logn != 16) return false;
-    const int v16 = ntt16_variant(t);
+    const int v16 = ntt16_variant(t, set_limbs(out));
     if (v16 != 0 && v16 != 1) return false;
     if (v16 == 1) launch_ntt16_inverse_unscaled_v<4, true>(t, in, out, st);
     else launch_ntt16_inverse_unscaled_v<3, true>(t, in, out, st);
@@ -932,7 +1008,7 @@ bool ntt_inverse_unscaled(const DevTables& t, const PolySet& in, const PolySet& 
 bool ntt_forward_epilogue(const DevTables& t, const PolySet& io, const NttEpi& e, cudaStream_t st) {
     if (io.count == 0) return true;
     if (t.logn != 16) return false;
-    const int v16 = ntt16_variant(t);
+    const int v16 = ntt16_variant(t, set_limbs(io));
     if (v16 != 0 && v16 != 1) return false;
     if (v16 == 1) launch_ntt16_epi_v<4, true>(t, io, e, st);
     else launch_ntt16_epi_v<3, true>(t, io, e, st);

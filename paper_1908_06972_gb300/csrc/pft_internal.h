@@ -68,8 +68,18 @@ struct DevTables {
     ulonglong2* inv_rows;
     int ntt_variant;       // N = 2^16 transform: 0 two-pass (3 CTAs/SM), 1 two-pass (4 CTAs/SM),
                            // 2 one-launch cluster, 3 generic staged passes
+    // Transform plan per launch size (bucket of the launch's total limbs: <= 64, <= 512,
+    // larger), chosen by the autotuner; kind < 0: the fixed variant above.
+    struct Plan {
+        int8_t kind;   // -1 none, 0 two-pass 3 CTAs/SM, 1 two-pass 4 CTAs/SM, 2 cluster, 3 generic
+        int8_t npass;  // generic: passes, first (largest stride) first
+        int8_t S[3];   // generic: stages per pass
+        int16_t C[3];  // generic: sub-transforms per CTA of each pass
+    } plan[3];
 };
 constexpr int kNttVariants = 4;
+constexpr int kNttBuckets = 3;
+inline int ntt_bucket(double limbs) { return limbs <= 64 ? 0 : limbs <= 512 ? 1 : 2; }
 
 struct Error {
     int code;
@@ -126,6 +136,9 @@ double bfly_ceiling(const DevTables& t, cudaStream_t st);
 // butterflies use: low-word multiply-add, high-word multiply, widening multiply (synchronous).
 void mul_rates(cudaStream_t st, double* lo, double* hi, double* wide);
 void ntt_inverse(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
+// The transform plans the autotuner searches for this ring degree (generic plans have S[], C[]),
+// with their names; plan_supported: the plan's kernels exist for this ring.
+int ntt_candidates(int logn, DevTables::Plan* out, const char** names, int cap);
 
 enum class EwOp { Add, Sub, Mul, Neg, Copy };
 // out[i] = a[i] (op) b[i] per limb (b ignored for Neg/Copy).

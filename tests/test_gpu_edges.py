@@ -1,7 +1,8 @@
 """Edge cases of the GPU path against the oracle and the layout definition.
 
-* Transforms at every supported shape class (one pass N <= 2^14, 8 + 7 stages at 2^15, the
-  two-pass kernels at 2^16) with primes on both sides of the lazy-butterfly bound 2^57 (57-bit
+* Transforms at every supported shape class (one pass N <= 2^14; at 2^15 and 2^16 every plan
+  the autotuner searches: the specialised kernels and the generic passes of every stage split)
+  with primes on both sides of the lazy-butterfly bound 2^57 (57-bit
   primes are the largest on the lazy path), the benchmark's 50-bit primes and small ones, on
   extreme inputs (every coefficient q - 1, alternating 0 / q - 1) and random ones: forward
   equal to the evaluation definition, inverse restoring the input exactly.
@@ -28,6 +29,8 @@ def test_transform_extreme_inputs(gpu, logn, bits):
     p = Pair(gpu, logn, 3, 1, 1, first_bits=first, mid_bits=mid, special_bits=special, gpu_keys=False,
              rot_steps=(), relin=False)
     try:
+        if logn >= 15:
+            gpu.pft_autotune(p.ctx)
         primes = gpu.pft_ctx_info(p.ctx)["primes"]  # q0, q1, q2 and the special prime
         n = 1 << logn
         x = synth.residues(17, primes, n, polys=3)
@@ -37,9 +40,11 @@ def test_transform_extreme_inputs(gpu, logn, bits):
         idx = np.arange(n) if logn <= 11 else np.r_[0:32, n // 2 - 16:n // 2 + 16, n - 32:n]
         want = [[OC.eval_at(x[poly, r], OP.root_2n(q, logn), q, logn, idx) for r, q in enumerate(primes)]
                 for poly in range(3)]
-        for variant in range(gpu.PFT_NTT16_VARIANTS) if logn == 16 else [None]:  # every N = 2^16 kernel variant
+        # every transform plan the autotuner searches at N = 2^15 and 2^16
+        plans = range(len(gpu.pft_autotune_report(p.ctx)["buckets"][0]["us_fwd_inv"])) if logn >= 15 else [None]
+        for variant in plans:
             if variant is not None:
-                gpu.pft_set_transform_variant(p.ctx, variant)
+                gpu.pft_set_transform_plan(p.ctx, variant)
             t = torch.from_numpy(x.view(np.int64).copy()).cuda()
             gpu.pft_ntt(p.ctx, t.data_ptr(), 3, len(primes), 0)
             y = t.cpu().numpy().view(np.uint64)

@@ -349,21 +349,31 @@ def test_graph_replay_matches_oracle(gpu):
 
 
 def test_every_transform_variant_bit_exact(p16):
-    """pft_autotune picks among the N = 2^16 transform variants; each one gives the same bits."""
+    """pft_autotune searches the N = 2^16 transform plans per launch size; every plan (and so
+    every choice it can make) gives the same bits, and so does every fixed variant."""
     o, pf, ctx = p16.orc, p16.pft, p16.ctx
     chosen, us = pf.pft_autotune(ctx)
-    nv = pf.PFT_NTT16_VARIANTS
-    assert 0 <= chosen < nv and all(u > 0 for u in us[:nv])
+    rep = pf.pft_autotune_report(ctx)
+    names = list(rep["buckets"][-1]["us_fwd_inv"])
+    assert rep["N"] == p16.N and len(rep["buckets"]) == 3 and len(names) >= 8
+    assert 0 <= chosen < len(names) and all(u > 0 for u in us[:len(names)])
+    for b in rep["buckets"]:
+        assert b["chosen"] in b["us_fwd_inv"] and b["us_fwd_inv"][b["chosen"]] == min(b["us_fwd_inv"].values())
     a = o.encrypt_sk(o.encode(synth.slots(31, 512), level=6), 41)
     b = o.encrypt_sk(o.encode(synth.slots(32, 512), level=6), 42)
     want = o.mul_relin(a, b)
     ga, gb = p16.ct(a), p16.ct(b)
-    for v in range(nv):
+    for v in range(len(names)):
+        pf.pft_set_transform_plan(ctx, v)
+        m = p16.empty()
+        pf.pft_mul_relin(ctx, ga, gb, m)
+        p16.assert_equal(m, want, "mul_relin with transform plan %s" % names[v])
+    for v in range(pf.PFT_NTT16_VARIANTS):
         pf.pft_set_transform_variant(ctx, v)
         m = p16.empty()
         pf.pft_mul_relin(ctx, ga, gb, m)
         p16.assert_equal(m, want, "mul_relin with transform variant %d" % v)
-    pf.pft_set_transform_variant(ctx, chosen)
+    pf.pft_set_transform_variant(ctx, 0)
 
 
 @pytest.mark.parametrize("which", ["p1", "p16"])
