@@ -223,6 +223,20 @@ int pft_ct_export_batch(pft_ctx* ctx, const pft_ct* const* cts, int B, uint64_t*
  * before then. */
 int pft_ct_export_batch_async(pft_ctx* ctx, const pft_ct* const* cts, int B, uint64_t* const* coeffs);
 
+/* ---- exchange of ciphertexts between processes (data-parallel training) ----
+ * Sec. 4.2 splits a minibatch over GPUs, so the ranks' encrypted gradients must be summed.  A
+ * sum of R ciphertexts of one level and scale is exact as an integer sum of their words when
+ * R (q - 1) < 2^64 for every prime q of the level (R <= 16 at 60-bit primes): each rank copies its
+ * words out (pft_ct_copy_out), a collective sums them as integers, and pft_ct_reduce_sum turns
+ * the sums back into a ciphertext.  Larger R: gather the words and add them with pft_add. */
+/* Device-to-device copy of ct's words ([2][l][N], evaluation layout) to dev_dst (2 l N words);
+ * asynchronous on the context's stream. */
+int pft_ct_copy_out(pft_ctx* ctx, const pft_ct* ct, uint64_t* dev_dst);
+/* out = the ciphertext at `level` and `scale` whose words are dev_words ([2][level][N] device
+ * words, each the exact integer sum of n_terms canonical residues of its limb's prime) reduced
+ * modulo those primes.  PFT_ERR_ARG if n_terms (q - 1) can reach 2^64 for a prime of the level. */
+int pft_ct_reduce_sum(pft_ctx* ctx, const uint64_t* dev_words, int level, double scale, int n_terms, pft_ct* out);
+
 /* ---- homomorphic operations (Sec. 2.3) ------------------------------------
  * `out` must be a handle from pft_ct_create / an op; it is resized as needed. */
 int pft_add(pft_ctx* ctx, const pft_ct* a, const pft_ct* b, pft_ct* out);       /* HADD */

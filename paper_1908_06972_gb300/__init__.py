@@ -115,6 +115,8 @@ def lib():
             "pft_mul_rates": [vp, POINTER(c_double), POINTER(c_double), POINTER(c_double)],
             "pft_autotune_report": [vp, ctypes.c_char_p, c_size_t, POINTER(c_size_t)],
             "pft_set_transform_plan": [vp, i],
+            "pft_ct_copy_out": [vp, vp, c_void_p],
+            "pft_ct_reduce_sum": [vp, c_void_p, i, d, i, vp],
             "pft_mul_const": [vp, vp, d, d, vp], "pft_ct_set_scale": [vp, d],
             "pft_ntt": [vp, c_void_p, i, i, i],
             "pft_rescale_noalloc": [vp, c_void_p, i, c_void_p],
@@ -179,7 +181,7 @@ def exported_symbols():
             "pft_fasttext_train_backward", "pft_ft_tape_destroy", "pft_fasttext_train_update",
             "pft_ct_export_batch_async", "pft_device_status", "pft_wait_selftest", "pft_ft_enc_model_create_diag",
             "pft_run_jobs", "pft_bfly_ceiling", "pft_ct_import_batch_into", "pft_mul_rates",
-            "pft_autotune_report", "pft_set_transform_plan"]
+            "pft_autotune_report", "pft_set_transform_plan", "pft_ct_copy_out", "pft_ct_reduce_sum"]
 
 
 def _check(rc, ctx=None):
@@ -578,6 +580,16 @@ def pft_autotune_report(ctx):
     buf = ctypes.create_string_buffer(n.value + 1)
     _check(lib().pft_autotune_report(ctx, buf, n.value + 1, None), ctx)
     return json.loads(buf.value.decode())
+
+
+def pft_ct_copy_out(ctx, ct, dev_ptr):
+    """Copy ct's [2][l][N] words (evaluation layout) to caller device memory (int pointer)."""
+    _check(lib().pft_ct_copy_out(ctx, ct, c_void_p(dev_ptr)), ctx)
+
+
+def pft_ct_reduce_sum(ctx, dev_ptr, level, scale, n_terms, out):
+    """out = the ciphertext whose words are the integer sums at dev_ptr reduced mod each prime."""
+    _check(lib().pft_ct_reduce_sum(ctx, c_void_p(dev_ptr), level, scale, n_terms, out), ctx)
 
 
 def pft_set_transform_plan(ctx, plan):

@@ -1616,6 +1616,35 @@ int pft_ct_data(const pft_ct* ct, uint64_t** p) {
     return PFT_OK;
 }
 
+int pft_ct_copy_out(pft_ctx* c, const pft_ct* ct, uint64_t* dst) {
+    return guard(c, [&] {
+        NEED(c && dst, PFT_ERR_ARG, "null argument");
+        check_ct(c, ct);
+        PFT_CUDA(cudaMemcpyAsync(dst, ct->data, (size_t)2 * ct->level * c->n * 8, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    });
+}
+
+int pft_ct_reduce_sum(pft_ctx* c, const uint64_t* words, int level, double scale, int n_terms, pft_ct* out) {
+    return guard(c, [&] {
+        NEED(c && words, PFT_ERR_ARG, "null argument");
+        NEED(level >= 1 && level <= c->L, PFT_ERR_ARG, "level must be in 1..L");
+        NEED(n_terms >= 1, PFT_ERR_ARG, "n_terms must be positive");
+        u64 qmax = 0;
+        for (int r = 0; r < level; r++) qmax = std::max(qmax, c->primes[r]);
+        NEED((unsigned __int128)n_terms * (qmax - 1) < ((unsigned __int128)1 << 64), PFT_ERR_ARG,
+             "n_terms canonical residues can exceed 64 bits: exchange by gathering instead");
+        ensure_ct(c, out, level);
+        out->scale = scale;
+        std::vector<PolyRef> in, o;
+        for (int pol = 0; pol < 2; pol++) {
+            in.push_back(ref((u64*)words + (size_t)pol * level * c->n, level));
+            o.push_back(ref(out->data + (size_t)pol * level * c->n, level));
+        }
+        reduce_words(c->tabs, mkset(in, 0, 2), mkset(o, 0, 2), c->stream);
+    });
+}
+
 static pft_pt* new_pt(pft_ctx* c) {
     pft_pt* p = new pft_pt();
     p->ctx = c;

@@ -226,6 +226,8 @@ void sample_uniform(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32
 void sample_small(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 sub, int kind, const u32* cdt,
                   int nt, i64* out_dev, cudaStream_t st);  // kind 0 = ternary, 1 = Gaussian
 void reduce_signed(const DevTables& t, const i64* x_dev, const PolySet& out, cudaStream_t st);
+// out = in mod q per limb, for words of any 64-bit value (e.g. exact integer sums of residues)
+void reduce_words(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
 
 // ---- host math (encode.cpp) -----------------------------------------------------------
 std::vector<u64> gen_primes(int logn, int bits, int count, const std::vector<u64>& exclude);

@@ -618,11 +618,16 @@ __global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt,
 // of kKsStages shared-memory stages (one input's digits, 2 KiB each) filled by one thread
 // with 1-D bulk copies whose bytes an mbarrier per stage counts: the CTA computes input u
 // while the copies of the next inputs are in flight.  Every wait is bounded; on expiry the
-// kernel records the failure in g_wait_timeout, waits (bounded) for its own copies in
-// flight and returns.
+// kernel records the failure in g_wait_timeout, then drains its own copies in flight: one
+// thread waits for every stage that still expects bytes, with a bound 16 times the first
+// (kDrainPolls), before the CTA returns.  A copy of 2 KiB per digit row lands in microseconds;
+// only a memory system that has stopped answering could outlast both bounds, and then the CTA
+// returns with the copy still pending and its results flagged invalid (the host reads
+// PFT_ERR_TIMEOUT from pft_device_status).
 constexpr int kKsStages = 3;
 constexpr int kKsChunk = 256;                // coefficients per CTA (2 KiB per digit row)
 constexpr long long kWaitPolls = 1ll << 22;  // polls of a bounded wait (seconds at most)
+constexpr long long kDrainPolls = kWaitPolls << 4;  // polls of the drain after an expired wait
 
 __device__ int g_wait_timeout;
 
@@ -649,8 +654,8 @@ __device__ __forceinline__ bool mbar_test(u64* bar, u32 parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity) {
-    for (long long i = 0; i < kWaitPolls; i++)
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, long long polls = kWaitPolls) {
+    for (long long i = 0; i < polls; i++)
         if (mbar_test(bar, parity)) return true;
     return false;
 }
@@ -716,10 +721,10 @@ __global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, 
             // record, then wait (bounded) for the copies still in flight on the other stages
             if (threadIdx.x == 0) {
                 atomicExch(&g_wait_timeout, 1);
-                mbar_wait(&bars[s], parity);
+                mbar_wait(&bars[s], parity, kDrainPolls);
                 int uu = u + 1;
                 for (int bb = next(b + 1); bb < ib; bb = next(bb + 1), uu++)
-                    mbar_wait(&bars[uu % kKsStages], (u32)((uu / kKsStages) & 1));
+                    mbar_wait(&bars[uu % kKsStages], (u32)((uu / kKsStages) & 1), kDrainPolls);
             }
             return;
         }
@@ -1082,6 +1087,26 @@ void reduce_signed(const DevTables& t, const i64* x_dev, const PolySet& out, cud
     PFT_PROF("reduce_signed", st, 0.0);
     k_reduce_signed<<<grid, 256, 0, st>>>(t, x_dev, out);
     PFT_LAUNCH_CHECK("reduce_signed");
+}
+
+// words of `in` (any 64-bit values) -> residues modulo each limb's prime in `out`
+__global__ void k_reduce_words(DevTables t, PolySet in, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= t.n) return;
+    const DPrime P = load_prime(t.primes, prime_of(Ro, limb));
+    const size_t o = ((size_t)limb << t.logn) + c;
+    Ro.ptr[o] = reduce64(in.p[poly].ptr[o], P);
+}
+
+void reduce_words(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("reduce_words", st, set_limbs(out) * t.n * 16.0);
+    k_reduce_words<<<grid, 256, 0, st>>>(t, in, out);
+    PFT_LAUNCH_CHECK("reduce_words");
 }
 
 }  // namespace pft
