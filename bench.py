@@ -368,8 +368,8 @@ def run_gpu(args):
 
     sv = None
     if args.serve > 0:
-        sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_low_load,
-                           args.serve_diag > 0)
+        sv = serve_measure(pft, torch, args.serve, args.serve_rate, args.serve_budget_gib, args.serve_near,
+                           args.serve_fig3 > 0)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -637,29 +637,36 @@ SV_RINGS = [  # (log_n, limbs, special primes, primes per digit, request levels)
     (16, 30, 4, 4, (12, 30)),
     (15, 18, 2, 2, (12, 18)),
 ]
-SV_WORKLOAD = ("Poisson arrivals of encrypted fastText inferences (vocab 32768, dim 64, 14 classes, the Fig. 3 "
-               "sequence); two rings, half the requests each: N=2^16 (60 + 29x40 bits + 4 special, digits of 4; "
-               "request levels U{12..30}) and N=2^15 (60 + 17x40 bits + 2 special, digits of 2; U{12..18}, "
+SV_WORKLOAD = ("Poisson arrivals of encrypted fastText inferences (vocab 32768, dim 64, 14 classes); two rings, half "
+               "the requests each: N=2^16 (60 + 29x40 bits + 4 special, digits of 4; request levels U{12..30}; "
+               "vocabulary in 1 ciphertext) and N=2^15 (60 + 17x40 bits + 2 special, digits of 2; U{12..18}, "
                "vocabulary in 2 ciphertexts); keys and models resident; inputs and scores in host memory")
 
 
-def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, seed=31):
+def serve_measure(pft, torch, n_req, rate, budget_gib, near, fig3_leg=True, seed=31):
+    """Serving legs: the rotation-light sequence on both rings (diagonal packing; per vocabulary
+    chunk on the N=2^15 ring; inputs at 2^50) saturated at `rate`, then offered at `near` times
+    the measured capacity; and (fig3_leg) the Fig. 3 sequence (960 rotations per inference at
+    N=2^16, inputs at 2^40) saturated, for comparison."""
     from paper_1908_06972_gb300 import serving, synth
 
     H, O = synth.fasttext_weights(77, FT_M, FT_N, FT_C)
-    streams, ctxs, models = [], [], []
+    streams, ctxs = [], []
     for logn, lim, ksp, alpha, _ in SV_RINGS:
         st = torch.cuda.Stream()
         ctx = pft.pft_ctx_create(logn, lim, ksp, alpha, 60, 40, 60, 2.0 ** 40, SEED, stream=st.cuda_stream)
-        pft.pft_keygen(ctx, [1 << i for i in range(logn - 1)], False)
-        models.append(pft.pft_ft_model_create(ctx, H, O, lim))
+        steps = [1 << i for i in range(logn - 1)] + list(range(3, FT_N))  # TotalSum; diagonal shifts 1..n-1
+        pft.pft_keygen(ctx, steps, False)
         streams.append(st)
         ctxs.append(ctx)
     torch.cuda.synchronize()
+    seqs = {"rotation_light": ([pft.pft_ft_model_create_diag(c, H, O, r[1]) for c, r in zip(ctxs, SV_RINGS)],
+                               2.0 ** 50, [[FT_N * cc for cc in range(FT_C)]] * len(SV_RINGS))}
+    if fig3_leg:
+        seqs["fig3"] = ([pft.pft_ft_model_create(c, H, O, r[1]) for c, r in zip(ctxs, SV_RINGS)], 2.0 ** 40,
+                        [list(range(FT_C))] * len(SV_RINGS))
 
-    scales = [2.0 ** 40] * len(SV_RINGS)
-
-    def trace(count, rate_, tseed):
+    def trace(count, rate_, tseed, scale):
         rng = np.random.default_rng(tseed)
         times = serving.poisson_arrivals(rate_, count, tseed)
         docs = synth.documents(tseed + 1, FT_M, count)
@@ -672,17 +679,17 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, 
             chunks = -(-FT_M // t)
             coeffs = np.zeros((chunks, 2, level, n), np.uint64)
             for c in range(chunks):
-                pt = pft.pft_encode(ctxs[r], docs[i][c * t:(c + 1) * t], scales[r], level)
+                pt = pft.pft_encode(ctxs[r], docs[i][c * t:(c + 1) * t], scale, level)
                 ct = pft.pft_encrypt(ctxs[r], pt, pft.PFT_ENC_SK, 40000 + 4 * i + c)
                 pft.pft_ct_export(ctxs[r], ct, coeffs[c])
                 pft.pft_ct_destroy(ct)
                 pft.pft_pt_destroy(pt)
             out = np.zeros((2, level - 2, n), np.uint64)
-            reqs.append(serving.Request(t=float(times[i]), ring=r, level=level, scale=scales[r], coeffs=coeffs,
+            reqs.append(serving.Request(t=float(times[i]), ring=r, level=level, scale=scale, coeffs=coeffs,
                                         out=out, tag=i))
         return reqs, docs
 
-    def run(reqs):
+    def run(models, reqs):
         srv = pft.pft_server_create(ctxs, models, int(budget_gib * 2 ** 30))
         try:
             return serving.replay(srv, reqs)
@@ -697,13 +704,6 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, 
                 "requests_per_ring": [sum(1 for q in reqs if q.ring == r) for r in range(len(SV_RINGS))],
                 "mean_level": round(float(np.mean([q.level for q in reqs])), 2)}
 
-    fig3_model0 = models[0]
-    warm, _ = trace(2, 1000.0, seed + 100)  # kernels loaded, allocator pools grown
-    run(warm)
-    reqs, docs = trace(n_req, rate, seed)
-    res = run(reqs)
-    out = {"workload": SV_WORKLOAD, "unit": "inferences/s", "budget_gib": budget_gib,
-           "saturated": summary(res, reqs, rate)}
     def accuracy(res, reqs, docs, slots):
         """Decrypt the first request of each ring against FP64 Algorithm 1."""
         err = 0.0
@@ -719,31 +719,20 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, low_load, diag_leg=True, 
             err = max(err, float(np.max(np.abs(got - fp64_scores(docs[q.tag], H, O)))))
         return err
 
-    fig3_slots = [list(range(FT_C))] * len(SV_RINGS)
-    out["max_abs_err_vs_fp64"] = accuracy(res, reqs, docs, fig3_slots)
-    if low_load > 0:
-        rate_low = low_load * res.throughput()
-        reqs_low, _ = trace(n_req, rate_low, seed + 7)
-        out["under_capacity"] = summary(run(reqs_low), reqs_low, rate_low)
-    if diag_leg:
-        # the same saturated trace with the rotation-light sequence on the N = 2^16 ring (its
-        # vocabulary fits one ciphertext there; inputs at 2^50, scores in slots 64 c)
-        logn0 = SV_RINGS[0][0]
-        pft.pft_add_rotation_keys(ctxs[0], list(range(1, FT_N)) + [FT_N << k for k in range(logn0 - 1 - 6)])
-        dmodel = pft.pft_ft_model_create_diag(ctxs[0], H, O, SV_RINGS[0][1])
-        models[0] = dmodel  # the server of run() now serves ring 0 with the diagonal model
-        scales[0] = 2.0 ** 50
-        warm_d, _ = trace(2, 1000.0, seed + 101)
-        run(warm_d)
-        reqs_d, docs_d = trace(n_req, rate, seed)
-        res_d = run(reqs_d)
-        out["rotation_light_ring16"] = summary(res_d, reqs_d, rate)
-        out["rotation_light_ring16"]["max_abs_err_vs_fp64"] = accuracy(
-            res_d, reqs_d, docs_d, [[FT_N * c for c in range(FT_C)]] + fig3_slots[1:])
-        models[0] = fig3_model0
-        pft.pft_ft_model_destroy(dmodel)
-    for m in models:
-        pft.pft_ft_model_destroy(m)
+    out = {"workload": SV_WORKLOAD, "unit": "inferences/s", "budget_gib": budget_gib}
+    for name, (models, scale, slots) in seqs.items():
+        warm, _ = trace(2, 1000.0, seed + 100, scale)  # kernels loaded, allocator pools grown
+        run(models, warm)
+        reqs, docs = trace(n_req, rate, seed, scale)
+        res = run(models, reqs)
+        leg = {"saturated": summary(res, reqs, rate), "max_abs_err_vs_fp64": accuracy(res, reqs, docs, slots)}
+        if name == "rotation_light" and near > 0:
+            rate_near = near * res.throughput()
+            reqs_n, _ = trace(n_req, rate_near, seed + 7, scale)
+            leg["near_capacity"] = summary(run(models, reqs_n), reqs_n, rate_near)
+        out[name] = leg
+        for m in models:
+            pft.pft_ft_model_destroy(m)
     for c in ctxs:
         pft.pft_ctx_destroy(c)
     return out
@@ -1279,13 +1268,13 @@ def main():
     ap.add_argument("--train-diag", type=int, default=1, help="also time the rotation-light training layout (0: skip)")
     ap.add_argument("--queue", type=int, default=10, help="repetitions of the two-ring job-queue leg (0: skip)")
     ap.add_argument("--ops", type=int, default=20, help="repetitions of each primitive at the top level (0: skip)")
-    ap.add_argument("--serve", type=int, default=48, help="requests in the serving trace (0: skip)")
+    ap.add_argument("--serve", type=int, default=96, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load of the serving trace (req/s)")
     ap.add_argument("--serve-budget-gib", type=float, default=48.0, help="admission budget of the server")
-    ap.add_argument("--serve-diag", type=int, default=1,
-                    help="also serve with the rotation-light sequence on the N=2^16 ring")
-    ap.add_argument("--serve-low-load", type=float, default=0.7,
-                    help="second trace offered at this fraction of the measured throughput (0: skip)")
+    ap.add_argument("--serve-fig3", type=int, default=1,
+                    help="also serve the Fig. 3 sequence (the rotation-light one is the default)")
+    ap.add_argument("--serve-near", type=float, default=0.9,
+                    help="second trace offered at this fraction of the measured capacity (0: skip)")
     args = ap.parse_args()
     if args.case == "ntt":
         run_case_ntt(args)

@@ -432,20 +432,22 @@ int pft_ft_model_create(pft_ctx* ctx, const double* H, const double* O, int m, i
 int pft_ft_model_import(pft_ctx* ctx, const pft_pt* const* H_pts, const pft_pt* const* O_pts, int m, int n,
                         int c, pft_ft_model** out);
 int pft_ft_model_destroy(pft_ft_model* model);
-/* Rotation-light variant (not in the paper): diagonal packing D_k[i] = H[(i+k) mod t, i mod n]
- * (k < n, at `level`) and P[n c' + j] = O[j, c'] (one plaintext, level-1).  Inference computes
- * Q = sum_k rot(v, k) D_k with n-1 hoisted rotations, Q += rot(Q, n 2^s) while n 2^s < t,
- * rescale, S = Q P, S += rot(S, 2^s) while 2^s < n, rescale: n - 1 + log2(t/n) + log2(n)
- * rotations (78 for n = 64, t = 32768) instead of n log2(t) (960), n - 1 of them sharing one
- * ModUp.  Needs m <= t, n a power of two dividing t, n c <= t, rotation keys for 1..n-1 and
- * n 2^s.  Scores land in slots n c' (c' < c), not 0..c-1.  The input is rotated before its
- * plaintext product, so key-switching noise is relative to the input's scale: encrypt v at a
- * scale of 2^50 or more (instead of 2^40) to keep the scores within 2^-20. */
+/* Rotation-light variant (not in the paper): diagonal packing, per vocabulary chunk i (rows
+ * i t .. i t + t - 1 of H, ceil(m/t) chunks) D_{i,k}[s] = H[i t + (s+k) mod t, s mod n] (k < n, at
+ * `level`; plaintext i n + k) and P[n c' + j] = O[j, c'] (one plaintext, level-1).  Inference
+ * computes Q = sum_i sum_k rot(v_i, k) D_{i,k} with n-1 hoisted rotations per chunk,
+ * Q += rot(Q, n 2^s) while n 2^s < t, rescale, S = Q P, S += rot(S, 2^s) while 2^s < n,
+ * rescale: chunks (n - 1) + log2(t/n) + log2(n) rotations (78 for one chunk, n = 64,
+ * t = 32768) instead of n log2(t) (960), the n - 1 of a chunk sharing one ModUp.  Needs n a
+ * power of two dividing t, n c <= t, rotation keys for 1..n-1 and n 2^s.  Scores land in slots
+ * n c' (c' < c), not 0..c-1.  The input is rotated before its plaintext product, so
+ * key-switching noise is relative to the input's scale: encrypt v at a scale of 2^50 or more
+ * (instead of 2^40) to keep the scores within 2^-20. */
 int pft_ft_model_create_diag(pft_ctx* ctx, const double* H, const double* O, int m, int n, int c, int level,
                              pft_ft_model** out);
 int pft_ft_model_import_diag(pft_ctx* ctx, const pft_pt* const* D_pts, const pft_pt* P_pt, int m, int n, int c,
                              pft_ft_model** out);
-/* Scores of one document: v = ceil(m/t) ciphertexts at one level l, 3 <= l <= the model
+/* Scores of one document: v = ceil(m/t) ciphertexts at one level l (either packing), 3 <= l <= the model
  * level (the client's count vector, already divided by w; a model encoded at level L serves
  * every l <= L through the first l limbs of its plaintexts, which equal the encoding at
  * level l).  Sequence: h_j = TotalSum(sum_i v_i * H_{j,i}) with TotalSum rotating by 2^i,
@@ -495,7 +497,7 @@ int pft_server_destroy(pft_server* srv);
 /* Text of the last error on srv; srv = NULL: of the last failed pft_server_create. */
 const char* pft_server_last_error(const pft_server* srv);
 /* Queues one request.  in: host [chunks][2][level][N] u64 in coefficient form, canonical
- * residues (chunks = ceil(m/t), 1 for the diagonal variant), at `scale`; out: host
+ * residues (chunks = ceil(m/t) for both packings), at `scale`; out: host
  * buffer of 2 (level-2) N words that receives the score in the same form.  Both stay
  * owned by the caller and must stay valid until the request is returned by
  * pft_server_poll (the inputs are read at admission).  PFT_ERR_OOM if the request's

@@ -77,18 +77,32 @@ def column_total_sum(orc, v_cts, H_pts_j):
 # Output layer: S = Q * P with P[n c + j] = O[j, c]; a rotate-and-sum with steps 2^s, s < log2 n,
 # leaves s_c = sum_j h_j O[j, c] in slot n c.
 
-def pack_diag(H, O, t):
-    """Slot vectors of the diagonal packing: D [n][t] and P [t]."""
+# A vocabulary larger than one ciphertext (m > t) comes in chunks v_i = v[i t : i t + t]: with
+# H_i the rows i t .. i t + t - 1 of H, h_j = sum_i sum_u v_i[u] H_i[u, j], so every chunk gets
+# its own diagonals D_{i,k}[s] = H_i[(s + k) mod t, s mod n] and its own hoisted rotations, and
+# Q = sum_i sum_k rot(v_i, k) D_{i,k}; the rest of the sequence is unchanged.
+
+def pack_diag_chunks(H, O, t):
+    """Slot vectors of the diagonal packing of a vocabulary in ceil(m/t) chunks: D [chunks][n][t]
+    and P [t]."""
     m, n = H.shape
     c = O.shape[1]
-    Hp = np.zeros((t, n))
+    chunks = -(-m // t)
+    Hp = np.zeros((chunks * t, n))
     Hp[:m] = H
     i = np.arange(t)
-    D = np.stack([Hp[(i + k) % t, i % n] for k in range(n)])
+    D = np.stack([np.stack([Hp[ch * t + (i + k) % t, i % n] for k in range(n)]) for ch in range(chunks)])
     P = np.zeros(t)
     for cc in range(c):
         P[n * cc: n * cc + n] = O[:, cc]
     return D, P
+
+
+def pack_diag(H, O, t):
+    """Slot vectors of the diagonal packing of a vocabulary of at most t words: D [n][t] and P [t]."""
+    assert H.shape[0] <= t
+    D, P = pack_diag_chunks(H, O, t)
+    return D[0], P
 
 
 def diag_score_slots(n, c):
@@ -98,12 +112,21 @@ def diag_score_slots(n, c):
 
 def encrypted_scores_diag(orc, v_ct, D_pts, P_pt):
     """The rotation-light sequence on the oracle (one input ciphertext, m <= t)."""
-    n = len(D_pts)
+    return encrypted_scores_diag_chunks(orc, [v_ct], [D_pts], P_pt)
+
+
+def encrypted_scores_diag_chunks(orc, v_cts, D_pts, P_pt):
+    """The rotation-light sequence on the oracle for a vocabulary in chunks: v_cts[i] the chunk
+    ciphertexts, D_pts[i][k] the diagonals of chunk i; the products of chunk i, k = 0..n-1, are
+    added in that order after those of chunk i - 1."""
+    n = len(D_pts[0])
     t = orc.N // 2
-    R = [v_ct] + orc.rotate_hoisted(v_ct, list(range(1, n)))
-    Q = orc.mul_plain(R[0], D_pts[0])
-    for k in range(1, n):
-        Q = orc.add(Q, orc.mul_plain(R[k], D_pts[k]))
+    Q = None
+    for v_ct, Dc in zip(v_cts, D_pts):
+        R = [v_ct] + orc.rotate_hoisted(v_ct, list(range(1, n)))
+        for k in range(n):
+            term = orc.mul_plain(R[k], Dc[k])
+            Q = term if Q is None else orc.add(Q, term)
     s = n
     while s < t:
         Q = orc.add(Q, orc.rotate(Q, s))

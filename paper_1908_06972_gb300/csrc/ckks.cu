@@ -1051,10 +1051,7 @@ std::vector<FtStage> ft_program(pft_ctx* c, const pft_ft_model* M) {
 
 void ft_check_doc(pft_ctx* c, const pft_ft_model* M, const pft_ct* const* v, int n_chunks) {
     NEED(M && M->ctx == c, PFT_ERR_ARG, "model from another context");
-    if (M->variant == 1)
-        NEED(n_chunks == 1, PFT_ERR_ARG, "the diagonal variant takes one input ciphertext per document");
-    else
-        NEED(n_chunks == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
+    NEED(n_chunks == M->chunks, PFT_ERR_ARG, "number of input ciphertexts must be ceil(m/t)");
     NEED(v, PFT_ERR_ARG, "null input");
     for (int i = 0; i < n_chunks; i++) {
         check_ct(c, v[i]);
@@ -1159,19 +1156,22 @@ static void ft_finish_columns(pft_ctx* c, const pft_ft_model* M, const std::vect
 // BEGIN, diagonal packing: Q = sum_k rot(v, k) D_k, documents in chunks that bound the memory
 // of the rotated copies.
 static void ft_begin_diag(pft_ctx* c, const pft_ft_model* M, const std::vector<FtDoc*>& docs) {
-    const int cols = M->n;
+    const int cols = M->n, nch = M->chunks;
     const size_t limb = c->n;
     std::vector<int32_t> hsteps;
     for (int k = 1; k < cols; k++) hsteps.push_back(k);
     for (FtDoc* d : docs) ft_init_work(c, d, 1, d->v[0]->scale * M->H[0]->scale);
+    // per document: the n - 1 hoisted rotations of each vocabulary chunk, then one dot product
+    // Q = sum_i sum_k rot(v_i, k) D_{i,k} over all of them (K = chunks n terms)
+    const size_t rot_per_doc = (size_t)nch * (cols - 1);
     for (auto& kv : docs_by_level(docs)) {
         const int l = kv.first;
         const std::vector<FtDoc*>& G = kv.second;
-        const size_t per_doc = (size_t)(cols - 1) * 2 * l * limb * 8;
+        const size_t per_doc = rot_per_doc * 2 * l * limb * 8;
         const size_t chunk = std::max<size_t>(1, std::min<size_t>(G.size(), ((size_t)16 << 30) / per_doc));
         for (size_t b0 = 0; b0 < G.size(); b0 += chunk) {
             const size_t b1 = std::min(G.size(), b0 + chunk);
-            std::vector<pft_ct> R((b1 - b0) * (cols - 1));
+            std::vector<pft_ct> R((b1 - b0) * rot_per_doc);
             struct CleanR {
                 pft_ctx* c;
                 std::vector<pft_ct>* T;
@@ -1180,24 +1180,30 @@ static void ft_begin_diag(pft_ctx* c, const pft_ft_model* M, const std::vector<F
                 }
             } cleanR{c, &R};
             for (auto& x : R) x.ctx = c;
-            for (size_t b = b0; b < b1; b++) {
-                std::vector<pft_ct*> outs;
-                for (int k = 0; k < cols - 1; k++) outs.push_back(&R[(b - b0) * (cols - 1) + k]);
-                op_rotate_hoisted(c, G[b]->v[0], hsteps.data(), cols - 1, outs.data());
-            }
+            auto rot = [&](size_t b, int i, int k) -> pft_ct& {  // rot(v_i, k) of document b, k >= 1
+                return R[(b - b0) * rot_per_doc + (size_t)i * (cols - 1) + k - 1];
+            };
+            for (size_t b = b0; b < b1; b++)
+                for (int i = 0; i < nch; i++) {
+                    std::vector<pft_ct*> outs;
+                    for (int k = 1; k < cols; k++) outs.push_back(&rot(b, i, k));
+                    op_rotate_hoisted(c, G[b]->v[i], hsteps.data(), cols - 1, outs.data());
+                }
             std::vector<const u64*> A, Bv;
             std::vector<u64*> O;
-            for (int k = 0; k < cols; k++) Bv.push_back(M->H[k]->data);
+            for (int i = 0; i < nch; i++)
+                for (int k = 0; k < cols; k++) Bv.push_back(M->H[(size_t)i * cols + k]->data);
             for (size_t b = b0; b < b1; b++)
                 for (int pol = 0; pol < 2; pol++) {
-                    A.push_back(G[b]->v[0]->data + (size_t)pol * l * limb);
-                    for (int k = 1; k < cols; k++)
-                        A.push_back(R[(b - b0) * (cols - 1) + k - 1].data + (size_t)pol * l * limb);
+                    for (int i = 0; i < nch; i++) {
+                        A.push_back(G[b]->v[i]->data + (size_t)pol * l * limb);
+                        for (int k = 1; k < cols; k++) A.push_back(rot(b, i, k).data + (size_t)pol * l * limb);
+                    }
                     O.push_back(G[b]->W[0].data + (size_t)pol * l * limb);
                 }
             Scratch dA(c, A.size() * 8), dB(c, Bv.size() * 8), dO(c, O.size() * 8);
-            ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), cols, true, l,
-                   c->stream);
+            ew_dot(c->tabs, upload(c, dA, A), upload(c, dB, Bv), upload(c, dO, O), (int)O.size(), nch * cols, true,
+                   l, c->stream);
         }
     }
 }
@@ -2296,10 +2302,11 @@ int pft_ft_model_create_diag(pft_ctx* c, const double* H, const double* O, int m
                              pft_ft_model** out) {
     return guard(c, [&] {
         const int t = c ? c->n / 2 : 0;
-        NEED(c && H && O && out && m >= 1 && m <= t && n >= 2 && cl >= 1, PFT_ERR_ARG, "bad arguments");
+        NEED(c && H && O && out && m >= 1 && n >= 2 && cl >= 1, PFT_ERR_ARG, "bad arguments");
         NEED((n & (n - 1)) == 0 && t % n == 0 && (size_t)n * cl <= (size_t)t, PFT_ERR_ARG,
              "diagonal packing needs n a power of two dividing N/2 and n c <= N/2");
         NEED(level >= 3 && level <= c->L, PFT_ERR_ARG, "model level must be in 3..L");
+        const int nch = (m + t - 1) / t;
         std::vector<pft_pt*> dp, op;
         auto cleanup = [&] {
             for (auto p : dp) pft_pt_destroy(p);
@@ -2307,16 +2314,18 @@ int pft_ft_model_create_diag(pft_ctx* c, const double* H, const double* O, int m
         };
         std::vector<double> slots(2 * (size_t)t);
         int rc = PFT_OK;
-        for (int k = 0; k < n && rc == PFT_OK; k++) {  // D_k[i] = H[(i + k) mod t, i mod n] (zero rows >= m)
-            std::fill(slots.begin(), slots.end(), 0.0);
-            for (int i = 0; i < t; i++) {
-                const int row = (i + k) % t;
-                if (row < m) slots[2 * (size_t)i] = H[(size_t)row * n + (i % n)];
+        // chunk ch, diagonal k: D_{ch,k}[i] = H[ch t + (i + k) mod t, i mod n] (zero rows >= m)
+        for (int ch = 0; ch < nch && rc == PFT_OK; ch++)
+            for (int k = 0; k < n && rc == PFT_OK; k++) {
+                std::fill(slots.begin(), slots.end(), 0.0);
+                for (int i = 0; i < t; i++) {
+                    const size_t row = (size_t)ch * t + (i + k) % t;
+                    if (row < (size_t)m) slots[2 * (size_t)i] = H[row * n + (i % n)];
+                }
+                pft_pt* p = nullptr;
+                rc = pft_encode(c, slots.data(), t, c->prm.scale, level, &p);
+                if (rc == PFT_OK) dp.push_back(p);
             }
-            pft_pt* p = nullptr;
-            rc = pft_encode(c, slots.data(), t, c->prm.scale, level, &p);
-            if (rc == PFT_OK) dp.push_back(p);
-        }
         if (rc == PFT_OK) {  // P[n c + j] = O[j, c]
             std::fill(slots.begin(), slots.end(), 0.0);
             for (int cc = 0; cc < cl; cc++)
@@ -2334,7 +2343,7 @@ int pft_ft_model_create_diag(pft_ctx* c, const double* H, const double* O, int m
         M->m = m;
         M->n = n;
         M->c = cl;
-        M->chunks = 1;
+        M->chunks = nch;
         M->level = level;
         M->variant = 1;
         M->H = dp;
@@ -2347,15 +2356,16 @@ int pft_ft_model_import_diag(pft_ctx* c, const pft_pt* const* D_pts, const pft_p
                              pft_ft_model** out) {
     return guard(c, [&] {
         const int t = c ? c->n / 2 : 0;
-        NEED(c && D_pts && P_pt && out && m >= 1 && m <= t && n >= 2 && cl >= 1, PFT_ERR_ARG, "bad arguments");
+        NEED(c && D_pts && P_pt && out && m >= 1 && n >= 2 && cl >= 1, PFT_ERR_ARG, "bad arguments");
         NEED((n & (n - 1)) == 0 && t % n == 0 && (size_t)n * cl <= (size_t)t, PFT_ERR_ARG,
              "diagonal packing needs n a power of two dividing N/2 and n c <= N/2");
+        const int nch = (m + t - 1) / t;
         std::unique_ptr<pft_ft_model> M(new pft_ft_model());
         M->ctx = c;
         M->m = m;
         M->n = n;
         M->c = cl;
-        M->chunks = 1;
+        M->chunks = nch;
         M->level = D_pts[0]->level;
         M->variant = 1;
         auto copy_pt = [&](const pft_pt* p) {
@@ -2366,7 +2376,8 @@ int pft_ft_model_import_diag(pft_ctx* c, const pft_pt* const* D_pts, const pft_p
             PFT_CUDA(cudaMemcpyAsync(q->data, p->data, (size_t)p->level * c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
             return q;
         };
-        for (int k = 0; k < n; k++) {
+        for (int k = 0; k < nch * n; k++) {
+            check_pt(c, D_pts[k]);
             NEED(D_pts[k]->level == M->level, PFT_ERR_LEVEL_MISMATCH, "diagonal plaintexts at different levels");
             M->H.push_back(copy_pt(D_pts[k]));
         }

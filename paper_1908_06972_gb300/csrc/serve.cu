@@ -124,12 +124,12 @@ static int sguard(pft_server* s, F f) {
 }
 
 // Device bytes a request holds while admitted: its input ciphertexts, the working
-// ciphertexts of its sequence (the n columns; or Q, the n - 1 rotated copies and the
-// score of the diagonal variant), its score and the export copy, all at its level.
+// ciphertexts of its sequence (the n columns; or Q, the n - 1 rotated copies of each input
+// and the score of the diagonal variant), its score and the export copy, all at its level.
 static size_t footprint(const Ring& r, int level) {
     const size_t ct = (size_t)2 * level * r.ctx->n * 8;
     const int cols = r.M->n;
-    return (r.M->variant == 0 ? (size_t)(r.chunks + cols + 2) : (size_t)(cols + 3)) * ct;
+    return (r.M->variant == 0 ? (size_t)(r.chunks + cols + 2) : (size_t)(r.chunks * cols + 3)) * ct;
 }
 
 static void release_device(pft_ctx* c, Request* q) {
@@ -296,7 +296,7 @@ int pft_server_create(pft_ctx* const* ctxs, const pft_ft_model* const* models, i
             r.ctx = ctxs[i];
             r.M = models[i];
             r.prog = ft_program(r.ctx, r.M);
-            r.chunks = r.M->variant == 1 ? 1 : r.M->chunks;
+            r.chunks = r.M->chunks;
             for (const FtStage& st : r.prog)
                 if (st.kind == FT_ROT)
                     NEED(r.ctx->keys.count(st.g), PFT_ERR_NO_KEY, "ring " + std::to_string(i) + ": missing rotation key");

@@ -414,6 +414,35 @@ def test_fasttext_diagonal_bit_exact_n12(p1):
         pf.pft_ft_model_destroy(model)
 
 
+def test_fasttext_diagonal_chunks_bit_exact_n12(p1):
+    """Rotation-light matvec for a vocabulary of 2.5 ciphertexts (diagonals and hoisted rotations
+    per chunk), two documents in one call, against the oracle's sequence."""
+    o, pf, ctx = p1.orc, p1.pft, p1.ctx
+    t = p1.N // 2
+    m, n, c = 2 * t + t // 2, 8, 3
+    H, O = synth.fasttext_weights(21, m, n, c)
+    docs = synth.documents(22, m, 2, 20, 60)
+    D, P = OF.pack_diag_chunks(H, O, t)
+    D_o = [[o.encode(D[i, k], level=3) for k in range(n)] for i in range(3)]
+    P_o = o.encode(P, level=2)
+    model = pf.pft_ft_model_import_diag(ctx, [p1.pt(D_o[i][k]) for i in range(3) for k in range(n)], p1.pt(P_o),
+                                        m, n, c)
+    try:
+        v = np.zeros((2, 3 * t))
+        v[:, :m] = docs
+        v_o = [[o.encrypt_sk(o.encode(v[d, i * t:(i + 1) * t], level=3), 130 + 3 * d + i) for i in range(3)]
+               for d in range(2)]
+        scores = [p1.empty() for _ in range(2)]
+        pf.pft_fasttext_infer_batch(ctx, model, [p1.ct(x) for d in range(2) for x in v_o[d]], 3, scores)
+        for d in range(2):
+            want = OF.encrypted_scores_diag_chunks(o, v_o[d], D_o, P_o)
+            p1.assert_equal(scores[d], want, "fasttext diagonal, 3 chunks, doc %d" % d)
+            got = o.decode(o.decrypt(want)).real[OF.diag_score_slots(n, c)]
+            assert np.max(np.abs(got - OF.plain_scores(docs[d], H, O))) < 2.0 ** -20
+    finally:
+        pf.pft_ft_model_destroy(model)
+
+
 # ---- seeded compressed switching keys -----------------------------------------------------------
 @pytest.mark.parametrize("logn,L,k,alpha,mid", [(12, 3, 1, 1, 40), (12, 10, 1, 1, 40), (16, 6, 2, 4, 50)])
 def test_compressed_keys_bit_exact(gpu, logn, L, k, alpha, mid):

@@ -1,7 +1,8 @@
 """Request server (continuous batching of encrypted fastText inferences) on the GPU.
 
 Two rings of different N run through one server: N = 2^12 (vocabulary in one input
-ciphertext) and N = 2^11 (the same vocabulary spans two).  Documents at every level from
+ciphertext) and N = 2^11 (the same vocabulary spans two), both with the Fig. 3 sequence or both
+with the rotation-light one (diagonal packing, per vocabulary chunk at N = 2^11).  Documents at every level from
 3 to the top are submitted while others are in flight, so stages of different requests
 share iterations.  Every score must equal, bit for bit, the oracle's sequence at the
 request's level (model plaintexts encoded at that level: this pins that the top-level
@@ -27,17 +28,20 @@ class Ring:
         o, t, L = pair.orc, pair.N // 2, pair.orc.L
         self.t, self.L, self.diag = t, L, diag
         self.H, self.O = H, O
-        if diag:
-            D, P = OF.pack_diag(H, O, t)
-            self.model = gpu.pft_ft_model_import_diag(pair.ctx, [pair.pt(o.encode(D[k], level=L)) for k in range(N_COLS)],
-                                                      pair.pt(o.encode(P, level=L - 1)), M_VOCAB, N_COLS, N_CLS)
-            self.chunks = 1
+        if diag:  # rotation-light packing, one set of diagonals per vocabulary chunk
+            D, P = OF.pack_diag_chunks(H, O, t)
+            self.chunks = D.shape[0]
+            D_pts = [pair.pt(o.encode(D[i, k], level=L)) for i in range(self.chunks) for k in range(N_COLS)]
+            self.model = gpu.pft_ft_model_import_diag(pair.ctx, D_pts, pair.pt(o.encode(P, level=L - 1)), M_VOCAB,
+                                                      N_COLS, N_CLS)
+            self.score_slots = OF.diag_score_slots(N_COLS, N_CLS)
         else:
             Hp, Op = OF.pack_H(H, t), OF.pack_O(O, t)
             self.chunks = Hp.shape[1]
             H_pts = [pair.pt(o.encode(Hp[j, i], level=L)) for j in range(N_COLS) for i in range(self.chunks)]
             O_pts = [pair.pt(o.encode(Op[j], level=L - 1)) for j in range(N_COLS)]
             self.model = gpu.pft_ft_model_import(pair.ctx, H_pts, O_pts, M_VOCAB, N_COLS, N_CLS)
+            self.score_slots = list(range(N_CLS))
 
     def encrypt(self, doc, level, nonce):
         """The client's input: oracle ciphertexts (one per vocabulary chunk)."""
@@ -50,9 +54,9 @@ class Ring:
     def oracle_scores(self, v_o, level):
         o = self.p.orc
         if self.diag:
-            D, P = OF.pack_diag(self.H, self.O, self.t)
-            return OF.encrypted_scores_diag(o, v_o[0], [o.encode(D[k], level=level) for k in range(N_COLS)],
-                                            o.encode(P, level=level - 1))
+            D, P = OF.pack_diag_chunks(self.H, self.O, self.t)
+            D_o = [[o.encode(D[i, k], level=level) for k in range(N_COLS)] for i in range(self.chunks)]
+            return OF.encrypted_scores_diag_chunks(o, v_o, D_o, o.encode(P, level=level - 1))
         Hp, Op = OF.pack_H(self.H, self.t), OF.pack_O(self.O, self.t)
         H_o = [[o.encode(Hp[j, i], level=level) for i in range(self.chunks)] for j in range(N_COLS)]
         O_o = [o.encode(Op[j], level=level - 1) for j in range(N_COLS)]
@@ -69,16 +73,28 @@ class Ring:
 
 
 @pytest.fixture(scope="module")
-def rings(gpu):
-    H, O = synth.fasttext_weights(71, M_VOCAB, N_COLS, N_CLS)
+def pairs(gpu):
+    """N = 2^12 with digits of two 40-bit primes (Fig. 3), N = 2^11 and N = 2^12 with one prime per
+    digit.  The rotation-light sequence rotates its input at the input's scale, so it needs
+    key-switching noise well below that scale: digits no larger than the 60-bit special prime."""
     a = Pair(gpu, 12, 5, 1, 2, seed=(0xA1, 2, 3, 4), rot_steps=[1 << i for i in range(11)] + [3])
-    b = Pair(gpu, 11, 4, 1, 1, seed=(0xB2, 2, 3, 4), rot_steps=[1 << i for i in range(10)])
-    rs = [Ring(gpu, a, H, O), Ring(gpu, b, H, O)]
+    b = Pair(gpu, 11, 4, 1, 1, seed=(0xB2, 2, 3, 4), rot_steps=[1 << i for i in range(10)] + [3])
+    a1 = Pair(gpu, 12, 5, 1, 1, seed=(0xA3, 2, 3, 4), rot_steps=[1 << i for i in range(11)] + [3])
+    yield a, b, a1
+    for p in (a, b, a1):
+        p.close()
+
+
+@pytest.fixture(scope="module", params=["fig3", "rotation_light"])
+def rings(gpu, pairs, request):
+    """The two rings serving the Fig. 3 sequence, or both serving the rotation-light one (the
+    N = 2^11 ring's vocabulary spans two ciphertexts: diagonals per chunk)."""
+    H, O = synth.fasttext_weights(71, M_VOCAB, N_COLS, N_CLS)
+    diag = request.param == "rotation_light"
+    rs = [Ring(gpu, pairs[2] if diag else pairs[0], H, O, diag=diag), Ring(gpu, pairs[1], H, O, diag=diag)]
     yield rs
     for r in rs:
         r.close()
-    a.close()
-    b.close()
 
 
 def submit(pf, srv, ring, v_o, level, tag, keep):
@@ -143,7 +159,7 @@ def test_server_mix_equals_alone_and_oracle(gpu, rings):
             want = ring.oracle_scores(inputs[i], lv)
             assert np.array_equal(got, want.c), "request %d differs from the oracle" % i
             assert d["scale"] == want.scale
-            dec = ring.p.orc.decode(ring.p.orc.decrypt(OK.Ciphertext(got, d["scale"])))[:N_CLS].real
+            dec = ring.p.orc.decode(ring.p.orc.decrypt(OK.Ciphertext(got, d["scale"]))).real[ring.score_slots]
             assert np.max(np.abs(dec - OF.plain_scores(docs[i], ring.H, ring.O))) < 2.0 ** -20
 
 
@@ -211,11 +227,11 @@ def test_server_rejects_bad_requests(gpu, rings):
     assert e.value.code == pf.PFT_ERR_ARG and "context of its own" in str(e.value)
 
 
-def test_server_diagonal_variant_bit_exact(gpu, rings):
+def test_server_diagonal_variant_bit_exact(gpu, pairs):
     """The rotation-light sequence through the server: two documents at levels 5 and 3."""
     pf = gpu
-    base = rings[0]
-    ring = Ring(gpu, base.p, base.H, base.O, diag=True)
+    H, O = synth.fasttext_weights(71, M_VOCAB, N_COLS, N_CLS)
+    ring = Ring(gpu, pairs[2], H, O, diag=True)
     try:
         docs = synth.documents(74, M_VOCAB, 2, 20, 80)
         levels = [5, 3]

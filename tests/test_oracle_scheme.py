@@ -261,6 +261,30 @@ def test_fasttext_diagonal_variant(small):
     assert np.max(np.abs(got - fasttext.plain_scores(v[:m], H, O))) < 2 ** -20
 
 
+def test_fasttext_diagonal_variant_chunks(small):
+    """The rotation-light matvec for a vocabulary of more than one ciphertext (m = 2.5 t in
+    three chunks): per-chunk diagonal identity in FP64, and the encrypted sequence within 2^-20
+    of Algorithm 1."""
+    orc = small
+    t = orc.N // 2
+    m, n, c = 2 * t + t // 2, 8, 3
+    H = rng.normal(0, 0.1, (m, n))
+    O = rng.normal(0, 0.1, (n, c))
+    v = np.bincount(rng.integers(0, m, 40), minlength=3 * t) / 40.0
+    D, P = fasttext.pack_diag_chunks(H, O, t)
+    assert D.shape == (3, n, t)
+    Q = sum(np.roll(v[i * t:(i + 1) * t], -k) * D[i, k] for i in range(3) for k in range(n))
+    h = np.array([Q[j::n].sum() for j in range(n)])
+    assert np.allclose(h, v[:m] @ H, atol=1e-12)
+    l = orc.L
+    D_pts = [[orc.encode(D[i, k], level=l) for k in range(n)] for i in range(3)]
+    P_pt = orc.encode(P, level=l - 1)
+    v_cts = [orc.encrypt_sk(orc.encode(v[i * t:(i + 1) * t], level=l), 90 + i) for i in range(3)]
+    S = fasttext.encrypted_scores_diag_chunks(orc, v_cts, D_pts, P_pt)
+    got = orc.decode(orc.decrypt(S)).real[fasttext.diag_score_slots(n, c)]
+    assert np.max(np.abs(got - fasttext.plain_scores(v[:m], H, O))) < 2 ** -20
+
+
 def test_compressed_keys_draw_a_in_the_evaluation_layout(small_compressed):
     """a_j of a compressed key evaluates, at the layout points, to the stream's uniform
     residues (the values the inner product regenerates), and differs from the full key's."""
