@@ -54,11 +54,17 @@ __device__ __forceinline__ void split30(u64 a, u32& lo, u32& hi) {
     lo = (u32)a & 0x3fffffffu;
     hi = (u32)(a >> 30);
 }
+// acc + a b as one widening multiply-add (32 x 32 + 64 -> 64)
+__device__ __forceinline__ u64 mad_wide(u32 a, u32 b, u64 acc) {
+    u64 r;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(acc));
+    return r;
+}
 __device__ __forceinline__ void acc3_mac(Acc3& A, u32 a0, u32 a1, u32 b0, u32 b1) {
-    A.s00 += (u64)a0 * b0;
-    A.s01 += (u64)a0 * b1;
-    A.s01 += (u64)a1 * b0;
-    A.s11 += (u64)a1 * b1;
+    A.s00 = mad_wide(a0, b0, A.s00);
+    A.s01 = mad_wide(a0, b1, A.s01);
+    A.s01 = mad_wide(a1, b0, A.s01);
+    A.s11 = mad_wide(a1, b1, A.s11);
 }
 // Karatsuba form for at most 4 terms: S00 = sum a0 b0, S11 = sum a1 b1 and
 // SM = sum (a0 + a1)(b0 + b1) (each factor below 2^31, so 4 terms stay below 2^64);
@@ -67,9 +73,9 @@ struct Acc3K {
     u64 s00, sm, s11;
 };
 __device__ __forceinline__ void acc3k_mac(Acc3K& A, u32 a0, u32 a1, u32 a01, u32 b0, u32 b1, u32 b01) {
-    A.s00 += (u64)a0 * b0;
-    A.s11 += (u64)a1 * b1;
-    A.sm += (u64)a01 * b01;
+    A.s00 = mad_wide(a0, b0, A.s00);
+    A.s11 = mad_wide(a1, b1, A.s11);
+    A.sm = mad_wide(a01, b01, A.sm);
 }
 __device__ __forceinline__ Acc3 acc3k_fold(const Acc3K& A) { return Acc3{A.s00, A.sm - A.s00 - A.s11, A.s11}; }
 // the 128-bit value S00 + 2^30 S01 + 2^60 S11

@@ -125,11 +125,15 @@ __device__ __forceinline__ u64 canon8(u64 v, u64 q, u64 q2) {
 // LM (the row round W0 = 0 of stages 12..15, thread = row r, lane w): the twiddles come from
 // the lane-major copy of that round's twiddles, lm = its entries for (prime, row r, lane w):
 // slot (2^k - 1 + j) of stage 12 + k at lm[16 (2^k - 1 + j)].
-template <bool INV, int W0, int DIMHI, bool LAZY = false, bool UNSCALED = false, bool LM = false>
+// RT (the row round W0 = 4 of stages 8..11, thread = row r): the row's 15 twiddles of those
+// stages were copied to shared memory, stage 8 + k entry j at rt[2^k - 1 + j].
+template <bool INV, int W0, int DIMHI, bool LAZY = false, bool UNSCALED = false, bool LM = false, bool RT = false>
 __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, const ulonglong2* __restrict__ tw,
                                             u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1,
-                                            const ulonglong2* __restrict__ lm = nullptr) {
+                                            const ulonglong2* __restrict__ lm = nullptr,
+                                            const ulonglong2* rt = nullptr) {
     static_assert(!LM || (W0 == 0 && DIMHI == 8), "lane-major twiddles serve the row round of stages 12..15");
+    static_assert(!RT || (W0 == 4 && DIMHI == 8), "staged row twiddles serve the row round of stages 8..11");
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int lb = INV ? k : 3 - k;
@@ -140,7 +144,9 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
             if (e & (1 << lb)) continue;
             const int elem = (e << W0) | wpart;
             const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
-            const ulonglong2 W = LM ? __ldg(&lm[16 * ((1 << (s - 12)) - 1 + (e >> (p + 1)))]) : __ldg(&tw[idx]);
+            const ulonglong2 W = LM   ? __ldg(&lm[16 * ((1 << (s - 12)) - 1 + (e >> (p + 1)))])
+                                 : RT ? rt[(1 << (s - 8)) - 1 + (elem >> (p + 1))]
+                                      : __ldg(&tw[idx]);
             if (!INV) {
                 ct_bfly<LAZY>(x[e], x[e | (1 << lb)], W, q, q2);
             } else if (s == 0 && !UNSCALED) {  // last inverse stage: N^-1 folded into both outputs
@@ -343,6 +349,18 @@ __device__ __forceinline__ u64 reduce_below66(u64 x, u64 q, u32 r, u32 sh) {
 // lane-major copy holds, per prime and row, [15 slots][16 lanes] (slot 2^k - 1 + j), so the 16
 // lanes of a row read 256 contiguous bytes per load.
 constexpr int kRowTwSlots = 15;
+// The 16 rows' twiddles of stages 8..11 (row u: entry 2^(8+k) + u 2^k + j, k < 4, j < 2^k) into
+// rt[16][15]: one 16-byte load and store for 240 of the 256 threads, made visible by the caller's
+// next barrier.
+__device__ __forceinline__ void stage_row_round1(const ulonglong2* __restrict__ tw, int u0, ulonglong2* rt) {
+    const int t = threadIdx.x;
+    if (t < 16 * 15) {
+        const int cc = t / 15, e = t % 15;
+        const int k = e >= 7 ? 3 : e >= 3 ? 2 : e >= 1 ? 1 : 0;
+        const int j = e + 1 - (1 << k);
+        rt[t] = __ldg(&tw[(1 << (8 + k)) + ((u0 + cc) << k) + j]);
+    }
+}
 __device__ __forceinline__ const ulonglong2* lm_base(const ulonglong2* rows, int pi, int u, int w) {
     return rows + ((size_t)pi * 256 + u) * (kRowTwSlots * 16) + w;
 }
@@ -360,13 +378,16 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
     const ulonglong2* tw = t.fwd + ((size_t)pi << logn);
     const ulonglong2 NI = make_ulonglong2(0, 0);
     const ulonglong2* lm = LM ? lm_base(t.fwd_rows, pi, u, w) : nullptr;
+    __shared__ ulonglong2 rt[16 * 15];  // LM: twiddles of stages 8..11 of the 16 rows
     u64* my = sm + cc * kRowStride;
     u64 x[16];
     const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
+    if (LM) stage_row_round1(tw, blockIdx.x * 16, rt);
 #pragma unroll
     for (int e = 0; e < 16; e++) x[e] = src[((size_t)u << 8) | (e << 4) | w];
-    if (lazy) ntt16_round<false, 4, 8, true>(x, w, u, tw, q, q2, NI, NI);
-    else ntt16_round<false, 4, 8>(x, w, u, tw, q, q2, NI, NI);
+    if (LM) __syncthreads();
+    if (lazy) ntt16_round<false, 4, 8, true, false, false, LM>(x, w, u, tw, q, q2, NI, NI, nullptr, rt + cc * 15);
+    else ntt16_round<false, 4, 8, false, false, false, LM>(x, w, u, tw, q, q2, NI, NI, nullptr, rt + cc * 15);
 #pragma unroll
     for (int e = 0; e < 16; e++) my[e * 17 + w] = x[e];  // point e*16 + w
     __syncthreads();
