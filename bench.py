@@ -365,6 +365,7 @@ def run_gpu(args):
     qu = None
     if args.queue > 0:
         qu = queue_measure(pft, torch, args.queue)
+        qu["two_ring_keyswitch"] = rings_measure(pft, torch, synth, 10)
 
     sv = None
     if args.serve > 0:
@@ -441,6 +442,82 @@ def graph_measure(pft, torch, synth, steps, warmup, rank, world):
         pft.pft_ct_destroy(h)
     pft.pft_ctx_destroy(ctx)
     return throughput(BATCH * steps, world, ms / 1e3)
+
+
+RG_WORKLOAD = ("key switching of the two serving rings in one step: N=2^16 (60 + 29x40 bits + 4 special, digits of "
+               "4) and N=2^15 (60 + 17x40 bits + 2 special, digits of 2), 32 ciphertext pairs each at levels "
+               "U{12..30} / U{12..18}, one batched HMUL + relinearisation per ring")
+
+
+def rings_measure(pft, torch, synth, reps):
+    """The key-switch stages of both serving rings (uneven ring sizes and levels) issued three
+    ways: on one stream one ring after the other; on two streams concurrently; and captured
+    together into one CUDA graph (the second stream forked from and joined back into the first)
+    replayed as a single launch."""
+    streams, ctxs, work = [], [], []
+    for logn, lim, ksp, alpha, (lo, hi) in SV_RINGS:
+        st = torch.cuda.Stream()
+        ctx = pft.pft_ctx_create(logn, lim, ksp, alpha, 60, 40, 60, 2.0 ** 40, SEED, allocator=None,
+                                 stream=st.cuda_stream)
+        pft.pft_keygen(ctx, [], True)
+        lv = synth.batch_levels(32, lo, hi, seed=logn)
+        A, B = [], []
+        for i, l in enumerate(lv):
+            for lst, base in ((A, 100), (B, 300)):
+                pt = pft.pft_encode(ctx, synth.slots(base + i, 64), 2.0 ** 40, l)
+                lst.append(pft.pft_encrypt(ctx, pt, pft.PFT_ENC_SK, base + i))
+                pft.pft_pt_destroy(pt)
+        C = [pft.pft_ct_create(ctx) for _ in lv]
+        streams.append(st)
+        ctxs.append(ctx)
+        work.append((A, B, C))
+
+    def both():
+        for i in range(2):
+            pft.pft_mul_relin_batch(ctxs[i], *work[i])
+
+    def timed(fn, fork):
+        """Events on stream 0; with fork the second stream starts after and ends before them."""
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(streams[0])
+        if fork:
+            streams[1].wait_event(e0)
+        for _ in range(reps):
+            fn()
+        if fork:
+            j = torch.cuda.Event()
+            j.record(streams[1])
+            streams[0].wait_event(j)
+        e1.record(streams[0])
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    both()
+    out = {"workload": RG_WORKLOAD, "unit": "ms per step (both rings)"}
+    pft.pft_set_stream(ctxs[1], streams[0].cuda_stream)  # one stream
+    both()
+    out["one_stream"] = round(timed(both, False), 3)
+    pft.pft_set_stream(ctxs[1], streams[1].cuda_stream)  # each ring on its own stream
+    out["two_streams"] = round(timed(both, True), 3)
+    # one graph: capture on stream 0, fork stream 1 into the capture, join it back
+    pft.pft_graph_begin(ctxs[0])
+    f = torch.cuda.Event()
+    f.record(streams[0])
+    streams[1].wait_event(f)
+    both()
+    j = torch.cuda.Event()
+    j.record(streams[1])
+    streams[0].wait_event(j)
+    g = pft.pft_graph_end(ctxs[0])
+    pft.pft_graph_launch(ctxs[0], g)
+    out["one_graph_launch"] = round(timed(lambda: pft.pft_graph_launch(ctxs[0], g), False), 3)
+    pft.pft_graph_destroy(g)
+    for ctx, (A, B, C) in zip(ctxs, work):
+        for h in A + B + C:
+            pft.pft_ct_destroy(h)
+        pft.pft_ctx_destroy(ctx)
+    return out
 
 
 # ---- encrypted fastText inference (Sec. 3.1, Fig. 3) ------------------------------------------------
