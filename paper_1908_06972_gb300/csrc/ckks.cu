@@ -73,6 +73,39 @@ static T* tab_upload(pft_ctx* c, const std::vector<T>& v) {
     return p;
 }
 
+namespace pft {
+// Byte planes of the tensor-core conversion: for target m, byte plane b and k = 8 i + a, the
+// bf16 of byte b of B[m][i][a] = c[m][i] 2^(8a) mod t_m.  Then for y_i = sum_a y_ia 2^(8a),
+// sum_i y_i c[m][i] = sum_b 2^(8b) sum_(i,a) y_ia byte_b(B[m][i][a]) (mod t_m): eight exact sums
+// of 32 products of bytes, one per byte plane.  A byte is exact in bf16 (8 significant bits), so
+// its bf16 is the top half of its FP32 bits.
+std::vector<uint32_t> bconv_tc_table(const std::vector<u64>& c, const std::vector<u64>& tp, int nt) {
+    std::vector<uint32_t> out((size_t)nt * 8 * kBconvTcStride, 0);
+    auto bf16 = [](uint32_t v) {
+        const float f = (float)v;
+        uint32_t u;
+        memcpy(&u, &f, 4);
+        return u >> 16;
+    };
+    for (int m = 0; m < nt; m++) {
+        const u64 t = tp[m];
+        for (int i = 0; i < 4; i++) {
+            u64 w = c[(size_t)m * 4 + i] % t;
+            for (int a = 0; a < 8; a++) {
+                for (int b = 0; b < 8; b++) {
+                    const int k = 8 * i + a;
+                    const uint32_t v = bf16((uint32_t)((w >> (8 * b)) & 0xff));
+                    uint32_t& word = out[((size_t)m * 8 + b) * kBconvTcStride + k / 2];
+                    word |= (k & 1) ? v << 16 : v;
+                }
+                w = mulmod_host(w, 256, t);
+            }
+        }
+    }
+    return out;
+}
+}  // namespace pft
+
 static void build_tables(pft_ctx* c) {
     const int P = (int)c->primes.size(), n = c->n, logn = c->logn, L = c->L, k = c->k;
     // primes
@@ -92,6 +125,10 @@ static void build_tables(pft_ctx* c) {
     c->tabs.logn = logn;
     c->tabs.n = n;
     for (int b = 0; b < kNttBuckets; b++) c->tabs.plan[b].kind = -1;  // until the autotuner chooses
+    {
+        const char* e = getenv("PFT_BCONV");
+        c->tabs.bconv_tc = e && strcmp(e, "tc") == 0 ? 1 : 0;  // integer pipes unless asked
+    }
     c->tabs.primes = tab_upload(c, dp);
     // twiddles
     std::vector<ulonglong2> fwd((size_t)P * n), inv((size_t)P * n), ninv(P), inv1(P);
@@ -164,12 +201,14 @@ static void build_tables(pft_ctx* c) {
     // (Montgomery form, 30-bit split), targets = rows 0..l+k-1 outside the digit, in order
     c->modup_tab.assign((size_t)L * c->beta_max, nullptr);
     c->modup_tab_u.assign((size_t)L * c->beta_max, nullptr);
+    c->modup_tc.assign((size_t)L * c->beta_max, nullptr);
     for (int l = 1; l <= L; l++) {
         const int beta = (l + c->alpha - 1) / c->alpha, E = l + k;
         for (int j = 0; j < beta; j++) {
             const int lo = j * c->alpha, hi = std::min(l, lo + c->alpha), ns = hi - lo;
             const int nt = E - ns;
             std::vector<u64> tab(2 * ns + (size_t)ns * nt);
+            std::vector<u64> plain((size_t)nt * 4, 0), tprime(nt, 0);  // for the tensor-core table
             for (int i = 0; i < ns; i++) {
                 const u64 qi = c->primes[lo + i];
                 u64 h = 1;
@@ -186,10 +225,15 @@ static void build_tables(pft_ctx* c) {
                     for (int i2 = 0; i2 < ns; i2++)
                         if (i2 != i) hm = mulmod_host(hm, c->primes[lo + i2] % t, t);
                     tab[2 * ns + (size_t)mi * ns + i] = split30_host(mont_host(hm, t));
+                    if (ns == 4) {
+                        plain[(size_t)mi * 4 + i] = hm;
+                        tprime[mi] = t;
+                    }
                     mi++;
                 }
             }
             c->modup_tab[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, tab);
+            if (ns == 4) c->modup_tc[(size_t)(l - 1) * c->beta_max + j] = tab_upload(c, bconv_tc_table(plain, tprime, nt));
             for (int i = 0; i < ns; i++) {
                 const u64 qi = c->primes[lo + i];
                 tab[2 * i] = mulmod_host(tab[2 * i], invmod_host((u64)c->n % qi, qi), qi);
@@ -202,8 +246,10 @@ static void build_tables(pft_ctx* c) {
     // 30-bit split)
     c->moddown_tab.assign(L, nullptr);
     c->moddown_tab_u.assign(L, nullptr);
+    c->moddown_tc.assign(L, nullptr);
     for (int l = 1; l <= L; l++) {
         std::vector<u64> tab(2 * k + (size_t)k * l);
+        std::vector<u64> plain((size_t)l * 4, 0), tprime(l, 0);  // for the tensor-core table (k = 4)
         for (int i = 0; i < k; i++) {
             const u64 pi = c->primes[L + i];
             u64 h = 1;
@@ -218,9 +264,14 @@ static void build_tables(pft_ctx* c) {
                 for (int i2 = 0; i2 < k; i2++)
                     if (i2 != i) hm = mulmod_host(hm, c->primes[L + i2] % t, t);
                 tab[2 * k + (size_t)m * k + i] = split30_host(mont_host(hm, t));
+                if (k == 4) {
+                    plain[(size_t)m * 4 + i] = hm;
+                    tprime[m] = t;
+                }
             }
         }
         c->moddown_tab[l - 1] = tab_upload(c, tab);
+        if (k == 4) c->moddown_tc[l - 1] = tab_upload(c, bconv_tc_table(plain, tprime, l));
         for (int i = 0; i < k; i++) {
             const u64 pi = c->primes[L + i];
             tab[2 * i] = mulmod_host(tab[2 * i], invmod_host((u64)c->n % pi, pi), pi);
@@ -417,6 +468,7 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
                 J.src = dc(b) + (size_t)lo * limb;
                 J.dst = ext(b, j);
                 J.table = (unscaled ? c->modup_tab_u : c->modup_tab)[(size_t)(l - 1) * c->beta_max + j];
+                J.tc = c->modup_tc[(size_t)(l - 1) * c->beta_max + j];
                 J.ns = hi - lo;
                 J.src_p0 = lo;
                 J.nrows = E;
@@ -468,6 +520,7 @@ void keyswitch_batch(pft_ctx* c, u32 key_id, const std::vector<KsIO>& io) {
                 J.src = uu(b, pol) + (size_t)l * limb;
                 J.dst = cv(b, pol);
                 J.table = nullptr;  // chosen below, with the form of the transform
+                J.tc = c->moddown_tc[l - 1];
                 J.ns = k;
                 J.src_p0 = L;
                 J.nrows = l;
@@ -715,6 +768,7 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
             J.src = Dc.u() + (size_t)lo * limb;
             J.dst = ext(Ext.u(), j);
             J.table = (unscaled ? c->modup_tab_u : c->modup_tab)[(size_t)(l - 1) * c->beta_max + j];
+            J.tc = c->modup_tc[(size_t)(l - 1) * c->beta_max + j];
             J.ns = hi - lo;
             J.src_p0 = lo;
             J.nrows = E;
@@ -766,6 +820,7 @@ void op_rotate_hoisted(pft_ctx* c, const pft_ct* a, const int32_t* steps, int n,
             J.src = up + (size_t)l * limb;
             J.dst = Cv.u() + (size_t)pol * l * limb;
             J.table = nullptr;  // chosen with the form of the transform
+            J.tc = c->moddown_tc[l - 1];
             J.ns = k;
             J.src_p0 = L;
             J.nrows = l;

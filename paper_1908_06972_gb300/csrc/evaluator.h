@@ -34,6 +34,8 @@ struct pft_ctx {
     // the same with every source constant times N^-1 (for inputs of an inverse transform that
     // skipped its N^-1)
     std::vector<const u64*> modup_tab_u, moddown_tab_u;
+    // the byte-plane tables of the tensor-core conversion (jobs of four source primes; else null)
+    std::vector<const uint32_t*> modup_tc, moddown_tc;
     const u64* moddown_consts = nullptr;           // [L][3] {0, P^-1, shoup}
     std::vector<const u64*> rescale_consts;        // [l-1] -> [l-1][3] {0, p^-1, shoup}
     std::vector<const u64*> pmodq_consts;          // digit j -> [alpha][3] {0, P mod q_m, shoup}

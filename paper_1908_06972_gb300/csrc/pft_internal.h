@@ -66,6 +66,8 @@ struct DevTables {
     // 2^(12+k) + u 2^(4+k) + w 2^k + j of the natural table
     ulonglong2* fwd_rows;
     ulonglong2* inv_rows;
+    int bconv_tc;          // basis conversion of four source primes on the tensor cores (1, opt-in:
+                           // environment PFT_BCONV=tc at context creation) or the integer pipes (0)
     int ntt_variant;       // N = 2^16 transform: 0 two-pass (3 CTAs/SM), 1 two-pass (4 CTAs/SM),
                            // 2 one-launch cluster, 3 generic staged passes
     // Transform plan per launch size (bucket of the launch's total limbs: <= 64, <= 512,
@@ -164,9 +166,17 @@ struct BconvJob {
     const u64* src;
     u64* dst;
     const u64* table;  // [ns]{qhat_inv, shoup} then [targets][ns] qhat mod target
+    // four source primes only, or null: the byte planes of the conversion constants for the
+    // tensor-core form, [targets][8 byte planes b][kBconvTcStride u32] of bf16 pairs: entry
+    // k = 8 i + a is byte b of (qhat_i mod t_m) 2^(8a) mod t_m (b, a < 8, i < 4)
+    const uint32_t* tc;
     int ns, src_p0, nrows, skip_lo, skip_hi, split, base2, pad;
 };
+constexpr int kBconvTcStride = 20;  // u32 words per (target, byte plane) row: 16 of data + 4 of padding
 void bconv(const DevTables& t, const BconvJob* jobs_host, int n_jobs, cudaStream_t st);  // jobs: host array
+// Byte-plane table of the tensor-core conversion for one job: c[m][i] = qhat_i mod t_m (plain
+// form) for nt targets of primes tp[m] and 4 sources; returns [nt][8][kBconvTcStride] u32.
+std::vector<uint32_t> bconv_tc_table(const std::vector<u64>& c, const std::vector<u64>& tp, int nt);
 
 // Key inner product: u[b][pol][m] = sum_j ext[b][j][m] * key[j][pol][row(m)] over B inputs at
 // any levels in one launch (the key is read once for all);

@@ -429,6 +429,118 @@ __global__ void __launch_bounds__(256) k_bconv(DevTables t, BconvBatch jobs) {
     }
 }
 
+// ---- basis conversion of four source primes on the tensor cores ----------------------------
+// The sum out_m = sum_i y_i c_im mod t_m (y_i the scaled source residues, c_im < t_m) as an
+// exact bf16 matrix product: with y_i = sum_a y_ia 2^(8a) (bytes) and the byte planes
+// byte_b(c_im 2^(8a) mod t_m) of bconv_tc_table, the FP32 products
+//   P_mb = sum_(i,a) y_ia byte_b(c_im 2^(8a) mod t_m)      (32 terms below 2^16: exact below 2^21)
+// give sum_b P_mb 2^(8b) = out_m (mod t_m), a value below 2^77, reduced once (Barrett).  One
+// mma.sync.m16n8k16 covers 16 coefficients (rows) x the 8 byte planes of one target (columns)
+// x 16 of the 32 (source, byte) pairs (k): two per target.  The accumulators start at 2^23, so
+// each P arrives as the FP32 bit pattern 0x4B000000 + P (P < 2^23 keeps it exact) and becomes
+// an integer by one subtraction.  A CTA converts 1024 coefficients of one job in tiles of 128:
+// warp w 16 of each tile,
+// with the A fragments (the bytes of its coefficients' y_i) built in registers once for all
+// targets; two targets per iteration, then each lane recombines one (coefficient, target).
+// The byte planes (about 22 KiB for 34 targets) are staged once per CTA of 1024 coefficients.
+constexpr int kTcRows = 1024;  // coefficients per CTA (each warp: 8 tiles of 16)
+__device__ __forceinline__ uint32_t bf16_byte(uint32_t v) {  // bf16 bits of an integer 0..255
+    return __float_as_uint(__uint_as_float(0x4B000000u | v) - 8388608.0f) >> 16;
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) k_bconv_tc(DevTables t, BconvBatch jobs) {
+    extern __shared__ __align__(16) uint32_t tsm[];
+    const BconvJob J = jobs.j[blockIdx.y];
+    const int gap = J.skip_hi - J.skip_lo;
+    const int nt = J.nrows - gap;
+    uint32_t* Bs = tsm;                                         // [nt][8][kBconvTcStride]
+    uint32_t* Cs = tsm + (size_t)nt * 8 * kBconvTcStride;       // [8 warps][2][16][8]
+    u64* sP = reinterpret_cast<u64*>(Cs + 8 * 2 * 16 * 8);      // [nt][3]: q, mu, (output row << 8) | s
+    for (int i = threadIdx.x; i < nt * 8 * kBconvTcStride; i += blockDim.x) Bs[i] = __ldg(&J.tc[i]);
+    for (int m = threadIdx.x; m < nt; m += blockDim.x) {
+        const int mrow = m < J.skip_lo ? m : m + gap;
+        const int tp = mrow < J.split ? mrow : J.base2 + mrow - J.split;
+        sP[3 * m] = __ldg(&t.primes[tp].q);
+        sP[3 * m + 1] = __ldg(&t.primes[tp].mu);
+        sP[3 * m + 2] = ((u64)mrow << 8) | __ldg(&t.primes[tp].s);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    const int logn = t.logn;
+    __syncthreads();  // the byte planes are in shared memory
+    uint32_t* cw = Cs + (size_t)w * 2 * 16 * 8;
+    const int my_t = lane >> 4, my_r = lane & 15;  // the (target, row) this lane recombines
+    const u64 K1 = 0x4B000000ull * 0x01010101ull;  // the accumulators' offset in four byte planes
+    for (int rt = 0; rt < kTcRows / 128; rt++) {
+        const size_t row0 = (size_t)blockIdx.x * kTcRows + (size_t)(rt * 8 + w) * 16;  // this tile's first coefficient
+        // A fragments: rows g and g + 8, k = 16 s + {2c, 2c+1} (source 2s) and + 8 (source 2s+1)
+        uint32_t A[2][4];
+        {
+            u64 y[2][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const u64 q = __ldg(&t.primes[J.src_p0 + i].q);
+                const u64 wv = __ldg(&J.table[2 * i]), wp = __ldg(&J.table[2 * i + 1]);
+                const u64* src = J.src + ((size_t)i << logn) + row0;
+                y[0][i] = mul_shoup(src[g], wv, wp, q);
+                y[1][i] = mul_shoup(src[g + 8], wv, wp, q);
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < 2; s2++)
+#pragma unroll
+                for (int h = 0; h < 2; h++) {      // h = 0: source 2 s2 (k 0..7), 1: source 2 s2 + 1 (k 8..15)
+#pragma unroll
+                    for (int r = 0; r < 2; r++) {  // row g, g + 8
+                        const u64 v = y[r][2 * s2 + h];
+                        const uint32_t lo = bf16_byte((uint32_t)(v >> (16 * c)) & 0xff);
+                        const uint32_t hi = bf16_byte((uint32_t)(v >> (16 * c + 8)) & 0xff);
+                        A[s2][2 * h + r] = lo | (hi << 16);
+                    }
+                }
+        }
+        for (int m0 = 0; m0 < nt; m0 += 2) {
+#pragma unroll
+            for (int tt = 0; tt < 2; tt++) {
+                const int m = m0 + tt < nt ? m0 + tt : m0;  // an odd last target repeats one (not stored)
+                float d[4] = {8388608.0f, 8388608.0f, 8388608.0f, 8388608.0f};
+                const uint32_t* brow = Bs + ((size_t)m * 8 + g) * kBconvTcStride;
+#pragma unroll
+                for (int s2 = 0; s2 < 2; s2++) mma_bf16(d, A[s2], brow[8 * s2 + c], brow[8 * s2 + 4 + c]);
+                uint32_t* o = cw + tt * 16 * 8;
+                *reinterpret_cast<uint2*>(o + g * 8 + 2 * c) = make_uint2(__float_as_uint(d[0]), __float_as_uint(d[1]));
+                *reinterpret_cast<uint2*>(o + (g + 8) * 8 + 2 * c) =
+                    make_uint2(__float_as_uint(d[2]), __float_as_uint(d[3]));
+            }
+            __syncwarp();
+            const int m = m0 + my_t;
+            if (m < nt) {
+                const uint4 p0 = *reinterpret_cast<const uint4*>(cw + (my_t * 16 + my_r) * 8);
+                const uint4 p1 = *reinterpret_cast<const uint4*>(cw + (my_t * 16 + my_r) * 8 + 4);
+                // sum_b P_b 2^(8b) = lo4 + hi4 2^32, lo4/hi4 = sum of four planes (< 2^45 each)
+                const u64 lo4 = (u64)p0.x + ((u64)p0.y << 8) + ((u64)p0.z << 16) + ((u64)p0.w << 24) - K1;
+                const u64 hi4 = (u64)p1.x + ((u64)p1.y << 8) + ((u64)p1.z << 16) + ((u64)p1.w << 24) - K1;
+                const u64 vlo = lo4 + (hi4 << 32);
+                const u64 vhi = (hi4 >> 32) + (vlo < lo4 ? 1 : 0);
+                DPrime P;
+                P.q = sP[3 * m];
+                P.mu = sP[3 * m + 1];
+                const u64 rs = sP[3 * m + 2];
+                P.s = (u32)(rs & 0xff);
+                const size_t mrow = (size_t)(rs >> 8);
+                J.dst[(mrow << logn) + row0 + my_r] = barrett_reduce(vhi, vlo, P);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st) {
     // one launch per source-prime count (the last ModUp digit can be shorter)
     for (int ns = 1; ns <= kMaxAlpha; ns++) {
@@ -446,6 +558,20 @@ void bconv(const DevTables& t, const BconvJob* jobs, int n_jobs, cudaStream_t st
             for (int i = 0; i < cnt; i++) {
                 b.j[i] = sel[a + i];
                 ntmax = max(ntmax, b.j[i].nrows - (b.j[i].skip_hi - b.j[i].skip_lo));
+            }
+            bool tc = ns == 4 && t.bconv_tc && t.n % kTcRows == 0;
+            for (int i = 0; i < cnt && tc; i++) tc = b.j[i].tc != nullptr;
+            if (tc) {
+                const size_t smem_tc =
+                    ((size_t)ntmax * 8 * kBconvTcStride + 8 * 2 * 16 * 8) * sizeof(uint32_t) + (size_t)ntmax * 24;
+                if (first_on_device((const void*)k_bconv_tc))
+                    PFT_CUDA(cudaFuncSetAttribute(k_bconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)((size_t)(kMaxPrimes * 8 * kBconvTcStride + 8 * 2 * 16 * 8) *
+                                                            sizeof(uint32_t) + (size_t)kMaxPrimes * 24)));
+                PFT_PROF("bconv", st, 0.0);
+                k_bconv_tc<<<dim3((unsigned)(t.n / kTcRows), (unsigned)cnt), 256, smem_tc, st>>>(t, b);
+                PFT_LAUNCH_CHECK("bconv (tensor cores)");
+                continue;
             }
             const size_t smem = (size_t)ntmax * ns * 8 + (size_t)ntmax * 20;
             dim3 grid((unsigned)((t.n / 2 + 255) / 256), (unsigned)cnt);

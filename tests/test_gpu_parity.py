@@ -443,6 +443,31 @@ def test_fasttext_diagonal_chunks_bit_exact_n12(p1):
         pf.pft_ft_model_destroy(model)
 
 
+def test_tensor_core_basis_conversion_bit_exact(gpu, monkeypatch):
+    """The tensor-core form of the basis conversion (four source primes: ModUp digits of 4 and
+    ModDown from 4 special primes; opt-in) gives the same bits: HMUL + relinearisation, rotation
+    and a batch at mixed levels against the oracle at N = 2^16."""
+    monkeypatch.setenv("PFT_BCONV", "tc")
+    p = Pair(gpu, 16, 8, 4, 4, mid_bits=50, rot_steps=[1])
+    monkeypatch.delenv("PFT_BCONV")
+    try:
+        o, pf, ctx = p.orc, p.pft, p.ctx
+        lv = [8, 6, 5]
+        A = [o.encrypt_sk(o.encode(synth.slots(70 + i, 256), level=l), 170 + i) for i, l in enumerate(lv)]
+        B = [o.encrypt_pk(o.encode(synth.slots(80 + i, 256), level=l), 180 + i) for i, l in enumerate(lv)]
+        gA, gB = [p.ct(x) for x in A], [p.ct(x) for x in B]
+        C = [p.empty() for _ in lv]
+        pf.pft_mul_relin_batch(ctx, gA, gB, C)
+        M = [o.mul_relin(a, b) for a, b in zip(A, B)]
+        for i in range(len(lv)):
+            p.assert_equal(C[i], M[i], "tensor-core conversion: mul_relin level %d" % lv[i])
+        pf.pft_rotate_batch(ctx, C, 1, C)
+        for i in range(len(lv)):
+            p.assert_equal(C[i], o.rotate(M[i], 1), "tensor-core conversion: rotate level %d" % lv[i])
+    finally:
+        p.close()
+
+
 # ---- seeded compressed switching keys -----------------------------------------------------------
 @pytest.mark.parametrize("logn,L,k,alpha,mid", [(12, 3, 1, 1, 40), (12, 10, 1, 1, 40), (16, 6, 2, 4, 50)])
 def test_compressed_keys_bit_exact(gpu, logn, L, k, alpha, mid):
