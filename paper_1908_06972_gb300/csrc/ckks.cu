@@ -354,6 +354,30 @@ static u64* make_switch_key(pft_ctx* c, const u64* sp, u32 key_id) {
     return K;
 }
 
+// An uncompressed key's copy for the key inner product: every word k as (k 2^64 mod p) split
+// into 30-bit halves (the same 8 bytes; the inner product then sums 30-bit products without
+// carries and reduces once in Montgomery form).
+static void add_key(pft_ctx* c, u32 key_id, u64* K) {
+    c->keys[key_id] = K;
+    if (c->compressed_keys) return;
+    const int R = c->L + c->k;
+    const size_t words = (size_t)c->beta_max * 2 * R * c->n;
+    u64* M = (u64*)dalloc(c, words * 8);
+    std::vector<PolyRef> in, out;
+    for (int i = 0; i < 2 * c->beta_max; i++) {
+        in.push_back(ref(K + (size_t)i * R * c->n, R, 0, c->L, c->L));
+        out.push_back(ref(M + (size_t)i * R * c->n, R, 0, c->L, c->L));
+    }
+    chunks(in.size(), [&](size_t a, size_t b) { mont_split(c->tabs, mkset(in, a, b), mkset(out, a, b), c->stream); });
+    c->keys_mont[key_id] = M;
+}
+static void free_keys(pft_ctx* c) {
+    for (auto& kv : c->keys) dfree(c, kv.second);
+    for (auto& kv : c->keys_mont) dfree(c, kv.second);
+    c->keys.clear();
+    c->keys_mont.clear();
+}
+
 static void add_rot_keys(pft_ctx* c, const int32_t* steps, int n_steps) {
     NEED(c->have_sk, PFT_ERR_NO_KEY, "keygen has not run");
     const int n = c->n, R = c->L + c->k;
@@ -363,7 +387,7 @@ static void add_rot_keys(pft_ctx* c, const int32_t* steps, int n_steps) {
         Scratch sg(c, (size_t)R * n * 8);
         std::vector<PolyRef> in{ref(c->s_ntt, R, 0, c->L, c->L)}, out{ref(sg.u(), R, 0, c->L, c->L)};
         chunks(1, [&](size_t a, size_t b) { automorph(c->tabs, mkset(in, a, b), mkset(out, a, b), g, c->stream); });
-        c->keys[g] = make_switch_key(c, sg.u(), g);
+        add_key(c, g, make_switch_key(c, sg.u(), g));
     }
 }
 
@@ -376,6 +400,8 @@ KeyRef keyref(pft_ctx* c, u32 key_id) {
     NEED(c->keys.count(key_id), PFT_ERR_NO_KEY, "no such key");
     KeyRef r;
     r.ptr = c->keys[key_id];
+    auto m = c->keys_mont.find(key_id);
+    r.mont = m == c->keys_mont.end() ? nullptr : m->second;
     r.id = key_id;
     r.compressed = c->compressed_keys ? 1 : 0;
     for (int i = 0; i < 4; i++) {
@@ -1518,7 +1544,7 @@ int pft_ctx_create(const pft_params* prm, const pft_allocator* alloc, pft_ctx** 
 int pft_ctx_destroy(pft_ctx* c) {
     if (!c) return PFT_OK;
     cudaStreamSynchronize(c->stream);
-    for (auto& kv : c->keys) dfree(c, kv.second);
+    free_keys(c);
     dfree(c, c->s_ntt);
     dfree(c, c->pk);
     cudaStreamSynchronize(c->stream);
@@ -1576,13 +1602,12 @@ int pft_keygen(pft_ctx* c, const int32_t* rot_steps, int n_steps, int want_relin
             ew(c, EwOp::Sub, rb, ras, rb);
         }
         c->have_sk = true;
-        for (auto& kv : c->keys) dfree(c, kv.second);
-        c->keys.clear();
+        free_keys(c);
         if (want_relin) {
             Scratch s2(c, (size_t)R * limb * 8);
             std::vector<PolyRef> rs{ref(c->s_ntt, R, 0, L, L)}, r2{ref(s2.u(), R, 0, L, L)};
             ew(c, EwOp::Mul, rs, rs, r2);
-            c->keys[0] = make_switch_key(c, s2.u(), 0);
+            add_key(c, 0, make_switch_key(c, s2.u(), 0));
         }
         if (n_steps > 0) {
             NEED(rot_steps, PFT_ERR_ARG, "null rotation steps");

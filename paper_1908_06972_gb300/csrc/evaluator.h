@@ -47,6 +47,7 @@ struct pft_ctx {
     std::vector<i64> s_coeff;
     u64* pk = nullptr;  // [2][L][N]  (b, a)
     std::map<u32, u64*> keys;  // [beta][2][L+k][N], or [beta][L+k][N] (b only) when compressed
+    std::map<u32, u64*> keys_mont;  // uncompressed keys in split Montgomery form (KeyRef::mont)
     bool compressed_keys = false;
 };
 

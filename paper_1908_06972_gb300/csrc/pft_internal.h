@@ -197,6 +197,9 @@ constexpr int kMaxKs = 128;  // inputs per launch (by-value parameters)
 constexpr u32 kDomKskAEval = 11;
 struct KeyRef {
     const u64* ptr;
+    // uncompressed keys: the same words in Montgomery form split into 30-bit halves,
+    // (k 2^64 mod p) = k1 2^30 + k0 stored as k0 | k1 << 32 (the key inner product's operand)
+    const u64* mont;
     u32 id;
     int compressed;
     u32 seedw[8];
@@ -238,6 +241,8 @@ void sample_small(const DevTables& t, const u64 seed[4], u32 dom, u32 obj, u32 s
 void reduce_signed(const DevTables& t, const i64* x_dev, const PolySet& out, cudaStream_t st);
 // out = in mod q per limb, for words of any 64-bit value (e.g. exact integer sums of residues)
 void reduce_words(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
+// out = (in 2^64 mod q) split into 30-bit halves, k0 | k1 << 32 (canonical residues in)
+void mont_split(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st);
 
 // ---- host math (encode.cpp) -----------------------------------------------------------
 std::vector<u64> gen_primes(int logn, int bits, int count, const std::vector<u64>& exclude);

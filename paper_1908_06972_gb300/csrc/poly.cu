@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, 
     const int xl = 2 * threadIdx.x;
     const size_t xo = chunk0 + xl;
     const DPrime P = load_prime(t.primes, row);
-    const u64* key = kr.ptr;
+    const u64* key = kr.mont;  // split Montgomery form: k0 | k1 << 32 with k 2^64 mod p = k1 2^30 + k0
     ulonglong2 kb[BMAX], ka[BMAX];
 #pragma unroll
     for (int j = 0; j < BMAX; j++) {
@@ -858,22 +858,34 @@ __global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, 
         const int l = D.l, E = l + k, beta = (l + alpha - 1) / alpha;
         const int m = row < L ? row : l + row - L;
         const u64* st = ring + (size_t)s * stage_digits * kKsChunk + xl;
-        U128 s0x = {0, 0}, s0y = {0, 0}, s1x = {0, 0}, s1y = {0, 0};
+        // sums of at most 8 products of residues below 2^60 in 30-bit-split partial sums (four
+        // widening multiply-adds per product), then one Montgomery reduction: the key words carry
+        // the factor 2^64 (sum < 8 p^2 < p 2^63)
+        Acc3 s0x = {0, 0, 0}, s0y = {0, 0, 0}, s1x = {0, 0, 0}, s1y = {0, 0, 0};
 #pragma unroll
         for (int j = 0; j < BMAX; j++) {
-            if (j < beta) {  // beta <= 8: 128-bit sums of at most 8 products
+            if (j < beta) {
                 const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(st + (size_t)j * kKsChunk);
-                mac_wide(s0x, v.x, kb[j].x);
-                mac_wide(s0y, v.y, kb[j].y);
-                mac_wide(s1x, v.x, ka[j].x);
-                mac_wide(s1y, v.y, ka[j].y);
+                u32 x0, x1, y0, y1;
+                split30(v.x, x0, x1);
+                split30(v.y, y0, y1);
+                acc3_mac(s0x, x0, x1, (u32)kb[j].x, (u32)(kb[j].x >> 32));
+                acc3_mac(s0y, y0, y1, (u32)kb[j].y, (u32)(kb[j].y >> 32));
+                acc3_mac(s1x, x0, x1, (u32)ka[j].x, (u32)(ka[j].x >> 32));
+                acc3_mac(s1y, y0, y1, (u32)ka[j].y, (u32)(ka[j].y >> 32));
             }
         }
         ulonglong2 r0, r1;
-        r0.x = barrett_reduce(s0x.hi, s0x.lo, P);
-        r0.y = barrett_reduce(s0y.hi, s0y.lo, P);
-        r1.x = barrett_reduce(s1x.hi, s1x.lo, P);
-        r1.y = barrett_reduce(s1y.hi, s1y.lo, P);
+        {
+            U128 a = acc3_value(s0x);
+            r0.x = mont_reduce(a.hi, a.lo, P.q, P.mneg);
+            a = acc3_value(s0y);
+            r0.y = mont_reduce(a.hi, a.lo, P.q, P.mneg);
+            a = acc3_value(s1x);
+            r1.x = mont_reduce(a.hi, a.lo, P.q, P.mneg);
+            a = acc3_value(s1y);
+            r1.y = mont_reduce(a.hi, a.lo, P.q, P.mneg);
+        }
         *reinterpret_cast<ulonglong2*>(D.u + ((size_t)m << logn) + xo) = r0;
         *reinterpret_cast<ulonglong2*>(D.u + (((size_t)E + m) << logn) + xo) = r1;
         __syncthreads();  // every thread has read stage s
@@ -1083,7 +1095,7 @@ void ks_inner_multi(const DevTables& t, const KsDesc* descs, int B, const KeyRef
         dim3 grid2((unsigned)((t.n / 2 + 127) / 128), (unsigned)(L + k));
         dim3 grid1((unsigned)((t.n + 127) / 128), (unsigned)(L + k));
         PFT_PROF("ks_inner", st, bytes);
-        if (beta_max <= 8 && !key.compressed && t.n % kKsChunk == 0) {
+        if (beta_max <= 8 && !key.compressed && key.mont && t.n % kKsChunk == 0) {
             const int sd = beta_max <= 4 ? 4 : 8;
             dim3 gb((unsigned)(t.n / kKsChunk), (unsigned)(L + k));
             const size_t smem = (size_t)kKsStages * sd * kKsChunk * 8;
@@ -1225,6 +1237,26 @@ __global__ void k_reduce_words(DevTables t, PolySet in, PolySet out) {
     const DPrime P = load_prime(t.primes, prime_of(Ro, limb));
     const size_t o = ((size_t)limb << t.logn) + c;
     Ro.ptr[o] = reduce64(in.p[poly].ptr[o], P);
+}
+
+__global__ void k_mont_split(DevTables t, PolySet in, PolySet out) {
+    const int poly = blockIdx.z, limb = blockIdx.y;
+    const PolyRef& Ro = out.p[poly];
+    if (limb >= Ro.nlimbs) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= t.n) return;
+    const DPrime P = load_prime(t.primes, prime_of(Ro, limb));
+    const size_t o = ((size_t)limb << t.logn) + c;
+    const u64 m = mulmod(in.p[poly].ptr[o], P.r64, P);  // k 2^64 mod p
+    Ro.ptr[o] = (m & 0x3fffffffull) | ((m >> 30) << 32);
+}
+
+void mont_split(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
+    if (out.count == 0) return;
+    dim3 grid((unsigned)((t.n + 255) / 256), (unsigned)out.max_limbs, (unsigned)out.count);
+    PFT_PROF("mont_split", st, 0.0);
+    k_mont_split<<<grid, 256, 0, st>>>(t, in, out);
+    PFT_LAUNCH_CHECK("mont_split");
 }
 
 void reduce_words(const DevTables& t, const PolySet& in, const PolySet& out, cudaStream_t st) {
