@@ -11,8 +11,8 @@ Output: one JSON line (rank 0).  `value` is HE mult+relin per second of the batc
 path with inputs resident in HBM (each counted mult+relin carries its 16 rotations);
 `e2e` measures the same through the C ABI from page-locked host buffers: every step's
 128 input ciphertexts are copied in (pft_ct_import_batch) and its 64 results copied out
-(pft_ct_export_batch_async) inside the timed region, on a copy stream that overlaps the
-previous and next steps' compute.  Further legs: the step as one CUDA-graph launch, the
+(pft_ct_export_batch_async) inside the timed region, on an import and an export stream that
+overlap the previous and next steps' compute (split.link_gbs: the host link's copy rates).  Further legs: the step as one CUDA-graph launch, the
 plain path, encrypted fastText inference, the encrypted training step and the request
 server.  `--impl reference` times the CPU oracle on a bounded sample of the same workload.
 """
@@ -231,32 +231,36 @@ def run_gpu(args):
     h2d = sum(a.nbytes for a, _ in host_in)
     d2h = sum(o.nbytes for o in host_out)
 
-    # Pipelined through the public API on a copy stream: step i+1's inputs are copied into one of
-    # two fixed sets of input handles (pft_ct_import_batch_into) and step i's results out of one
-    # of two sets of outputs into page-locked buffers (pft_ct_export_batch_async) while the
-    # compute stream runs; the streams order themselves with events (an import waits behind the
-    # export of the step that last read its set, a step waits for the export that last read its
-    # outputs), so the host never blocks before the end; every step's results are in host memory
-    # before the timed region ends.
+    # Pipelined through the public API on two copy streams: step i+1's inputs are copied into one
+    # of two fixed sets of input handles (pft_ct_import_batch_into, on the import stream) and step
+    # i's results out of one of two sets of outputs into page-locked buffers
+    # (pft_ct_export_batch_async, on the export stream) while the compute stream runs, so the two
+    # directions use their own copy engines at the same time.  Events order the streams: an import
+    # waits for the end of the step that last read its set, an export for the end of its step, a
+    # step for its import and for the export that last read its outputs; the host never blocks
+    # before the end, and every step's results are in host memory before the timed region ends.
     S = torch.cuda.current_stream()
-    Cs = torch.cuda.Stream()
+    Ci, Ce = torch.cuda.Stream(), torch.cuda.Stream()
     C2 = [C, [pft.pft_ct_create(ctx) for _ in range(BATCH)]]
     IN2 = [[pft.pft_ct_create(ctx) for _ in range(2 * BATCH)] for _ in range(2)]
     outs2 = [host_out, [torch.empty(o.shape, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
                         for o in host_out]]
     marks = []
+    step_end = {}  # step -> event at the end of its compute
 
-    def on_copy_stream(fn):
-        pft.pft_set_stream(ctx, Cs.cuda_stream)
+    def on_stream(strm, fn):
+        pft.pft_set_stream(ctx, strm.cuda_stream)
         fn()
         ev = torch.cuda.Event(enable_timing=True)
-        ev.record(Cs)
+        ev.record(strm)
         pft.pft_set_stream(ctx, S.cuda_stream)
         return ev
 
     def import_into(k):
-        return on_copy_stream(lambda: pft.pft_ct_import_batch_into(ctx, [arr for arr, _ in host_in],
-                                                                   [sc for _, sc in host_in], IN2[k % 2]))
+        if k - 2 in step_end:  # step k - 2 read this set of input handles
+            Ci.wait_event(step_end.pop(k - 2))
+        return on_stream(Ci, lambda: pft.pft_ct_import_batch_into(ctx, [arr for arr, _ in host_in],
+                                                                  [sc for _, sc in host_in], IN2[k % 2]))
 
     host = {"import": 0.0, "compute": 0.0, "export": 0.0, "wait": 0.0}
     exported = {}
@@ -273,9 +277,10 @@ def run_gpu(args):
         ins = IN2[k % 2]
         step_batched(ins[0::2], ins[1::2], C2[k % 2])
         ev[1].record(S)
+        step_end[k] = ev[1]
         h2 = time.perf_counter()
-        Cs.wait_event(ev[1])
-        exported[k] = on_copy_stream(lambda: pft.pft_ct_export_batch_async(ctx, C2[k % 2], outs2[k % 2]))
+        Ce.wait_event(ev[1])
+        exported[k] = on_stream(Ce, lambda: pft.pft_ct_export_batch_async(ctx, C2[k % 2], outs2[k % 2]))
         h3 = time.perf_counter()
         for key, dt in (("import", h1 - h0), ("compute", h2 - h1), ("export", h3 - h2)):
             host[key] += dt
@@ -284,9 +289,11 @@ def run_gpu(args):
 
     def drain():
         h = time.perf_counter()
-        Cs.synchronize()
+        Ci.synchronize()
+        Ce.synchronize()
         S.synchronize()
         exported.clear()
+        step_end.clear()
         host["wait"] += time.perf_counter() - h
 
     # warm-up over both sets, so that no buffer is allocated inside the timed region
@@ -306,7 +313,8 @@ def run_gpu(args):
     e2e = throughput(BATCH * args.steps, world, e2e_s)
     e2e_split = {"compute_ms": round(sum(ev[0].elapsed_time(ev[1]) for ev in marks) / len(marks), 2),
                  "wall_ms": round(1e3 * e2e_s / args.steps, 2),
-                 "host_ms": {key: round(1e3 * v / args.steps, 2) for key, v in host.items()}}
+                 "host_ms": {key: round(1e3 * v / args.steps, 2) for key, v in host.items()},
+                 "link_gbs": link_rates(host_in[0][0], host_out[0])}
     for h in C2[1] + IN2[0] + IN2[1]:
         pft.pft_ct_destroy(h)
 
@@ -1165,7 +1173,33 @@ def train_measure(pft, torch, n_docs, plain_docs, with_diag=True):
             "max_abs_err_grad_vs_fp64": err, "model_levels_after": [lvH, lvO], "eta": TR_ETA}
 
 
+def link_rates(host_in, host_out, reps=5):
+    """Host <-> device copy rates (GB/s, best of `reps`) of one page-locked input and one output
+    buffer of the end-to-end leg, timed with CUDA events on a stream of their own: the bound the
+    end-to-end figure meets when its copies take longer than a step's compute."""
+    import torch
+
+    st = torch.cuda.Stream()
+    dev = torch.empty(max(host_in.nbytes, host_out.nbytes) // 8, dtype=torch.int64, device="cuda")
+    src = torch.from_numpy(host_in.view(np.int64)).view(-1)
+    dst = torch.from_numpy(host_out.view(np.int64)).view(-1)
+    best = {"h2d": 0.0, "d2h": 0.0}
+    with torch.cuda.stream(st):
+        for _ in range(reps):
+            for key, fn, nbytes in (("h2d", lambda: dev[:src.numel()].copy_(src, non_blocking=True), host_in.nbytes),
+                                    ("d2h", lambda: dst.copy_(dev[:dst.numel()], non_blocking=True), host_out.nbytes)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                e1.synchronize()
+                best[key] = max(best[key], nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del dev
+    return {key: round(v, 1) for key, v in best.items()}
+
+
 # ---- isolated kernel case (for ncu captures and burst rooflines) --------------------------------
+
 def run_case_ntt(args):
     """Forward + inverse transform of 16 polynomials x 30 limbs at N = 2^16 (252 MB > L2)."""
     import torch

@@ -376,6 +376,13 @@ int pft_set_transform_plan(pft_ctx* ctx, int plan);
 /* Pin the N = 2^16 transform variant (0..PFT_NTT16_VARIANTS-1: two-pass 3 CTAs/SM, two-pass 4
  * CTAs/SM, cluster, generic 8 + 8) for every launch size, without timing. */
 int pft_set_transform_variant(pft_ctx* ctx, int variant);
+/* Environment switches (measured defaults otherwise), all kernel choices with identical results:
+ *   PFT_NTT_ORDER  read at pft_ctx_create; bit 0: the second pass of an N = 2^16 two-pass
+ *                  transform visits (polynomial, limb) in reverse, so it starts on the data the
+ *                  first pass wrote last (still in L2); bit 1: the row twiddles are read with an
+ *                  L2 evict-last policy.  Default 3.
+ *   PFT_BCONV=tc   read at pft_ctx_create: basis conversion of four-prime digits on the tensor
+ *                  cores (exact byte-plane products; measured slower than the default). */
 
 /* ---- CUDA graphs of batched operations ------------------------------------
  * pft_graph_begin starts capturing the work the following calls queue on the context

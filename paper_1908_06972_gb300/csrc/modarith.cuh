@@ -66,9 +66,11 @@ __device__ __forceinline__ void acc3_mac(Acc3& A, u32 a0, u32 a1, u32 b0, u32 b1
     A.s01 = mad_wide(a1, b0, A.s01);
     A.s11 = mad_wide(a1, b1, A.s11);
 }
-// Karatsuba form for at most 4 terms: S00 = sum a0 b0, S11 = sum a1 b1 and
-// SM = sum (a0 + a1)(b0 + b1) (each factor below 2^31, so 4 terms stay below 2^64);
-// the middle sum is SM - S00 - S11.  Three products per term instead of four.
+// Karatsuba form: S00 = sum a0 b0, S11 = sum a1 b1 and SM = sum (a0 + a1)(b0 + b1) (each
+// factor below 2^31); the middle sum is SM - S00 - S11.  Three products per term instead of
+// four.  SM is kept modulo 2^64: up to 4 terms it does not wrap; up to 8 terms it may, but the
+// middle sum itself is below 2^64 (8 terms of a0 b1 + a1 b0 < 2^61), so SM - S00 - S11 taken
+// modulo 2^64 is still exactly the middle sum.
 struct Acc3K {
     u64 s00, sm, s11;
 };

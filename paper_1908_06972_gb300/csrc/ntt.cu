@@ -109,6 +109,31 @@ __device__ __forceinline__ u64 canon8(u64 v, u64 q, u64 q2) {
     return canon4(v, q, q2);
 }
 
+// L2 policy of the row twiddles: evict-last keeps the per-row tables (1 MiB per prime) in L2
+// while the streamed limbs pass through it; evict-normal is the default behaviour.
+__device__ __forceinline__ u64 tw_policy(bool keep) {
+    u64 pol;
+    if (keep) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// read-only 16-byte load under an L2 policy (the tables do not change during a launch)
+__device__ __forceinline__ ulonglong2 ldg_pol(const ulonglong2* p, u64 pol) {
+    ulonglong2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;" : "=l"(v.x), "=l"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+// Pass flags of the two-pass kernels: bit 0 canonical output (the last pass of a transform),
+// bit 1 reverse order: the CTAs visit (polynomial, limb) from the last to the first, so that a
+// pass that follows another over the same data starts on what that pass wrote last.
+constexpr int kPassFinal = 1, kPassReverse = 2;
+__device__ __forceinline__ int pass_poly(int flags) {
+    return (flags & kPassReverse) ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+}
+__device__ __forceinline__ int pass_limb(int flags) {
+    return (flags & kPassReverse) ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+}
+
 // ---- N = 2^16 in one launch: an 8-CTA cluster per limb ------------------------------------
 // The limb is viewed as a 256 x 256 array, element j = row * 256 + col.  Forward stages
 // 0..7 pair elements along a column (row bit 7 - s), stages 8..15 along a row (col bit
@@ -124,14 +149,14 @@ __device__ __forceinline__ u64 canon8(u64 v, u64 q, u64 q2) {
 // stages (s = 15 - p, r = the row being transformed).
 // LM (the row round W0 = 0 of stages 12..15, thread = row r, lane w): the twiddles come from
 // the lane-major copy of that round's twiddles, lm = its entries for (prime, row r, lane w):
-// slot (2^k - 1 + j) of stage 12 + k at lm[16 (2^k - 1 + j)].
+// slot (2^k - 1 + j) of stage 12 + k at lm[16 (2^k - 1 + j)], loaded under the L2 policy pol.
 // RT (the row round W0 = 4 of stages 8..11, thread = row r): the row's 15 twiddles of those
 // stages were copied to shared memory, stage 8 + k entry j at rt[2^k - 1 + j].
 template <bool INV, int W0, int DIMHI, bool LAZY = false, bool UNSCALED = false, bool LM = false, bool RT = false>
 __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, const ulonglong2* __restrict__ tw,
                                             u64 q, u64 q2, ulonglong2 NI, ulonglong2 NI1,
                                             const ulonglong2* __restrict__ lm = nullptr,
-                                            const ulonglong2* rt = nullptr) {
+                                            const ulonglong2* rt = nullptr, u64 pol = 0) {
     static_assert(!LM || (W0 == 0 && DIMHI == 8), "lane-major twiddles serve the row round of stages 12..15");
     static_assert(!RT || (W0 == 4 && DIMHI == 8), "staged row twiddles serve the row round of stages 8..11");
 #pragma unroll
@@ -144,7 +169,7 @@ __device__ __forceinline__ void ntt16_round(u64 (&x)[16], int wpart, int r, cons
             if (e & (1 << lb)) continue;
             const int elem = (e << W0) | wpart;
             const int idx = (1 << s) + (r << (7 - p)) + (elem >> (p + 1));
-            const ulonglong2 W = LM   ? __ldg(&lm[16 * ((1 << (s - 12)) - 1 + (e >> (p + 1)))])
+            const ulonglong2 W = LM   ? ldg_pol(&lm[16 * ((1 << (s - 12)) - 1 + (e >> (p + 1)))], pol)
                                  : RT ? rt[(1 << (s - 8)) - 1 + (elem >> (p + 1))]
                                       : __ldg(&tw[idx]);
             if (!INV) {
@@ -282,9 +307,9 @@ constexpr u64 kLazyBound = 1ull << 57;  // forward butterflies skip the correcti
 // UNSCALED (inverse): the last stage is a plain Gentleman-Sande butterfly (no N^-1) and the
 // output stays in [0, 4q): N times the inverse transform, for a consumer that scales anyway.
 template <bool INV, int LOGT, int MINB, bool UNSCALED = false>
-__global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet in, PolySet out, int is_final) {
+__global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet in, PolySet out, int flags) {
     __shared__ u64 sm[256 * 17];
-    const int poly = blockIdx.z, limb = blockIdx.y;
+    const int poly = pass_poly(flags), limb = pass_limb(flags);
     const PolyRef& Ro = out.p[poly];
     if (limb >= Ro.nlimbs) return;
     const int logn = t.logn;
@@ -326,7 +351,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_strided(DevTables t, PolySet
         ntt16_round<true, 4, 0, false, UNSCALED>(x, w, 0, tw, q, q2, NI, NI1);
 #pragma unroll
         for (int e = 0; e < 16; e++)
-            dst[(size_t)((e << 4) | w) << LOGT] = is_final && !UNSCALED ? canon4(x[e], q, q2) : x[e];
+            dst[(size_t)((e << 4) | w) << LOGT] = (flags & kPassFinal) && !UNSCALED ? canon4(x[e], q, q2) : x[e];
     }
 }
 
@@ -352,13 +377,13 @@ constexpr int kRowTwSlots = 15;
 // The 16 rows' twiddles of stages 8..11 (row u: entry 2^(8+k) + u 2^k + j, k < 4, j < 2^k) into
 // rt[16][15]: one 16-byte load and store for 240 of the 256 threads, made visible by the caller's
 // next barrier.
-__device__ __forceinline__ void stage_row_round1(const ulonglong2* __restrict__ tw, int u0, ulonglong2* rt) {
+__device__ __forceinline__ void stage_row_round1(const ulonglong2* __restrict__ tw, int u0, ulonglong2* rt, u64 pol) {
     const int t = threadIdx.x;
     if (t < 16 * 15) {
         const int cc = t / 15, e = t % 15;
         const int k = e >= 7 ? 3 : e >= 3 ? 2 : e >= 1 ? 1 : 0;
         const int j = e + 1 - (1 << k);
-        rt[t] = __ldg(&tw[(1 << (8 + k)) + ((u0 + cc) << k) + j]);
+        rt[t] = ldg_pol(&tw[(1 << (8 + k)) + ((u0 + cc) << k) + j], pol);
     }
 }
 __device__ __forceinline__ const ulonglong2* lm_base(const ulonglong2* rows, int pi, int u, int w) {
@@ -378,11 +403,12 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
     const ulonglong2* tw = t.fwd + ((size_t)pi << logn);
     const ulonglong2 NI = make_ulonglong2(0, 0);
     const ulonglong2* lm = LM ? lm_base(t.fwd_rows, pi, u, w) : nullptr;
+    const u64 pol = tw_policy(t.ntt_order & 2);
     __shared__ ulonglong2 rt[16 * 15];  // LM: twiddles of stages 8..11 of the 16 rows
     u64* my = sm + cc * kRowStride;
     u64 x[16];
     const bool lazy = q < kLazyBound;  // uniform over the CTA (one limb)
-    if (LM) stage_row_round1(tw, blockIdx.x * 16, rt);
+    if (LM) stage_row_round1(tw, blockIdx.x * 16, rt, pol);
 #pragma unroll
     for (int e = 0; e < 16; e++) x[e] = src[((size_t)u << 8) | (e << 4) | w];
     if (LM) __syncthreads();
@@ -394,7 +420,7 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
 #pragma unroll
     for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
     if (lazy) {
-        ntt16_round<false, 0, 8, true, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm);
+        ntt16_round<false, 0, 8, true, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm, nullptr, pol);
         const u32 ps = __ldg(&t.primes[pi].s);
         if (ps >= 24) {
             const u32 r = (u32)(__ldg(&t.primes[pi].mu) >> 32);
@@ -409,7 +435,7 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
             }
         }
     } else {
-        ntt16_round<false, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm);
+        ntt16_round<false, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI, lm, nullptr, pol);
 #pragma unroll
         for (int e = 0; e < 16; e++) my[w * 17 + e] = canon8(x[e], q, q2);
     }
@@ -417,9 +443,9 @@ __device__ __forceinline__ void contig_fwd_rows(const DevTables& t, const u64* _
 }
 
 template <bool INV, int MINB, bool LM = false>
-__global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet in, PolySet out, int is_final) {
+__global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet in, PolySet out, int flags) {
     __shared__ u64 sm[16 * kRowStride];
-    const int poly = blockIdx.z, limb = blockIdx.y;
+    const int poly = pass_poly(flags), limb = pass_limb(flags);
     const PolyRef& Ro = out.p[poly];
     if (limb >= Ro.nlimbs) return;
     const int logn = t.logn;
@@ -444,6 +470,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     const ulonglong2 NI = __ldg(&t.ninv[pi]);
     const ulonglong2 NI1 = __ldg(&t.inv1ninv[pi]);
     const ulonglong2* lm = LM ? lm_base(t.inv_rows, pi, u, w) : nullptr;
+    const u64 pol = tw_policy(t.ntt_order & 2);
     u64* my = sm + cc * kRowStride;
     u64 x[16];
 #pragma unroll
@@ -455,7 +482,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; e++) x[e] = my[w * 17 + e];  // point w*16 + e
-    ntt16_round<true, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI1, lm);
+    ntt16_round<true, 0, 8, false, false, LM>(x, w << 4, u, tw, q, q2, NI, NI1, lm, nullptr, pol);
 #pragma unroll
     for (int e = 0; e < 16; e++) my[w * 17 + e] = x[e];
     __syncthreads();
@@ -463,16 +490,17 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig(DevTables t, PolySet 
     for (int e = 0; e < 16; e++) x[e] = my[e * 17 + w];  // point e*16 + w
     ntt16_round<true, 4, 8>(x, w, u, tw, q, q2, NI, NI1);
 #pragma unroll
-    for (int e = 0; e < 16; e++) dst[((size_t)u << 8) | (e << 4) | w] = is_final ? canon4(x[e], q, q2) : x[e];
+    for (int e = 0; e < 16; e++)
+        dst[((size_t)u << 8) | (e << 4) | w] = (flags & kPassFinal) ? canon4(x[e], q, q2) : x[e];
 }
 
 // Forward stages 8..15 fused with the ModDown epilogue: for the canonical transform value v,
 // out = (x + c - v) s mod q (+ acc when the polynomial has one), with per-limb constants
 // {c, s, s'} (Shoup) at consts[3 limb].  The rows of `in` hold the output of stages 0..7.
 template <int MINB, bool LM = false>
-__global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, PolySet in, NttEpi e) {
+__global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, PolySet in, NttEpi e, int flags) {
     __shared__ u64 sm[16 * kRowStride];
-    const int poly = blockIdx.z, limb = blockIdx.y;
+    const int poly = pass_poly(flags), limb = pass_limb(flags);
     const PolyRef& Ri = in.p[poly];
     if (limb >= Ri.nlimbs) return;
     const int logn = t.logn;
@@ -511,10 +539,12 @@ static void prepare_twopass(void) {
 }
 
 template <bool INV, int MINB, bool LM>
-static void launch_contig(const DevTables& t, const PolySet& in, const PolySet& out, int is_final, cudaStream_t st) {
+static void launch_contig(const DevTables& t, const PolySet& in, const PolySet& out, int flags, cudaStream_t st) {
     dim3 grid(16, (unsigned)out.max_limbs, (unsigned)out.count);
-    k_ntt8_contig<INV, MINB, LM><<<grid, 256, 0, st>>>(t, in, out, is_final);
+    k_ntt8_contig<INV, MINB, LM><<<grid, 256, 0, st>>>(t, in, out, flags);
 }
+// flags of the second pass of a transform over the same data
+static int second_pass(const DevTables& t, int flags) { return flags | ((t.ntt_order & 1) ? kPassReverse : 0); }
 
 template <int MINB, bool LM>
 static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const PolySet& out, bool inverse,
@@ -530,7 +560,7 @@ static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const 
         PFT_LAUNCH_CHECK("ntt pass A");
         {
             PFT_PROF("ntt.fwd.contig", st, work);
-            launch_contig<false, MINB, LM>(t, out, out, 1, st);
+            launch_contig<false, MINB, LM>(t, out, out, second_pass(t, kPassFinal), st);
         }
         PFT_LAUNCH_CHECK("ntt pass B");
     } else {
@@ -541,7 +571,7 @@ static void launch_ntt16_twopass_v(const DevTables& t, const PolySet& in, const 
         PFT_LAUNCH_CHECK("intt pass B");
         {
             PFT_PROF("ntt.inv.strided", st, work);
-            k_ntt8_strided<true, 8, MINB><<<grid, 256, 0, st>>>(t, out, out, 1);
+            k_ntt8_strided<true, 8, MINB><<<grid, 256, 0, st>>>(t, out, out, second_pass(t, kPassFinal));
         }
         PFT_LAUNCH_CHECK("intt pass A");
     }
@@ -567,7 +597,7 @@ static void launch_ntt16_inverse_unscaled_v(const DevTables& t, const PolySet& i
     PFT_LAUNCH_CHECK("intt pass B");
     {
         PFT_PROF("ntt.inv.strided", st, work);
-        k_ntt8_strided<true, 8, MINB, true><<<grid, 256, 0, st>>>(t, out, out, 1);
+        k_ntt8_strided<true, 8, MINB, true><<<grid, 256, 0, st>>>(t, out, out, second_pass(t, kPassFinal));
     }
     PFT_LAUNCH_CHECK("intt pass A (unscaled)");
 }
@@ -585,7 +615,7 @@ static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttE
     {
         // named apart from the plain transform launches: it also moves the epilogue's operands
         PFT_PROF("epi.ntt_moddown", st, work);
-        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e);
+        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e, second_pass(t, 0));
     }
     PFT_LAUNCH_CHECK("ntt pass B + ModDown epilogue");
 }
@@ -965,7 +995,9 @@ double bfly_ceiling(const DevTables& t, cudaStream_t st) {
 // Issue rates of the two forms of 32-bit integer multiply the butterflies use: the low-word
 // multiply-add (mad.lo) and the forms that produce a high word (mad.hi, mad.wide).  Each thread
 // runs 8 independent chains of one form; the result word is written only for a value the
-// chains cannot reach, which keeps the work.
+// chains cannot reach, which keeps the work.  (Written as single PTX multiply-adds, the
+// high-word form measured slower, 24.2 against 28.1 per SM and clock: the faster forms below
+// give the higher, stricter bound.)
 template <int FORM>
 __global__ void __launch_bounds__(256) k_mul_rate(u32* sink, u32 a, u32 b, int rounds) {
     u32 x[8];

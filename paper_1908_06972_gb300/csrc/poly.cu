@@ -749,7 +749,9 @@ __global__ void __launch_bounds__(128) k_ks_inner_multi(DevTables t, KsBatch bt,
 // (kDrainPolls), before the CTA returns.  A copy of 2 KiB per digit row lands in microseconds;
 // only a memory system that has stopped answering could outlast both bounds, and then the CTA
 // returns with the copy still pending and its results flagged invalid (the host reads
-// PFT_ERR_TIMEOUT from pft_device_status).
+// PFT_ERR_TIMEOUT from pft_device_status).  (Per-warp waits with an "empty" mbarrier per stage
+// in place of the two CTA barriers per input measured slower: 201 against 196 us for 4
+// ciphertexts at level 30.)
 constexpr int kKsStages = 3;
 constexpr int kKsChunk = 256;                // coefficients per CTA (2 KiB per digit row)
 constexpr long long kWaitPolls = 1ll << 22;  // polls of a bounded wait (seconds at most)
@@ -784,6 +786,23 @@ __device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, long long polls 
     for (long long i = 0; i < polls; i++)
         if (mbar_test(bar, parity)) return true;
     return false;
+}
+
+// One digit's term of both key products for one coefficient: v (a residue below 2^60) times the
+// key words kb and ka (split Montgomery form k0 | k1 << 32, k0 and k1 below 2^30), added to the
+// Karatsuba sums of the b and a outputs.
+__device__ __forceinline__ void ks_mac(Acc3K& sb, Acc3K& sa, u64 v, u64 kb, u64 ka) {
+    u32 x0, x1;
+    split30(v, x0, x1);
+    const u32 x01 = x0 + x1;
+    const u32 b0 = (u32)kb, b1 = (u32)(kb >> 32), a0 = (u32)ka, a1 = (u32)(ka >> 32);
+    acc3k_mac(sb, x0, x1, x01, b0, b1, b0 + b1);
+    acc3k_mac(sa, x0, x1, x01, a0, a1, a0 + a1);
+}
+// the canonical residue of the sum: (S00 + 2^30 S01 + 2^60 S11) 2^-64 mod p
+__device__ __forceinline__ u64 ks_value(const Acc3K& s, const DPrime& P) {
+    const U128 a = acc3_value(acc3k_fold(s));
+    return mont_reduce(a.hi, a.lo, P.q, P.mneg);
 }
 
 template <int BMAX>
@@ -858,34 +877,23 @@ __global__ void __launch_bounds__(128) k_ks_inner_bulk(DevTables t, KsBatch bt, 
         const int l = D.l, E = l + k, beta = (l + alpha - 1) / alpha;
         const int m = row < L ? row : l + row - L;
         const u64* st = ring + (size_t)s * stage_digits * kKsChunk + xl;
-        // sums of at most 8 products of residues below 2^60 in 30-bit-split partial sums (four
-        // widening multiply-adds per product), then one Montgomery reduction: the key words carry
-        // the factor 2^64 (sum < 8 p^2 < p 2^63)
-        Acc3 s0x = {0, 0, 0}, s0y = {0, 0, 0}, s1x = {0, 0, 0}, s1y = {0, 0, 0};
+        // sums of at most 8 products of residues below 2^60 in 30-bit-split Karatsuba partial
+        // sums (three widening multiply-adds per product), then one Montgomery reduction: the key
+        // words carry the factor 2^64 (sum < 8 p^2 < p 2^63)
+        Acc3K s0x = {0, 0, 0}, s0y = {0, 0, 0}, s1x = {0, 0, 0}, s1y = {0, 0, 0};
 #pragma unroll
         for (int j = 0; j < BMAX; j++) {
             if (j < beta) {
                 const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(st + (size_t)j * kKsChunk);
-                u32 x0, x1, y0, y1;
-                split30(v.x, x0, x1);
-                split30(v.y, y0, y1);
-                acc3_mac(s0x, x0, x1, (u32)kb[j].x, (u32)(kb[j].x >> 32));
-                acc3_mac(s0y, y0, y1, (u32)kb[j].y, (u32)(kb[j].y >> 32));
-                acc3_mac(s1x, x0, x1, (u32)ka[j].x, (u32)(ka[j].x >> 32));
-                acc3_mac(s1y, y0, y1, (u32)ka[j].y, (u32)(ka[j].y >> 32));
+                ks_mac(s0x, s1x, v.x, kb[j].x, ka[j].x);
+                ks_mac(s0y, s1y, v.y, kb[j].y, ka[j].y);
             }
         }
         ulonglong2 r0, r1;
-        {
-            U128 a = acc3_value(s0x);
-            r0.x = mont_reduce(a.hi, a.lo, P.q, P.mneg);
-            a = acc3_value(s0y);
-            r0.y = mont_reduce(a.hi, a.lo, P.q, P.mneg);
-            a = acc3_value(s1x);
-            r1.x = mont_reduce(a.hi, a.lo, P.q, P.mneg);
-            a = acc3_value(s1y);
-            r1.y = mont_reduce(a.hi, a.lo, P.q, P.mneg);
-        }
+        r0.x = ks_value(s0x, P);
+        r0.y = ks_value(s0y, P);
+        r1.x = ks_value(s1x, P);
+        r1.y = ks_value(s1y, P);
         *reinterpret_cast<ulonglong2*>(D.u + ((size_t)m << logn) + xo) = r0;
         *reinterpret_cast<ulonglong2*>(D.u + (((size_t)E + m) << logn) + xo) = r1;
         __syncthreads();  // every thread has read stage s
