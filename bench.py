@@ -1267,13 +1267,13 @@ def run_case_ks(args):
         pft.pft_mul_relin_batch(ctx, A, B, C)
     torch.cuda.synchronize()
     res = {"case": "ks", "level": L, "batch": 4, "compressed_keys": bool(args.compressed_keys)}
-    for fam in ("bconv", "ks_inner", "ntt", "sub_scale"):
+    for fam in ("bconv", "ks_inner", "ntt", "epi", "sub_scale"):
         pft.pft_prof_start(fam)
         for _ in range(args.steps):
             pft.pft_mul_relin_batch(ctx, A, B, C)
         ms, n, tot, work = pft.pft_prof_stop()
         res[fam] = {"us_per_launch": round(1e3 * ms / max(1, n), 2), "launches_per_op": n // args.steps,
-                    "gbs": round(work / (ms / 1e3) / 1e9, 1) if work and fam != "ntt" else None}
+                    "gbs": round(work / (ms / 1e3) / 1e9, 1) if work and fam not in ("ntt", "epi") else None}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):

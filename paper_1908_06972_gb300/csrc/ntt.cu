@@ -127,6 +127,8 @@ __device__ __forceinline__ ulonglong2 ldg_pol(const ulonglong2* p, u64 pol) {
 // bit 1 reverse order: the CTAs visit (polynomial, limb) from the last to the first, so that a
 // pass that follows another over the same data starts on what that pass wrote last.
 constexpr int kPassFinal = 1, kPassReverse = 2;
+// (fused ModDown pass) bit 2: prefetch the epilogue operands into L2 at the start of the CTA
+constexpr int kPassPrefetch = 4;
 __device__ __forceinline__ int pass_poly(int flags) {
     return (flags & kPassReverse) ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
 }
@@ -506,12 +508,20 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, Poly
     const int logn = t.logn;
     const int pi = prime_of(Ri, limb);
     const size_t base = (size_t)limb << logn;
-    contig_fwd_rows<LM>(t, Ri.ptr + base, pi, sm);
-    const u64 q = __ldg(&t.primes[pi].q);
-    const u64 c = __ldg(&e.consts[3 * limb]), s = __ldg(&e.consts[3 * limb + 1]), sp = __ldg(&e.consts[3 * limb + 2]);
     const u64* __restrict__ xs = e.x.p[poly].ptr + base;
     const u64* __restrict__ as = e.acc.p[poly].ptr;  // null: no accumulator for this polynomial
     u64* __restrict__ os = e.out.p[poly].ptr + base;
+    if (flags & kPassPrefetch) {
+        // ask L2 for this CTA's tile of the epilogue operands (one 128-byte line per thread and
+        // operand: 16 rows x 256 words) so that their DRAM reads overlap the transform
+        const int f = threadIdx.x * 16;
+        const size_t j = ((size_t)(blockIdx.x * 16 + (f >> 8)) << 8) | (f & 255);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(xs + j));
+        if (as) asm volatile("prefetch.global.L2 [%0];" ::"l"(as + base + j));
+    }
+    contig_fwd_rows<LM>(t, Ri.ptr + base, pi, sm);
+    const u64 q = __ldg(&t.primes[pi].q);
+    const u64 c = __ldg(&e.consts[3 * limb]), s = __ldg(&e.consts[3 * limb + 1]), sp = __ldg(&e.consts[3 * limb + 2]);
 #pragma unroll 4
     for (int k = 0; k < 16; k++) {
         const int f = threadIdx.x + 256 * k;
@@ -615,7 +625,11 @@ static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttE
     {
         // named apart from the plain transform launches: it also moves the epilogue's operands
         PFT_PROF("epi.ntt_moddown", st, work);
-        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e, second_pass(t, 0));
+        static const int prefetch = [] {
+            const char* v = getenv("PFT_EPI_PREFETCH");
+            return v && atoi(v) == 0 ? 0 : kPassPrefetch;
+        }();
+        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e, second_pass(t, prefetch));
     }
     PFT_LAUNCH_CHECK("ntt pass B + ModDown epilogue");
 }
