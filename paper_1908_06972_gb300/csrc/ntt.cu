@@ -625,11 +625,8 @@ static void launch_ntt16_epi_v(const DevTables& t, const PolySet& io, const NttE
     {
         // named apart from the plain transform launches: it also moves the epilogue's operands
         PFT_PROF("epi.ntt_moddown", st, work);
-        static const int prefetch = [] {
-            const char* v = getenv("PFT_EPI_PREFETCH");
-            return v && atoi(v) == 0 ? 0 : kPassPrefetch;
-        }();
-        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e, second_pass(t, prefetch));
+        k_ntt8_contig_epi<MINB, LM><<<grid, 256, 0, st>>>(t, io, e,
+                                                           second_pass(t, (t.ntt_order & 4) ? kPassPrefetch : 0));
     }
     PFT_LAUNCH_CHECK("ntt pass B + ModDown epilogue");
 }
