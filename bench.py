@@ -153,8 +153,10 @@ def run_gpu(args):
     pft.build()
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED,
                              flags=pft.PFT_COMPRESSED_KEYS if args.compressed_keys else 0)
-    tuned, tune_us = pft.pft_autotune(ctx)
-    tune_report = pft.pft_autotune_report(ctx)
+    tune_report = None
+    if AUTOTUNE[0]:
+        pft.pft_autotune(ctx)
+        tune_report = pft.pft_autotune_report(ctx)
     bfly_ceiling = pft.pft_bfly_ceiling(ctx) / 1e9  # G butterflies/s of the butterfly on register data
     mul_lo, mul_hi, mul_wide = pft.pft_mul_rates(ctx)  # measured 32-bit multiply issue rates
     pft.pft_keygen(ctx, STEPS_ROT, True)
@@ -209,9 +211,9 @@ def run_gpu(args):
 
     # the same step captured once as a CUDA graph and replayed (separate context: graph capture
     # needs the stream-ordered default allocator and a non-default stream)
-    graph_value = None
+    graph_value = graph_ctx_eager_value = None
     if args.graph:
-        graph_value = graph_measure(pft, torch, synth, args.steps, args.warmup, rank, world)
+        graph_value, graph_ctx_eager_value = graph_measure(pft, torch, synth, args.steps, args.warmup, rank, world)
 
     # plain one-op-per-launch path (same GPU, same inputs)
     plain = None
@@ -393,6 +395,7 @@ def run_gpu(args):
                       "parallelism": "replicas" if world > 1 else "single"},
            "plain_value": round(plain, 3) if plain else None,
            "graph_value": round(graph_value, 3) if graph_value else None,
+           "graph_context_eager_value": round(graph_ctx_eager_value, 3) if graph_ctx_eager_value else None,
            "e2e": {"value": round(e2e, 3), "unit": "mult+relin/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "split": e2e_split},
            "gpu_launches": int(all_launches), "roofline": roof,
@@ -412,6 +415,7 @@ def graph_measure(pft, torch, synth, steps, warmup, rank, world):
     stream = torch.cuda.Stream()
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, FIRST, MID, SPECIAL, SCALE, SEED, allocator=None,
                              stream=stream.cuda_stream)
+    tune(pft, ctx)  # the transform plans of the main context's step (chosen per launch size)
     pft.pft_keygen(ctx, STEPS_ROT, True)
     A, B = [], []
     for i, l in enumerate(levels()):
@@ -428,28 +432,33 @@ def graph_measure(pft, torch, synth, steps, warmup, rank, world):
         for s in STEPS_ROT:
             pft.pft_rotate_batch(ctx, C, s, C)
 
-    step()
+    def timed(fn):
+        stream.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return reduce_max(e0.elapsed_time(e1), "cuda")
+
+    for _ in range(warmup):
+        step()
+    eager_ms = timed(step)  # the same context's eager step (stream-ordered allocator, no autotuning)
     pft.pft_graph_begin(ctx)
     step()
     g = pft.pft_graph_end(ctx)
     for _ in range(warmup):
         pft.pft_graph_launch(ctx, g)
-    stream.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        pft.pft_graph_launch(ctx, g)
-    e1.record(stream)
-    stream.synchronize()
-    ms = reduce_max(e0.elapsed_time(e1), "cuda")
+    ms = timed(lambda: pft.pft_graph_launch(ctx, g))
     pft.pft_graph_destroy(g)
     for h in A + B + C:
         pft.pft_ct_destroy(h)
     pft.pft_ctx_destroy(ctx)
-    return throughput(BATCH * steps, world, ms / 1e3)
+    return throughput(BATCH * steps, world, ms / 1e3), throughput(BATCH * steps, world, eager_ms / 1e3)
 
 
 RG_WORKLOAD = ("key switching of the two serving rings in one step: N=2^16 (60 + 29x40 bits + 4 special, digits of "
@@ -467,6 +476,7 @@ def rings_measure(pft, torch, synth, reps):
         st = torch.cuda.Stream()
         ctx = pft.pft_ctx_create(logn, lim, ksp, alpha, 60, 40, 60, 2.0 ** 40, SEED, allocator=None,
                                  stream=st.cuda_stream)
+        tune(pft, ctx)
         pft.pft_keygen(ctx, [], True)
         lv = synth.batch_levels(32, lo, hi, seed=logn)
         A, B = [], []
@@ -543,6 +553,7 @@ def fasttext_measure(pft, torch, steps, warmup, plain_docs=1):
     from paper_1908_06972_gb300 import synth
 
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, 60, 40, 60, 2.0 ** 40, SEED)
+    tune(pft, ctx)
     n = 1 << LOGN
     t = n // 2
     pft.pft_keygen(ctx, [1 << i for i in range(15)], False)
@@ -662,6 +673,7 @@ def fasttext_measure_l30(pft, torch, level=30, batch=8):
     from paper_1908_06972_gb300 import synth
 
     ctx = pft.pft_ctx_create(LOGN, L, K_SP, ALPHA, 60, 40, 60, 2.0 ** 40, SEED)
+    tune(pft, ctx)
     pft.pft_keygen(ctx, [1 << i for i in range(15)], False)
     H, O = synth.fasttext_weights(77, FT_M, FT_N, FT_C)
     docs = synth.documents(78, FT_M, FT_BATCH)
@@ -740,6 +752,7 @@ def serve_measure(pft, torch, n_req, rate, budget_gib, near, fig3_leg=True, seed
     for logn, lim, ksp, alpha, _ in SV_RINGS:
         st = torch.cuda.Stream()
         ctx = pft.pft_ctx_create(logn, lim, ksp, alpha, 60, 40, 60, 2.0 ** 40, SEED, stream=st.cuda_stream)
+        tune(pft, ctx)
         steps = [1 << i for i in range(logn - 1)] + list(range(3, FT_N))  # TotalSum; diagonal shifts 1..n-1
         pft.pft_keygen(ctx, steps, False)
         streams.append(st)
@@ -1039,6 +1052,7 @@ def train_measure(pft, torch, n_docs, plain_docs, with_diag=True):
 
     sc = 2.0 ** 40
     ctx = pft.pft_ctx_create(LOGN, TR_L, K_SP, ALPHA, 60, 40, 60, sc, SEED)
+    tune(pft, ctx)
     pft.pft_keygen(ctx, [1 << i for i in range(LOGN - 1)], True)
     t = (1 << LOGN) // 2
     handles = []
@@ -1171,6 +1185,15 @@ def train_measure(pft, torch, n_docs, plain_docs, with_diag=True):
                 "note": "one call per operation per ciphertext, products relinearised one by one, "
                         "update not included"},
             "max_abs_err_grad_vs_fp64": err, "model_levels_after": [lvH, lvO], "eta": TR_ETA}
+
+
+AUTOTUNE = [True]  # --autotune 0: every context keeps the plans it starts with
+
+
+def tune(pft, ctx):
+    """The transform-plan search on a leg's context, as a user would run it (unless disabled)."""
+    if AUTOTUNE[0]:
+        pft.pft_autotune(ctx)
 
 
 def link_rates(host_in, host_out, reps=5):
@@ -1362,6 +1385,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="0: no transform-plan search; the contexts' initial plans (for ncu captures)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=1)
@@ -1387,6 +1412,7 @@ def main():
     ap.add_argument("--serve-near", type=float, default=0.9,
                     help="second trace offered at this fraction of the measured capacity (0: skip)")
     args = ap.parse_args()
+    AUTOTUNE[0] = bool(args.autotune)
     if args.case == "ntt":
         run_case_ntt(args)
     elif args.case == "ks":

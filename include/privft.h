@@ -362,7 +362,9 @@ int pft_rotate_batch(pft_ctx* ctx, const pft_ct* const* a, int B, int32_t step, 
  * stream) and the fastest is kept for launches of that size.  us_out (may be NULL) receives up
  * to `cap` plan times (microseconds) of the largest bucket, *chosen its choice (an index into
  * the plan list of pft_autotune_report).  Synchronous.  The environment variable PFT_NTT16
- * (twopass, twopass4, cluster, generic) overrides every choice at N = 2^16. */
+ * (twopass, twopass4, cluster, generic) overrides every choice at N = 2^16.  Before any search
+ * a context uses the two-pass kernels at 3 CTAs per SM, and at 4 CTAs per SM for launches of more
+ * than 512 limbs at N = 2^16 (the search's choice for that bucket on a GB300). */
 #define PFT_NTT16_VARIANTS 4
 int pft_autotune(pft_ctx* ctx, double* us_out, int cap, int* chosen);
 /* The last search as JSON text: {"N": n, "buckets": [{"limbs": k, "chosen": name,
@@ -371,7 +373,7 @@ int pft_autotune(pft_ctx* ctx, double* us_out, int cap, int* chosen);
  * *len (may be NULL) the full length. */
 int pft_autotune_report(pft_ctx* ctx, char* buf, size_t cap, size_t* len);
 /* Use plan `plan` (index into the ring's plan list, in the order above) for every launch size;
- * -1: back to the fixed variant. */
+ * -1: back to the plans a new context starts with. */
 int pft_set_transform_plan(pft_ctx* ctx, int plan);
 /* Pin the N = 2^16 transform variant (0..PFT_NTT16_VARIANTS-1: two-pass 3 CTAs/SM, two-pass 4
  * CTAs/SM, cluster, generic 8 + 8) for every launch size, without timing. */

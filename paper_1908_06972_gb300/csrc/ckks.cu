@@ -124,7 +124,7 @@ static void build_tables(pft_ctx* c) {
     }
     c->tabs.logn = logn;
     c->tabs.n = n;
-    for (int b = 0; b < kNttBuckets; b++) c->tabs.plan[b].kind = -1;  // until the autotuner chooses
+    default_plans(c->tabs);  // until the autotuner chooses
     {
         const char* e = getenv("PFT_BCONV");
         c->tabs.bconv_tc = e && strcmp(e, "tc") == 0 ? 1 : 0;  // integer pipes unless asked
@@ -2211,10 +2211,9 @@ int pft_set_transform_plan(pft_ctx* c, int plan) {
         DevTables::Plan cand[16];
         const int nc = ntt_candidates(c->logn, cand, nullptr, 16);
         NEED(plan >= -1 && plan < nc, PFT_ERR_ARG, "plan out of range");
-        for (int b = 0; b < kNttBuckets; b++) {
-            if (plan < 0) c->tabs.plan[b].kind = -1;
-            else c->tabs.plan[b] = cand[plan];
-        }
+        if (plan < 0) default_plans(c->tabs);
+        else
+            for (int b = 0; b < kNttBuckets; b++) c->tabs.plan[b] = cand[plan];
     });
 }
 

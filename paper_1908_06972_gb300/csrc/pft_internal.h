@@ -88,6 +88,13 @@ struct DevTables {
 constexpr int kNttVariants = 4;
 constexpr int kNttBuckets = 3;
 inline int ntt_bucket(double limbs) { return limbs <= 64 ? 0 : limbs <= 512 ? 1 : 2; }
+// Plans before any search: the fixed variant, except that launches of more than 512 limbs at
+// N = 2^16 take the two-pass kernels at 4 CTAs per SM (the search's choice for that bucket on a
+// GB300: 324.5 against 313.8 mult+relin/s in the benchmark step).
+inline void default_plans(DevTables& t) {
+    for (int b = 0; b < kNttBuckets; b++) t.plan[b].kind = -1;
+    if (t.logn == 16) t.plan[2].kind = 1;
+}
 
 struct Error {
     int code;
