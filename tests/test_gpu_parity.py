@@ -468,6 +468,33 @@ def test_tensor_core_basis_conversion_bit_exact(gpu, monkeypatch):
         p.close()
 
 
+
+@pytest.mark.parametrize("order", [0, 5])
+def test_transform_memory_order_flags_bit_exact(gpu, monkeypatch, order):
+    """The memory-order switches of the N = 2^16 two-pass transforms (PFT_NTT_ORDER: reverse second
+    pass, L2 policy of the row twiddles, prefetch of the ModDown epilogue's operands; the default
+    turns all on) change no bit: HMUL + relinearisation and rotation of a mixed-level batch against
+    the oracle with the switches off (0) and with two of them (5)."""
+    monkeypatch.setenv("PFT_NTT_ORDER", str(order))
+    p = Pair(gpu, 16, 8, 4, 4, mid_bits=50, rot_steps=[1])
+    monkeypatch.delenv("PFT_NTT_ORDER")
+    try:
+        o, pf, ctx = p.orc, p.pft, p.ctx
+        lv = [8, 5]
+        A = [o.encrypt_sk(o.encode(synth.slots(90 + i, 256), level=l), 190 + i) for i, l in enumerate(lv)]
+        B = [o.encrypt_sk(o.encode(synth.slots(95 + i, 256), level=l), 195 + i) for i, l in enumerate(lv)]
+        gA, gB = [p.ct(x) for x in A], [p.ct(x) for x in B]
+        C = [p.empty() for _ in lv]
+        pf.pft_mul_relin_batch(ctx, gA, gB, C)
+        M = [o.mul_relin(a, b) for a, b in zip(A, B)]
+        for i in range(len(lv)):
+            p.assert_equal(C[i], M[i], "order %d: mul_relin level %d" % (order, lv[i]))
+        pf.pft_rotate_batch(ctx, C, 1, C)
+        for i in range(len(lv)):
+            p.assert_equal(C[i], o.rotate(M[i], 1), "order %d: rotate level %d" % (order, lv[i]))
+    finally:
+        p.close()
+
 # ---- seeded compressed switching keys -----------------------------------------------------------
 @pytest.mark.parametrize("logn,L,k,alpha,mid", [(12, 3, 1, 1, 40), (12, 10, 1, 1, 40), (16, 6, 2, 4, 50)])
 def test_compressed_keys_bit_exact(gpu, logn, L, k, alpha, mid):
