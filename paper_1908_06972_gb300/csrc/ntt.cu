@@ -522,14 +522,34 @@ __global__ void __launch_bounds__(256, MINB) k_ntt8_contig_epi(DevTables t, Poly
     contig_fwd_rows<LM>(t, Ri.ptr + base, pi, sm);
     const u64 q = __ldg(&t.primes[pi].q);
     const u64 c = __ldg(&e.consts[3 * limb]), s = __ldg(&e.consts[3 * limb + 1]), sp = __ldg(&e.consts[3 * limb + 2]);
-#pragma unroll 4
-    for (int k = 0; k < 16; k++) {
-        const int f = threadIdx.x + 256 * k;
-        const int c2 = f >> 8, m = f & 255;
-        const size_t j = ((size_t)(blockIdx.x * 16 + c2) << 8) | m;
-        u64 r = mul_shoup(submod(addmod(xs[j], c, q), sm[c2 * kRowStride + m + (m >> 4)], q), s, sp, q);
-        if (as) r = addmod(r, as[base + j], q);
-        os[j] = r;
+    // each thread: two adjacent points (16-byte loads and stores) of rows r0, r0 + 2, ..., r0 + 14;
+    // the operands of four rows are loaded before any is used, so that more bytes are in flight
+    // (the transform's registers are free by now).  An even point m and m + 1 share their
+    // 16-point group, so their transform values are adjacent in shared memory.
+    const int m = 2 * (threadIdx.x & 127), r0 = threadIdx.x >> 7;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        ulonglong2 xv[4], av[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const size_t j = ((size_t)(blockIdx.x * 16 + r0 + 2 * (4 * h + i)) << 8) | m;
+            xv[i] = *reinterpret_cast<const ulonglong2*>(xs + j);
+            if (as) av[i] = *reinterpret_cast<const ulonglong2*>(as + base + j);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int c2 = r0 + 2 * (4 * h + i);
+            const size_t j = ((size_t)(blockIdx.x * 16 + c2) << 8) | m;
+            const u64* v = sm + c2 * kRowStride + m + (m >> 4);
+            ulonglong2 r;
+            r.x = mul_shoup(submod(addmod(xv[i].x, c, q), v[0], q), s, sp, q);
+            r.y = mul_shoup(submod(addmod(xv[i].y, c, q), v[1], q), s, sp, q);
+            if (as) {
+                r.x = addmod(r.x, av[i].x, q);
+                r.y = addmod(r.y, av[i].y, q);
+            }
+            *reinterpret_cast<ulonglong2*>(os + j) = r;
+        }
     }
 }
 
