@@ -201,6 +201,13 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step_batched(A, B, C)
+    # host cost of issuing one step into an idle queue (no back-pressure from the device): the
+    # rate the host could sustain if the device were infinitely fast
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    step_batched(A, B, C)
+    host_issue_ms = 1e3 * (time.perf_counter() - h0)
+    torch.cuda.synchronize()
     # timed region: batched path, dominant kernel family timed with events on the library stream
     pft.pft_prof_start(args.roofline_kernel)
     with ClockSampler(local) as clk:
@@ -316,7 +323,8 @@ def run_gpu(args):
     e2e_split = {"compute_ms": round(sum(ev[0].elapsed_time(ev[1]) for ev in marks) / len(marks), 2),
                  "wall_ms": round(1e3 * e2e_s / args.steps, 2),
                  "host_ms": {key: round(1e3 * v / args.steps, 2) for key, v in host.items()},
-                 "link_gbs": link_rates(host_in[0][0], host_out[0])}
+                 "link_gbs": link_rates(host_in[0][0], host_out[0]),
+                 "host_issue_ms_idle_queue": round(host_issue_ms, 2)}
     for h in C2[1] + IN2[0] + IN2[1]:
         pft.pft_ct_destroy(h)
 
