@@ -44,8 +44,10 @@ WORKLOAD = ("N=2^16, 30 limbs (60 + 29x50 bits) + 4 special (60 bits), digits of
 SMS, IMAD_PER_CLK, SM_MHZ_MAX, IMAD_PER_MULMOD = 152, 64, 2070.0, 9
 # DRAM bytes (read + written) per limb and pass of the N = 2^16 transform kernels: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum over the four two-pass launches of the
-# 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes.
-NTT_DRAM_BYTES_PER_LIMB_PASS = 1.0121e6
+# 16 x 30-limb case (bench.py --case ntt), divided by their 4 x 480 limb-passes (the kernels
+# with the reverse-order second pass and the evict-last row twiddles: 1913.7 MB; 1943.1 MB
+# before those changes).
+NTT_DRAM_BYTES_PER_LIMB_PASS = 0.9967e6
 
 
 def alu_bound(lo, hi):
