@@ -383,7 +383,8 @@ int pft_set_transform_variant(pft_ctx* ctx, int variant);
  *                  transform visits (polynomial, limb) in reverse, so it starts on the data the
  *                  first pass wrote last (still in L2); bit 1: the row twiddles are read with an
  *                  L2 evict-last policy; bit 2: the pass that applies ModDown's epilogue asks L2
- *                  for the epilogue's operands at the start of each block.  Default 7.
+ *                  for the epilogue's operands at the start of each block (measured slower with
+ *                  the current epilogue, off by default).  Default 3.
  *   PFT_BCONV=tc   read at pft_ctx_create: basis conversion of four-prime digits on the tensor
  *                  cores (exact byte-plane products; measured slower than the default). */
 

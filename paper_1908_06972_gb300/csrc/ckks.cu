@@ -129,7 +129,7 @@ static void build_tables(pft_ctx* c) {
         const char* e = getenv("PFT_BCONV");
         c->tabs.bconv_tc = e && strcmp(e, "tc") == 0 ? 1 : 0;  // integer pipes unless asked
         const char* o = getenv("PFT_NTT_ORDER");
-        c->tabs.ntt_order = o ? atoi(o) & 7 : 7;
+        c->tabs.ntt_order = o ? atoi(o) & 7 : 3;
     }
     c->tabs.primes = tab_upload(c, dp);
     // twiddles

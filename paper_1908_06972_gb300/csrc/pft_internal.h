@@ -72,7 +72,8 @@ struct DevTables {
     // creation: bit 0 = the second pass visits (polynomial, limb) in reverse, so its first CTAs
     // read what the first pass wrote last, still in L2; bit 1 = the row twiddles are loaded with
     // an L2 evict-last policy, so the streaming data evict them less; bit 2 = the fused ModDown
-    // pass asks L2 for its epilogue operands at the start of each CTA).  Default 7.
+    // pass asks L2 for its epilogue operands at the start of each CTA: faster while the epilogue
+    // read one 8-byte word per row, slower since it reads 16 bytes four rows ahead).  Default 3.
     int ntt_order;
     int ntt_variant;       // N = 2^16 transform: 0 two-pass (3 CTAs/SM), 1 two-pass (4 CTAs/SM),
                            // 2 one-launch cluster, 3 generic staged passes
